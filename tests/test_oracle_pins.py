@@ -1,0 +1,589 @@
+"""Pins of the FP64 oracle against things other than itself: published
+known-answer vectors, closed forms of the physics model, brute-force
+quadrature, exact invariants and numbers printed in the paper.
+
+Each test names the plausible mistake it would catch.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+import workloads as W
+from tests.conftest import read_golden
+
+MEC2 = 510.99895
+RE = 2.8179403262e-13
+
+
+# ---------------------------------------------------------------------------
+# RNG
+# ---------------------------------------------------------------------------
+def test_philox_known_answers(oracle):
+    """Philox4x32-10 against the Random123 KAT vectors (Salmon et al. SC'11).
+    Catches a wrong multiplier, Weyl constant, round count or word order."""
+    for row in read_golden("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in row.split()]
+        assert oracle.philox(v[0:4], v[4:6]) == v[6:10]
+
+
+def test_uniform_open_interval(oracle):
+    """u = (k + 1/2) 2^-23 from the top 23 bits: never 0 or 1, exact ends."""
+    assert oracle.uniform(0) == 0.5 * 2.0 ** -23
+    assert oracle.uniform(0xFFFFFFFF) == 1.0 - 0.5 * 2.0 ** -23
+    assert oracle.uniform(0x80000000) == 0.5 + 0.5 * 2.0 ** -23
+
+
+# ---------------------------------------------------------------------------
+# physics model
+# ---------------------------------------------------------------------------
+def kn_dsigma_domega(e_kev, cos_t):
+    """Klein-Nishina differential cross section per electron (cm^2/sr)."""
+    k = e_kev / MEC2
+    p = 1.0 / (1.0 + k * (1.0 - cos_t))  # E'/E
+    return 0.5 * RE * RE * p * p * (p + 1.0 / p - (1.0 - cos_t * cos_t))
+
+
+@pytest.mark.parametrize("e", [10.0, 30.0, 100.0, 340.0, 511.0, 2000.0])
+def test_sigma_kn_equals_integral_of_differential(oracle, e):
+    """Closed-form total KN cross section == 2 pi * integral of dsigma/dOmega,
+    over the transport's energy domain (cutoff 10 keV up to 511 keV).
+    Catches a dropped or mis-signed term of the closed form."""
+    val, _ = integrate.quad(lambda c: kn_dsigma_domega(e, c), -1.0, 1.0, epsabs=0, epsrel=1e-12)
+    assert oracle.sigma_kn(e) == pytest.approx(2 * math.pi * val, rel=1e-9, abs=0)
+
+
+def test_sigma_kn_thomson_limit(oracle):
+    """sigma -> (8 pi/3) r_e^2 (1 - 2k + 26/5 k^2 - 133/10 k^3 + 1144/35 k^4) at
+    low energy.  (Below ~2 keV the closed form loses digits to cancellation in
+    FP64; the transport never evaluates it there.)"""
+    e = 2.0
+    k = e / MEC2
+    thomson = 8 * math.pi / 3 * RE * RE
+    series = 1 - 2 * k + 26 / 5 * k ** 2 - 133 / 10 * k ** 3 + 1144 / 35 * k ** 4
+    assert oracle.sigma_kn(e) == pytest.approx(thomson * series, rel=1e-8, abs=0)
+
+
+def test_material_anchors(oracle):
+    """The configs fix mu_total(511) = 0.87/cm and a 0.34 photoelectric share for
+    LYSO, 0.096/cm for water; photoelectric scales as E^-3 from 511 keV."""
+    assert oracle.mu(W.LYSO, 511.0) == pytest.approx(0.87, rel=1e-14)
+    assert oracle.mu(W.LYSO, 511.0, "photo") == pytest.approx(0.87 * 0.34, rel=1e-14)
+    assert oracle.mu(W.LYSO, 255.5, "photo") == pytest.approx(8 * 0.87 * 0.34, rel=1e-14)
+    assert oracle.mu(W.WATER, 511.0) == pytest.approx(0.096, rel=1e-14)
+    assert oracle.mu(W.WATER, 200.0, "photo") == 0.0
+    # Compton part follows sigma_KN(E) / sigma_KN(511) from its 511 keV anchor
+    r = oracle.mu(W.LYSO, 200.0, "compton") / oracle.mu(W.LYSO, 511.0, "compton")
+    assert r == pytest.approx(oracle.sigma_kn(200.0) / oracle.sigma_kn(511.0), rel=1e-14)
+    # literal electron density reading: mu_C = n_e sigma_KN
+    assert oracle.mu(W.LYSO_LITERAL_NE, 511.0, "compton") == pytest.approx(0.6017, abs=1e-4)
+
+
+@pytest.mark.parametrize("e", [511.0, 340.0, 100.0])
+def test_kahn_sampler_matches_klein_nishina(oracle, e):
+    """Chi-square of sampled cos(theta) against the closed-form dsigma/dOmega.
+    Catches a wrong branch probability, acceptance test or kinematics."""
+    n = 200_000
+    ct, eo, tr = oracle.kahn(seed=7, h0=1000, n=n, e_kev=e)
+    edges = np.linspace(-1.0, 1.0, 41)
+    obs, _ = np.histogram(ct, edges)
+    tot = integrate.quad(lambda c: kn_dsigma_domega(e, c), -1, 1, epsrel=1e-12)[0]
+    exp = np.array([integrate.quad(lambda c: kn_dsigma_domega(e, c), a, b, epsrel=1e-12)[0]
+                    for a, b in zip(edges[:-1], edges[1:])]) / tot * n
+    chi2 = ((obs - exp) ** 2 / exp).sum()
+    p = stats.chi2.sf(chi2, len(obs) - 1)
+    assert p > 1e-3, (chi2, p)
+    # Compton kinematics: E' = E / (1 + k (1 - cos theta))
+    np.testing.assert_allclose(eo, e / (1.0 + e / MEC2 * (1.0 - ct)), rtol=1e-12)
+    # mean energy transfer against its quadrature
+    mean_t = integrate.quad(lambda c: kn_dsigma_domega(e, c) * (e - e / (1 + e / MEC2 * (1 - c))), -1, 1,
+                            epsrel=1e-12)[0] / tot
+    t = e - eo
+    assert abs(t.mean() - mean_t) < 4 * t.std() / math.sqrt(n)
+    assert tr.min() >= 1
+
+
+def test_rotation_keeps_angle_and_norm(oracle):
+    """New direction is a unit vector at angle theta from the old one, with the
+    azimuth spread uniformly; also near the pole branch."""
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=(2000, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    d[:10] = [0, 0, 1]
+    d[10:20] = [0, 0, -1]
+    c = rng.uniform(-1, 1, len(d))
+    u = rng.uniform(0, 1, len(d))
+    r = oracle.rotate(d, c, u)
+    np.testing.assert_allclose(np.linalg.norm(r, axis=1), 1.0, atol=1e-12)
+    np.testing.assert_allclose((r * d).sum(1), c, atol=1e-12)
+    # azimuth linear in u for a fixed d and theta
+    d0 = np.tile([0.3, -0.4, math.sqrt(1 - 0.25)], (64, 1))
+    uu = np.arange(64) / 64
+    rr = oracle.rotate(d0, np.full(64, 0.2), uu)
+    e1 = rr[0] - 0.2 * d0[0]
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(d0[0], e1)
+    ang = np.unwrap(np.arctan2((rr - 0.2 * d0) @ e2, (rr - 0.2 * d0) @ e1))
+    np.testing.assert_allclose(np.abs(np.diff(ang)), 2 * math.pi / 64, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# transport against closed forms
+# ---------------------------------------------------------------------------
+def slab_scanner(mu_total, photo_frac, depth):
+    mats = [W.AIR, dict(mu_total_511_cm=mu_total, photo_frac_511=photo_frac, electron_density_cm3=0.0)]
+    return W.scanner(1, 100.0, [W.layer(1, 1, 400.0, 0.0, depth)], materials=mats, name="slab")
+
+
+@pytest.mark.parametrize("mu_t,pf,depth", [(0.87, 0.34, 10.0), (0.5, 0.0, 20.0), (1.3, 1.0, 4.0)])
+def test_slab_transmission(oracle, mu_t, pf, depth):
+    """Pencil beam at normal incidence: uncollided fraction exp(-mu L), mean
+    first-interaction depth of the truncated exponential, photoelectric share
+    of first interactions.  Catches mm/cm mix-ups, a wrong majorant or a
+    swapped photo/Compton branch."""
+    n = 200_000
+    sc = slab_scanner(mu_t, pf, depth)
+    r = oracle.simulate(sc, W.pencil_source(direction=(1, 0, 0)), W.digitizer(), n, seed=11, threads=8)
+    hits = r["hits"]
+    g0 = hits[hits["gamma"] == 0]
+    assert (hits["gamma"] == 1).sum() == 0  # photon 1 flies away from the single panel
+    # first interaction of each photon 0
+    first_idx = np.unique(g0["h"], return_index=True)[1]
+    first = g0[first_idx]
+    p_int = len(first) / n
+    p_exp = 1.0 - math.exp(-mu_t * depth / 10.0)
+    assert abs(p_int - p_exp) < 4.5 * math.sqrt(p_exp * (1 - p_exp) / n)
+    mu_mm = mu_t / 10.0
+    mean_w = 1 / mu_mm - depth * math.exp(-mu_mm * depth) / (1 - math.exp(-mu_mm * depth))
+    sd_w = first["w"].std()
+    assert abs(first["w"].mean() - mean_w) < 4.5 * sd_w / math.sqrt(len(first))
+    n_photo = (first["edep"] == 511.0).sum()
+    assert abs(n_photo / len(first) - pf) < 4.5 * math.sqrt(max(pf * (1 - pf), 1e-12) / len(first)) + 1e-12
+    # all energy accounted for
+    assert np.all(r["tally_edep"] >= 0)
+
+
+def rect_solid_angle(a, b, d):
+    """Solid angle of an a x b rectangle seen from distance d on its normal axis."""
+    return 4.0 * math.atan(a * b / (2.0 * d * math.sqrt(4 * d * d + a * a + b * b)))
+
+
+def box_solid_angle_quadrature(corners_fn, src, n=600):
+    """Brute-force solid angle of a convex box: sum over faces that face the
+    source of the integral of cos / r^2 on a fine midpoint grid."""
+    total = 0.0
+    for (o, e1, e2) in corners_fn():
+        o, e1, e2 = map(np.asarray, (o, e1, e2))
+        nrm = np.cross(e1, e2)
+        nrm /= np.linalg.norm(nrm)
+        s = (np.arange(n) + 0.5) / n
+        P = o[None, None, :] + s[:, None, None] * e1[None, None, :] + s[None, :, None] * e2[None, None, :]
+        rv = P - src
+        r = np.linalg.norm(rv, axis=2)
+        cosang = (rv @ nrm) / r
+        dA = np.linalg.norm(np.cross(e1, e2)) / (n * n)
+        val = (cosang / (r * r)).sum() * dA
+        total += abs(val) if np.sign((o - src) @ nrm) != 0 and ((o - src) @ nrm) > 0 else 0.0
+    return total
+
+
+def test_geometric_acceptance_central(oracle):
+    """Config-1 ring, source at the centre: accepted fraction of isotropic rays
+    == 8 * rectangle solid angle / 4 pi (= 0.06357)."""
+    sc = W.config1_scanner()
+    ext = oracle.panel_extent(sc)
+    assert ext[0] == pytest.approx(12.8) and ext[1] == pytest.approx(12.8) and ext[2] == pytest.approx(10.0)
+    p_exp = 8 * rect_solid_angle(12.8, 12.8, 40.0) / (4 * math.pi)
+    assert p_exp == pytest.approx(0.06357, abs=2e-5)
+    rng = np.random.default_rng(5)
+    n = 1_000_000
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    pn, ti = oracle.flight(sc, np.zeros((n, 3)), d)
+    p = (pn >= 0).mean()
+    assert abs(p - p_exp) < 4 * math.sqrt(p_exp * (1 - p_exp) / n)
+    # the front face is entered at distance R / cos(angle to the normal)
+    k = pn[pn >= 0]
+    phi = 2 * math.pi * k / 8
+    cosn = d[pn >= 0, 0] * np.cos(phi) + d[pn >= 0, 1] * np.sin(phi)
+    np.testing.assert_allclose(ti[pn >= 0], 40.0 / cosn, rtol=1e-12)
+
+
+def test_geometric_acceptance_offcentre(oracle):
+    """Off-centre source: MC acceptance == brute-force face quadrature of the
+    panel boxes (front and visible side faces)."""
+    sc = W.config1_scanner()
+    src = np.array([9.0, -6.0, 3.0])
+    U, V, Wd, R = 12.8, 12.8, 10.0, 40.0
+    total = 0.0
+    for k in range(8):
+        phi = 2 * math.pi * k / 8
+        n_ = np.array([math.cos(phi), math.sin(phi), 0.0])
+        u_ = np.array([-math.sin(phi), math.cos(phi), 0.0])
+        v_ = np.array([0.0, 0.0, 1.0])
+        c0 = R * n_ - U / 2 * u_ - V / 2 * v_  # inner-face low corner
+
+        def faces(c0=c0, n_=n_, u_=u_, v_=v_):
+            return [(c0, U * u_, V * v_),                     # front (w = 0)
+                    (c0 + Wd * n_, V * v_, U * u_),           # back
+                    (c0, V * v_, Wd * n_),                    # side u = -U/2
+                    (c0 + U * u_, Wd * n_, V * v_),           # side u = +U/2
+                    (c0, Wd * n_, U * u_),                    # bottom v = -V/2
+                    (c0 + V * v_, U * u_, Wd * n_)]           # top v = +V/2
+        # outward normal orientation: use the box centre to orient each face
+        centre = c0 + U / 2 * u_ + V / 2 * v_ + Wd / 2 * n_
+
+        def oriented():
+            for o, e1, e2 in faces():
+                nn = np.cross(e1, e2)
+                fc = o + 0.5 * e1 + 0.5 * e2
+                if (fc - centre) @ nn < 0:
+                    e1, e2 = e2, e1
+                yield o, e1, e2
+
+        # a face is visible when its outward normal points toward the source
+        for o, e1, e2 in oriented():
+            nn = np.cross(e1, e2)
+            fc = o + 0.5 * e1 + 0.5 * e2
+            if (src - fc) @ nn > 0:
+                s = (np.arange(500) + 0.5) / 500
+                P = o[None, None, :] + s[:, None, None] * e1 + s[None, :, None] * e2
+                rv = P - src
+                r = np.linalg.norm(rv, axis=2)
+                nh = nn / np.linalg.norm(nn)
+                total += ((-(rv @ nh)) / r ** 3).sum() * np.linalg.norm(nn) / 500 ** 2
+    p_exp = total / (4 * math.pi)
+    rng = np.random.default_rng(6)
+    n = 1_000_000
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    pn, _ = oracle.flight(sc, np.tile(src, (n, 1)), d)
+    p = (pn >= 0).mean()
+    assert abs(p - p_exp) < 4 * math.sqrt(p_exp * (1 - p_exp) / n) + 1e-5, (p, p_exp)
+
+
+# ---------------------------------------------------------------------------
+# hierarchy indexing
+# ---------------------------------------------------------------------------
+def test_locate_lattice_points(oracle):
+    """Crystal centres locate to their own (layer, module, crystal) id; points in
+    the inter-crystal gaps, the reflector gap and the module gap are interval."""
+    sc = W.config3_scanner()   # two layers, the second offset by half a pitch
+    Us, Vs = sc["module_size_u"], sc["module_size_v"]
+    U = Us
+    V = 4 * Vs
+    cpm = sum(l["n_u"] * l["n_v"] for l in sc["layers"])
+    pts, want = [], []
+    w0 = 0.0
+    loff = 0
+    for li, l in enumerate(sc["layers"]):
+        w0 += l["gap_before"]
+        for mv in range(4):
+            for iv in range(l["n_v"]):
+                for iu in range(l["n_u"]):
+                    u = -U / 2 + l["offset_u"] + (iu + 0.5) * l["pitch_u"]
+                    v = -V / 2 + mv * Vs + l["offset_v"] + (iv + 0.5) * l["pitch_v"]
+                    pts.append((w0 + 0.5 * l["depth"], u, v))
+                    want.append((li, mv, (3 * 4 + mv) * cpm + loff + iv * l["n_u"] + iu, 1))
+        w0 += l["depth"]
+        loff += l["n_u"] * l["n_v"]
+    got = oracle.locate(sc, 3, pts)
+    assert np.array_equal(got, np.array(want, np.int32))
+    # gap points: inter-crystal gap, reflector gap, outside the offset layer's grid
+    gaps = [(2.5, -U / 2 + 1.0 + 0.01, 0.3 - V / 2),     # u on a cell boundary +- gap/2
+            (5.025, 0.0, 0.0),                           # reflector between the layers
+            (7.5, -U / 2 + 0.25, -V / 2 + 5.3)]          # below the offset grid of layer 2
+    got = oracle.locate(sc, 0, gaps)
+    assert np.all(got[:, 2] == -1) and np.all(got[:, 3] == 0)
+    assert got[1, 0] == -1
+
+
+def test_offset_dual_layer_volume_reduction(oracle):
+    """Sec. 3.2: the 2CL module has 1.94 % less crystal volume than 1CL
+    (50x50 + 51x51 half-depth layers vs 51x51).  Monte Carlo over the module
+    with the oracle's own locate()."""
+    vals = {k: float(v.split("=")[1]) if "=" in v else None
+            for k, v in ((r.split("=")[0].strip(), r) for r in read_golden("paper_text_values.txt"))}
+    rng = np.random.default_rng(9)
+    n = 600_000
+    pts = np.stack([rng.uniform(0, 10, n), rng.uniform(-25.5, 25.5, n), rng.uniform(-170.5, -170.5 + 51, n)], 1)
+    frac = {}
+    for kind in ("1CL", "2CL"):
+        sc = W.h2rspet(kind)
+        got = oracle.locate(sc, 0, pts)
+        frac[kind] = (got[:, 2] >= 0).mean()
+    red = 100 * (1 - frac["2CL"] / frac["1CL"])
+    assert abs(red - vals["volume_reduction_2cl_percent"]) < 0.12, red
+    assert frac["1CL"] == pytest.approx((0.92 / 1.0) ** 2, abs=3e-3)
+
+
+def test_h2rspet_dimensions(oracle):
+    """Sec. 2.2: panel 1.0 x 5.1 x 34.1 cm^3 (radial x tangential x axial)."""
+    vals = {r.split("=")[0].strip(): float(r.split("=")[1]) for r in read_golden("paper_text_values.txt")}
+    ext = oracle.panel_extent(W.h2rspet("1CL"))
+    assert ext[0] == pytest.approx(vals["h2rspet_panel_tangential_mm"])
+    assert ext[1] == pytest.approx(vals["h2rspet_panel_axial_mm"])
+    assert ext[2] == pytest.approx(vals["h2rspet_depth_mm"])
+
+
+# ---------------------------------------------------------------------------
+# whole-history invariants
+# ---------------------------------------------------------------------------
+def test_energy_conservation_per_history(oracle):
+    """Sum of crystal + passive + phantom deposits + escaped energy == 1022 keV."""
+    r = oracle.simulate(W.config1_scanner(), W.point_source(), W.digitizer(), 20000, seed=1, threads=4,
+                        balance=True)
+    np.testing.assert_allclose(r["balance"], 1022.0, atol=1e-9)
+    c3 = W.config3(2000)
+    r = oracle.simulate(c3["scanner"], c3["source"], c3["digitizer"], 2000, seed=3, phantom=c3["phantom"],
+                        threads=4, balance=True)
+    np.testing.assert_allclose(r["balance"], 1022.0, atol=1e-9)
+    assert r["counters"]["ph_steps"] > 0
+
+
+def test_split_zero_gap_equals_single_layer(oracle):
+    """Two 5 mm layers with no gap between them are the same detector as one
+    10 mm layer: same hits, history by history, only the layer label differs."""
+    one = W.scanner(8, 40.0, [W.layer(8, 8, 1.6, 0.1, 10.0)])
+    two = W.scanner(8, 40.0, [W.layer(8, 8, 1.6, 0.1, 5.0), W.layer(8, 8, 1.6, 0.1, 5.0)])
+    a = oracle.simulate(one, W.point_source((1.0, 2.0, 0.5)), W.digitizer(), 30000, seed=21, threads=4)["hits"]
+    b = oracle.simulate(two, W.point_source((1.0, 2.0, 0.5)), W.digitizer(), 30000, seed=21, threads=4)["hits"]
+    assert len(a) == len(b) and len(a) > 1000
+    for f in ("h", "gamma", "step", "panel", "module", "w", "u", "v", "edep", "t_ps"):
+        assert np.array_equal(a[f], b[f]), f
+    assert np.array_equal(b["layer"], (b["w"] >= 5.0).astype(np.int32))
+    # crystal index inside its layer is unchanged
+    ca = a["crystal"] % 64
+    cb = (b["crystal"] % 128) % 64
+    assert np.array_equal(ca, cb)
+
+
+def test_blur_width_and_normals(oracle):
+    """Box-Muller normals of the digitizer are N(0,1) (KS test); the photopeak
+    blur has sigma = 0.15 * 511 / 2.3548."""
+    h = np.arange(200_000, dtype=np.uint64)
+    unit = (np.arange(200_000) % 97).astype(np.int32)
+    z = oracle.blur_normals(5, h, unit)
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    r = oracle.simulate(W.config1_scanner(), W.point_source(), W.digitizer(e_lo=0, e_hi=2000), 100000, seed=1,
+                        threads=8)
+    s = r["singles"]
+    pk = s[s["e_raw"] == 511.0]
+    sig = 0.15 * 511.0 / (2 * math.sqrt(2 * math.log(2)))
+    dev = pk["e_blur"] - 511.0
+    assert abs(dev.std() / sig - 1) < 4 / math.sqrt(2 * len(dev))
+    assert abs(dev.mean()) < 4 * sig / math.sqrt(len(dev))
+
+
+def brute_force_coincidences(t, panel, window_ps):
+    """O(n^2) restatement of the window policy: repeatedly take the earliest
+    unconsumed single, collect every unconsumed single within the window."""
+    n = len(t)
+    consumed = np.zeros(n, bool)
+    pairs = set()
+    order_key = sorted(range(n), key=lambda i: (t[i], i))
+    while not consumed.all():
+        i0 = next(i for i in order_key if not consumed[i])
+        members = [j for j in range(n) if not consumed[j] and t[i0] <= t[j] <= t[i0] + window_ps]
+        for j in members:
+            consumed[j] = True
+        if len(members) == 2 and panel[members[0]] != panel[members[1]]:
+            pairs.add(frozenset(members))
+    return pairs
+
+
+def test_coincidence_policy_brute_force(oracle):
+    """Window sorter vs O(n^2) brute force on clustered random singles
+    (includes ties, multiples, same-panel pairs and isolated singles)."""
+    rng = np.random.default_rng(12)
+    for trial in range(20):
+        n = int(rng.integers(1, 300))
+        base = np.sort(rng.integers(0, 40_000, size=n // 2 + 1))
+        t = np.concatenate([base, base[: n - len(base)] + rng.integers(0, 3000, size=n - len(base))])[:n]
+        t = t.astype(np.uint64)
+        panel = rng.integers(0, 4, n).astype(np.int32)
+        unit = (panel * 100 + rng.integers(0, 3, n)).astype(np.int32)
+        h = rng.permutation(n).astype(np.uint64)
+        s = np.zeros(n, dtype=[("t_ps", "<u8"), ("unit", "<i4"), ("panel", "<i4"), ("h", "<u8")])
+        s["t_ps"], s["unit"], s["panel"], s["h"] = t, unit, panel, h
+        _, a, b = oracle.coincidences(s, 2.0)
+        got = {frozenset((int(x), int(y))) for x, y in zip(a, b)}
+        assert got == brute_force_coincidences(t, panel, 2000), trial
+
+
+def test_split_and_offset_relations_h2rspet(oracle):
+    """Context check on the paper's Table 1 relations, centred point source on
+    reduced H2RSPET rings: split == 1CL within Poisson error; 2CL lower."""
+    rows = {r.split("=")[0].strip(): float(r.split("=")[1]) for r in read_golden("paper_text_values.txt")}
+    assert rows["hits_split"] / rows["hits_1cl"] == pytest.approx(1.0005, abs=5e-4)
+    n = 60000
+    hits = {}
+    for kind in ("1CL", "split", "2CL"):
+        sc = W.h2rspet(kind, modules_v=2)
+        r = oracle.simulate(sc, W.point_source(), W.digitizer(), n, seed=31, threads=8, tallies=False)
+        hits[kind] = len(r["hits"])
+    assert abs(hits["split"] - hits["1CL"]) < 4 * math.sqrt(hits["1CL"])
+    assert hits["2CL"] < hits["1CL"]
+
+
+def test_hit_time_is_path_over_c(oracle):
+    """Back-to-back pencil pair onto two facing slabs at the same radius: the
+    hit-time difference of the first hits is (w0 - w1) / c to within the 1 ps
+    rounding of each time stamp."""
+    mats = [W.AIR, dict(mu_total_511_cm=2.0, photo_frac_511=1.0, electron_density_cm3=0.0)]
+    sc = W.scanner(2, 100.0, [W.layer(1, 1, 400.0, 0.0, 20.0)], materials=mats)
+    r = oracle.simulate(sc, W.pencil_source(direction=(1, 0, 0)), W.digitizer(), 20000, seed=3, threads=4)
+    h = r["hits"]
+    a, b = h[h["gamma"] == 0], h[h["gamma"] == 1]
+    common = np.intersect1d(a["h"], b["h"])
+    a = a[np.isin(a["h"], common)]
+    b = b[np.isin(b["h"], common)]
+    assert len(common) > 5000
+    dt = a["t_ps"].astype(np.int64) - b["t_ps"].astype(np.int64)
+    want = (a["w"] - b["w"]) / 0.299792458
+    assert np.all(np.abs(dt - want) <= 1.0 + 1e-9)
+    # decay times are uniform on [0, n / A)
+    t0 = np.minimum(a["t_ps"], b["t_ps"]).astype(np.float64)
+    span = r["t_span_ps"]
+    assert span == round(20000 / W.DEFAULT_ACTIVITY_BQ * 1e12)
+    assert stats.kstest(t0 / span, "uniform").pvalue > 1e-3
+
+
+def test_digitizer_singles_invariants(oracle):
+    """Singles are per (history, readout unit): one single per distinct unit,
+    energy sum of its hits, earliest hit time; the blur has sigma proportional
+    to sqrt(E) (FWHM 15 % at 511 keV) at every energy."""
+    for level in (W.READOUT_CRYSTAL, W.READOUT_MODULE, W.READOUT_PANEL):
+        sc = W.h2rspet("2CL", modules_v=2)
+        sc["readout_level"] = level
+        r = oracle.simulate(sc, W.point_source((3.0, 1.0, 20.0)), W.digitizer(), 20000, seed=8, threads=4)
+        hits, s = r["hits"], r["singles"]
+        cpm = 51 * 51 + 50 * 50
+        if level == W.READOUT_CRYSTAL:
+            unit = hits["crystal"]
+        elif level == W.READOUT_MODULE:
+            unit = hits["crystal"] // cpm
+        else:
+            unit = hits["panel"]
+        key_h = hits["h"].astype(np.int64) * 10_000_000 + unit
+        uk, inv = np.unique(key_h, return_inverse=True)
+        esum = np.bincount(inv, weights=hits["edep"])
+        tmin = np.full(len(uk), np.iinfo(np.int64).max)
+        np.minimum.at(tmin, inv, hits["t_ps"].astype(np.int64))
+        key_s = s["h"].astype(np.int64) * 10_000_000 + s["unit"]
+        assert len(key_s) == len(uk) and len(np.unique(key_s)) == len(key_s)
+        order = np.argsort(key_s)
+        assert np.array_equal(key_s[order], uk)
+        np.testing.assert_allclose(s["e_raw"][order], esum, rtol=1e-12)
+        assert np.array_equal(s["t_ps"][order].astype(np.int64), tmin)
+    sig_k = 0.15 / (2 * math.sqrt(2 * math.log(2)))
+    z = (s["e_blur"] - s["e_raw"]) / (sig_k * np.sqrt(511.0 * s["e_raw"]))
+    low = s["e_raw"] < 400
+    assert low.sum() > 1000
+    assert stats.kstest(z[low], "norm").pvalue > 1e-3
+
+
+def test_module_gap_is_interval(oracle):
+    """H2RSPET panel: six modules along the axis separated by 7 mm gaps."""
+    sc = W.h2rspet("1CL")
+    V = 6 * 51 + 5 * 7
+    pts = [(5.0, 0.25, -V / 2 + 51 + 3.5), (5.0, 0.25, -V / 2 + 2 * (51 + 7) + 0.5), (5.0, 0.25, -V / 2 + 51 - 0.5)]
+    got = oracle.locate(sc, 0, pts)
+    assert got[0, 2] == -1 and got[0, 3] == 0
+    assert got[1, 1] == 2 and got[1, 2] >= 0            # first crystal row of module 2
+    assert got[2, 1] == 0 and got[2, 2] >= 0            # last crystal of module 0
+    rng = np.random.default_rng(2)
+    n = 400_000
+    p = np.stack([rng.uniform(0, 10, n), rng.uniform(-25.5, 25.5, n), rng.uniform(-V / 2, V / 2, n)], 1)
+    frac = (oracle.locate(sc, 0, p)[:, 2] >= 0).mean()
+    want = 6 * 51 * 51 * 0.92 ** 2 / (51 * V)
+    assert abs(frac - want) < 4 * math.sqrt(want * (1 - want) / n)
+
+
+def box_chord_pairs(lo, hi, n, rng):
+    """Independent quadrature: mean of exp(-mu * chord) over uniform points in a
+    box and isotropic lines through them (chord = exit distance both ways)."""
+    x = rng.uniform(lo, hi, size=(n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+
+    def exit_dist(x, d):
+        t = np.full(len(x), np.inf)
+        for a in range(3):
+            with np.errstate(divide="ignore", invalid="ignore"):
+                tp = np.where(d[:, a] > 0, (hi[a] - x[:, a]) / d[:, a], np.inf)
+                tn = np.where(d[:, a] < 0, (lo[a] - x[:, a]) / d[:, a], np.inf)
+            t = np.minimum(t, np.minimum(tp, tn))
+        return t
+    return exit_dist(x, d) + exit_dist(x, -d)
+
+
+def test_phantom_no_scatter_fraction(oracle):
+    """Uniform water box with uniform activity: the fraction of pairs with no
+    real phantom interaction == E[exp(-mu (L1 + L2))] over points and lines
+    (numpy quadrature, independent of the oracle)."""
+    nx, ny, nz, vs = 20, 16, 12, 1.5
+    origin = (-15.0, -12.0, -9.0)
+    ph = dict(nx=nx, ny=ny, nz=nz, voxel=(vs, vs, vs), origin=origin,
+              material=np.ones((nz, ny, nx), np.uint8), activity=np.ones((nz, ny, nx), np.float32),
+              materials=[W.AIR, W.WATER])
+    n = 100_000
+    r = oracle.simulate(W.config1_scanner(), W.phantom_source(), W.digitizer(), n, seed=4, phantom=ph, threads=8,
+                        phantom_real=True, balance=True)
+    p_obs = (r["phantom_real"] == 0).mean()
+    lo = np.array(origin)
+    hi = lo + vs * np.array([nx, ny, nz])
+    chord = box_chord_pairs(lo, hi, 2_000_000, np.random.default_rng(1))
+    p_exp = np.exp(-0.0096 * chord).mean()
+    assert abs(p_obs - p_exp) < 4 * math.sqrt(p_exp * (1 - p_exp) / n) + 3e-4, (p_obs, p_exp)
+    np.testing.assert_allclose(r["balance"], 1022.0, atol=1e-9)
+
+
+def test_decay_sampling_follows_activity(oracle):
+    """Decay points: voxel counts follow the activity map (chi-square), the
+    point is uniform inside its voxel, directions are isotropic, times uniform."""
+    rng = np.random.default_rng(17)
+    nx, ny, nz, vs = 6, 5, 4, 2.0
+    act = rng.uniform(0, 1, size=(nz, ny, nx)).astype(np.float32)
+    act[act < 0.25] = 0.0          # some empty voxels, including possibly the first
+    act[0, 0, 0] = 0.0
+    ph = dict(nx=nx, ny=ny, nz=nz, voxel=(vs, vs, vs), origin=(-6.0, -5.0, -4.0),
+              material=np.ones((nz, ny, nx), np.uint8), activity=act, materials=[W.AIR, W.WATER])
+    n = 300_000
+    t, pos, d = oracle.decays(W.phantom_source(), n, 9, 0, n, phantom=ph)
+    idx = np.floor((pos - np.array(ph["origin"])) / vs).astype(int)
+    flat = (idx[:, 2] * ny + idx[:, 1]) * nx + idx[:, 0]
+    cnt = np.bincount(flat, minlength=nx * ny * nz)
+    p = act.reshape(-1).astype(np.float64) / act.sum()
+    assert cnt[p == 0].sum() == 0
+    m = p > 0
+    chi2 = ((cnt[m] - n * p[m]) ** 2 / (n * p[m])).sum()
+    assert stats.chi2.sf(chi2, m.sum() - 1) > 1e-3
+    frac = (pos - np.array(ph["origin"])) / vs - idx
+    assert stats.kstest(frac[:, 0], "uniform").pvalue > 1e-3
+    assert stats.kstest(frac[:, 2], "uniform").pvalue > 1e-3
+    # isotropy: cos(theta) uniform on [-1, 1], azimuth uniform
+    assert stats.kstest((d[:, 2] + 1) / 2, "uniform").pvalue > 1e-3
+    az = (np.arctan2(d[:, 1], d[:, 0]) / (2 * math.pi)) % 1.0
+    assert stats.kstest(az, "uniform").pvalue > 1e-3
+    np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-12)
+
+
+def test_energy_conservation_high_cutoff(oracle):
+    """With a 300 keV cutoff many Compton scatters end below it and the photon's
+    remaining energy is deposited on the spot: every history still sums to
+    1022 keV, and a photon either deposits all 511 keV or carries at least the
+    cutoff energy away."""
+    mats = [W.AIR, dict(mu_total_511_cm=0.9, photo_frac_511=0.0, electron_density_cm3=0.0)]
+    sc = W.scanner(8, 40.0, [W.layer(8, 8, 1.6, 0.1, 10.0)], materials=mats)
+    r = oracle.simulate(sc, W.point_source(), W.digitizer(e_cut=300.0), 20000, seed=2, threads=4, balance=True)
+    np.testing.assert_allclose(r["balance"], 1022.0, atol=1e-9)
+    # a photon that drops below 300 keV deposits everything it had left at once:
+    # the last hit of such a photon is its whole remaining energy, so no photon's
+    # hits sum to less than 511 - (energy carried away by a >= 300 keV photon)
+    h = r["hits"]
+    key = h["h"].astype(np.int64) * 2 + h["gamma"]
+    _, inv = np.unique(key, return_inverse=True)
+    tot = np.bincount(inv, weights=h["edep"])
+    assert np.all((tot > 511.0 - 1e-9) | (tot < 511.0 - 300.0 + 1e-9))
