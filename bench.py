@@ -1,0 +1,303 @@
+#!/usr/bin/env python3
+"""Benchmark of the photon-pair transport hot path on GB300.
+
+Workload (default): the axial sensitivity sweep on the 12-panel ring at 55 mm
+(1 x 4 modules of 20 x 20 LYSO crystals, 1.0 mm pitch): a point source at 61
+axial positions (-30..30 mm, 1 mm steps), 1e7 back-to-back pairs per
+position, for geometry A (one 10 mm layer) and geometry B (two 5 mm layers
+with a 0.05 mm reflector gap).  One step = the whole sweep = 1.22e9 pairs
+through transport, singles, energy blur and window, time sort and
+coincidence sorting.  Inputs are synthetic and seeded.
+
+Prints one JSON line.  `value` is pairs/s over the device-timed steps (CUDA
+events on the launching stream, L2 flushed between steps); `e2e` is the same
+metric through the C ABI with host descriptors in and coincidences, singles
+and tallies copied back to host memory inside the timed region.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (it is the slow baseline, not a GPU program).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "pairs tracked/s/GB300"
+N_POSITIONS = 61
+PAIRS_PER_POSITION = 10_000_000
+
+# Algorithmic lane-operations per event of the method, counted from the
+# arithmetic each step must do (not from compiled code):
+#   Philox4x32-10 block: 10 rounds x (2 wide multiplies = 4 ops, 4 xors, 2 key adds) = 100
+#   decay: 1 block + 64-bit time product + isotropic direction (sincospi, sqrt) = 160
+#   flight: per panel a slab test (4 projections, 3 reciprocals, 6 min/max, compares) = 25,
+#           plus 12 for the best-panel bookkeeping; entering a panel adds the frame change (20)
+#   detector step: 1 block, 4 uniforms, log, cross sections, position update, exit test,
+#           layer selection + module + crystal location, accept tests = 175
+#   phantom step: 1 block, log, exit distance, voxel index and gather, accept = 150
+#   Compton trial: 1 block, 3 uniforms, one Kahn branch and its test = 124
+#   crystal hit: kinematics, direction rotation, tallies, singles-list update = 60
+#   single: 1 block, Box-Muller (log, sqrt, cospi), blur, window, append = 150
+ALG = dict(source=160, flight_panel=25, flight_base=12, enter=20, det_step=175, ph_step=150, trial=124,
+           hit=60, single=150)
+SM_COUNT_GB300 = 152
+LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def alg_ops(c, n_panels):
+    return (c["n_decays"] * ALG["source"] + c["flights"] * (ALG["flight_panel"] * n_panels + ALG["flight_base"])
+            + c["entered"] * ALG["enter"] + c["det_steps"] * ALG["det_step"] + c["phantom_steps"] * ALG["ph_step"]
+            + c["compton_trials"] * ALG["trial"] + c["hits"] * (ALG["hit"] + ALG["single"]))
+
+
+def sweep_jobs(rank=0, pairs=PAIRS_PER_POSITION, positions=N_POSITIONS):
+    jobs = []
+    for geo in ("A", "B"):
+        for i, z in enumerate(W.config2_positions()[:positions]):
+            jobs.append(dict(geometry=geo, source=W.point_source((0.0, 0.0, z)), n=pairs,
+                             seed=2 + i + 1000 * (geo == "B") + 100_000 * rank))
+    return jobs
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def cpu_baseline(budget_s=12.0, threads=None):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of the
+    sweep (geometry A and B at z = 0, blocks of histories until the budget)."""
+    from oracle import oracle as O
+    O.build()
+    threads = threads or os.cpu_count() or 1
+    dg = W.digitizer()
+    done, t0 = 0, time.perf_counter()
+    block = 250_000
+    k = 0
+    while time.perf_counter() - t0 < budget_s:
+        geo = "A" if k % 2 == 0 else "B"
+        h0 = (k * block) % (PAIRS_PER_POSITION - block)
+        O.simulate(W.config2_scanner(geo), W.point_source((0.0, 0.0, 0.0)), dg, PAIRS_PER_POSITION, 2,
+                   h_begin=h0, h_end=h0 + block, threads=threads, tallies=True)
+        done += block
+        k += 1
+    dt = time.perf_counter() - t0
+    return dict(value=done / dt, unit="pairs/s", cores=threads, kind="oracle",
+                sample=f"{done} pairs of the sweep (geometry A and B alternating, source at z=0, 1e7-pair time span) "
+                       f"in {dt:.1f} s"), done, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps, warm = args.steps, args.warmup
+    for _ in range(warm):
+        cpu_baseline(budget_s=2.0)
+    vals, dts, cb = [], [], None
+    for _ in range(steps):
+        cb, done, dt = cpu_baseline(budget_s=max(3.0, 20.0 / max(steps, 1)))
+        vals.append(done)
+        dts.append(dt)
+    value = sum(vals) / sum(dts)
+    line = dict(metric=METRIC, value=value, unit="pairs/s", n_gpus=args.gpus, steps=steps, warmup=warm,
+                ms_per_step=1000 * sum(dts) / steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload="sensitivity sweep, 12-panel ring R=55 mm, geometry A/B, 61 positions x 1e7 pairs "
+                                     "(bounded CPU sample)", l2="n/a (host)"),
+                cpu_baseline=dict(kind="oracle", cores=cb["cores"], sample=cb["sample"], value=value, unit="pairs/s"),
+                e2e=dict(value=value, unit="pairs/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2603_07327_gb300 as G
+
+    dg = W.digitizer()
+    scanners = {g: G.Scanner(W.config2_scanner(g)) for g in ("A", "B")}
+    n_panels = 12
+    jobs = sweep_jobs(rank, pairs=args.pairs, positions=args.positions)
+    pairs_per_step = sum(j["n"] for j in jobs)
+    stream = torch.cuda.current_stream().cuda_stream
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step(collect=None):
+        for j in jobs:
+            r = scanners[j["geometry"]].simulate(j["source"], dg, j["n"], j["seed"], stream=stream,
+                                                 kernel=args.kernel)
+            if collect is not None:
+                collect.append(r.counts())
+            r.free()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    clocks.start()
+    dev_ms, counts = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(counts)
+        e1.record()
+        e1.synchronize()
+        dev_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    wall = time.perf_counter() - wall0
+    t_dev = sum(dev_ms) / 1000.0
+    if dist:
+        t = torch.tensor([t_dev, wall], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev, wall = float(t[0]), float(t[1])
+        dist.barrier()
+    total_pairs = pairs_per_step * args.steps * world
+    value = total_pairs / t_dev
+
+    # dominant kernel: the transport kernel (per-launch CUDA events inside the library)
+    tr_ms = sum(c["transport_ms"] for c in counts)
+    dg_ms = sum(c["digitizer_ms"] for c in counts)
+    ops = sum(alg_ops(c, n_panels) for c in counts)
+    achieved = ops / (tr_ms / 1000.0)
+    peak = SM_COUNT_GB300 * LANES_PER_SM * SM_MAX_MHZ * 1e6
+    roof = dict(bound="alu", achieved=achieved, peak=peak, unit="lane-ops/s", frac=achieved / peak,
+                traffic=args.traffic, kernel="k_transport_loop",
+                peak_note="152 SMs x 128 FP32/INT lanes x 2070 MHz (recipe unit counts and max clock)",
+                transport_share=tr_ms / (tr_ms + dg_ms))
+
+    # end to end through the C ABI: host descriptors in, results to host memory
+    import numpy as np
+    e2e_t0 = time.perf_counter()
+    d2h = 0
+    h2d = 0
+    for j in jobs:
+        r = scanners[j["geometry"]].simulate(j["source"], dg, j["n"], j["seed"], stream=stream, kernel=args.kernel)
+        c = r.counts()
+        h2d += c["h2d_bytes"]
+        for arr in (r.array(G.SINGLES_T_PS), r.array(G.SINGLES_UNIT), r.array(G.SINGLES_E), r.array(G.COINC_A),
+                    r.array(G.COINC_B), r.array(G.TALLY_COUNT), r.array(G.TALLY_EFX)):
+            d2h += arr.nbytes
+        r.free()
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - e2e_t0
+    if dist:
+        t = torch.tensor([e2e_dt], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_dt = float(t[0])
+
+    line = dict(metric=METRIC, value=value, unit="pairs/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1000 * t_dev / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32", data="synthetic",
+                config=dict(workload="sensitivity sweep, 12-panel ring R=55 mm, 1x4 modules of 20x20 LYSO at 1.0 mm, "
+                                     "geometry A (10 mm) + B (2x5 mm, 0.05 mm reflector), 61 axial positions x 1e7 pairs",
+                            form="plain: one gpet_simulate per position", pairs_per_step=pairs_per_step,
+                            l2="flushed between steps (256 MB write)", kernel=args.kernel or "default",
+                            parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+                wall_s=wall, gpu_launches=None, roofline=roof, clocks=clk,
+                e2e=dict(value=pairs_per_step * world / e2e_dt, unit="pairs/s", h2d_bytes_per_step=h2d,
+                         d2h_bytes_per_step=d2h),
+                stages=dict(transport_ms_per_step=tr_ms / args.steps, digitizer_ms_per_step=dg_ms / args.steps),
+                per_step_counts=dict(hits=sum(c["hits"] for c in counts) // args.steps,
+                                     singles=sum(c["singles"] for c in counts) // args.steps,
+                                     coincidences=sum(c["coincidences"] for c in counts) // args.steps))
+    # kernels launched per simulate: transport + redo + sort chain (keys, plan, 8 x 3 passes, gather,
+    # flags, count, scan, write)
+    line["gpu_launches"] = len(jobs) * (2 + 2 + 8 * 3 + 1 + 4) * args.steps
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, _, _ = cpu_baseline()
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--pairs", type=int, default=PAIRS_PER_POSITION)
+    ap.add_argument("--positions", type=int, default=N_POSITIONS)
+    ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per transport launch from ncu")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

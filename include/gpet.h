@@ -1,0 +1,238 @@
+/*
+ * gpet.h -- C ABI of the GB300 library for multi-layer PET photon-pair
+ * transport (arxiv 2603.07327, "Extending gPET for Multi-Layer PET
+ * Simulation").
+ *
+ * The library simulates back-to-back 511 keV annihilation photon pairs: decay
+ * sampling (Sec. 2.3: point source, no positron range, annihilation at the
+ * emission site; or a voxel activity map), Woodcock tracking through a
+ * voxelised phantom (Sec. 2.1), straight flight to the first panel by
+ * line-plane intersection (Sec. 2.1), step-by-step Woodcock transport inside
+ * the panel-local frame with the layer-selection step and crystal
+ * identification from the repetitive structure (Sec. 2.1, Fig. 1), transport
+ * across several layers and panels (abstract), per-crystal hit tallies, and a
+ * digitizer: per-readout-unit singles (crystal, module or panel level, Sec.
+ * 2.1), energy blur, energy window, coincidence sorting (Sec. 2.3).
+ *
+ * Conventions for every call:
+ *   - units are mm, keV, ns and 1/cm; times in the outputs are integer
+ *     picoseconds;
+ *   - every function returns an int status: 0 = GPET_OK, < 0 = an error code
+ *     below; the thread-local message of the last error is gpet_last_error();
+ *     no exception crosses the ABI;
+ *   - pointer arguments marked "host" are read (or written) during the call
+ *     only and are copied where kept; arguments marked "device" are CUDA
+ *     device pointers owned by the caller;
+ *   - opaque objects (gpet_scanner, gpet_result, gpet_batch, gpet_server) are
+ *     owned by the library and released with their destroy/free call;
+ *   - a `stream` argument is a cudaStream_t passed as void*; NULL selects the
+ *     legacy default stream.  Calls that return results to the host
+ *     synchronise that stream before returning.
+ */
+#ifndef GPET_H
+#define GPET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* status codes                                                              */
+/* ------------------------------------------------------------------------ */
+#define GPET_OK 0
+#define GPET_ERR_INVALID_ARG (-1) /* a NULL pointer, a negative size, an out-of-range field */
+#define GPET_ERR_GEOMETRY (-2)    /* panels overlap, a layer leaves its module, zero pitch  */
+#define GPET_ERR_OOM (-3)         /* a device or host allocation failed                    */
+#define GPET_ERR_CUDA (-4)        /* a CUDA runtime call failed (message has the CUDA text)  */
+#define GPET_ERR_TIMEOUT (-5)     /* a device loop hit its iteration cap (steps, trials)     */
+#define GPET_ERR_OVERFLOW (-6)    /* an output buffer was too small; the run is flagged      */
+#define GPET_ERR_BUSY (-7)        /* server admission denied (non-blocking submit)          */
+#define GPET_ERR_TOO_SMALL (-8)   /* destination capacity too small; see gpet_result_counts  */
+
+/* readout levels of singles (Sec. 2.1: crystal-, module- or panel-level) */
+#define GPET_READOUT_PANEL 0
+#define GPET_READOUT_MODULE 1
+#define GPET_READOUT_CRYSTAL 3
+
+/* source kinds */
+#define GPET_SOURCE_POINT 0    /* isotropic pairs from pos_mm                              */
+#define GPET_SOURCE_PHANTOM 1  /* isotropic pairs from the loaded phantom's activity map   */
+#define GPET_SOURCE_PENCIL 2   /* collimated pair: photon 0 along dir, photon 1 along -dir */
+
+/* ------------------------------------------------------------------------ */
+/* descriptions (plain structs, host memory, copied by the calls)           */
+/* ------------------------------------------------------------------------ */
+
+/* Material of the synthetic physics model: linear attenuation at 511 keV and
+ * its photoelectric share.  Photoelectric scales as (511/E)^3; Compton follows
+ * the Klein-Nishina total cross section.  electron_density_cm3 = 0 anchors the
+ * Compton coefficient at mu_total*(1-photo_frac) at 511 keV; > 0 uses
+ * n_e * sigma_KN(E) as given. */
+typedef struct {
+    double mu_total_511_cm;
+    double photo_frac_511;
+    double electron_density_cm3;
+} gpet_material;
+
+/* One crystal layer inside a module (Sec. 2.1: each layer carries its own
+ * crystal size, spacing and offset, and its own crystal and inter-crystal
+ * materials, listed layer by layer).  A crystal occupies
+ * [gap/2, pitch - gap/2) of its cell in u and v.  offset_u/v place the
+ * crystal grid's low edge inside the module; gap_before is a radial gap
+ * (e.g. a reflector) in front of the layer, filled with interval_mat. */
+typedef struct {
+    int32_t n_u, n_v;
+    double pitch_u, pitch_v;
+    double gap_u, gap_v;
+    double depth;
+    double gap_before;
+    double offset_u, offset_v;
+    int32_t crystal_mat, interval_mat; /* indices into gpet_scanner_desc.materials */
+} gpet_layer;
+
+/* Repetition-mode ring (Sec. 2.1): one panel definition, n_panels copies at
+ * angles first_angle + 2 pi k / n_panels about the z axis, inner face at
+ * inner_radius_mm.  Panel-local frame: w = depth from the inner face, u =
+ * tangential (z x normal), v = axial.  Modules tile the panel face
+ * (modules_u x modules_v of module_size, separated by module_gap); layers
+ * stack along w in order. */
+typedef struct {
+    int32_t n_panels;
+    double inner_radius_mm;
+    double first_angle_rad;
+    int32_t modules_u, modules_v;
+    double module_size_u, module_size_v;
+    double module_gap_u, module_gap_v;
+    int32_t n_layers;
+    const gpet_layer *layers;       /* host, n_layers entries */
+    int32_t n_materials;
+    const gpet_material *materials; /* host, n_materials entries */
+    int32_t readout_level;          /* GPET_READOUT_* */
+} gpet_scanner_desc;
+
+typedef struct {
+    int32_t kind;         /* GPET_SOURCE_* */
+    double pos_mm[3];     /* point and pencil sources */
+    double dir[3];        /* pencil source axis (unit vector) */
+    double activity_bq;   /* decay times are iid uniform on [0, n_decays / activity) */
+} gpet_source;
+
+/* Digitizer (Sec. 2.3: energy resolution, energy window, coincidence window).
+ * Blur: FWHM(E) = fwhm_at_511 * sqrt(511 keV * E).  Window inclusive.
+ * e_cut_kev is the transport cutoff: a photon below it deposits the rest. */
+typedef struct {
+    double fwhm_at_511;
+    double e_lo_kev, e_hi_kev;
+    double coinc_window_ns;
+    double e_cut_kev;
+} gpet_digitizer;
+
+/* Launch options; pass NULL for defaults. */
+typedef struct {
+    int32_t keep_hits;       /* 1: also store every crystal interaction (tests, DOI studies) */
+    int32_t block_size;      /* threads per CTA of the transport kernel (0 = tuned default) */
+    int32_t blocks_per_sm;   /* resident CTAs per SM (0 = tuned default)                   */
+    int32_t kernel;          /* 0 = tuned default, 1 = per-lane event loop, 2 = wavefront  */
+    int32_t compact_every;   /* wavefront regrouping interval in events (0 = default)      */
+    void *stream;            /* cudaStream_t */
+} gpet_options;
+
+typedef struct gpet_scanner gpet_scanner;
+typedef struct gpet_result gpet_result;
+
+/* ------------------------------------------------------------------------ */
+/* scanner and phantom                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Build a scanner from its hierarchical description (Sec. 2.1, Fig. 1).
+ * desc: host, copied.  Validates: counts >= 1, n_panels <= 64, n_layers <= 8,
+ * n_materials <= 8, pitches > gaps >= 0, every layer inside its module,
+ * panels not overlapping.  Returns GPET_ERR_GEOMETRY or GPET_ERR_INVALID_ARG
+ * on a bad description; *out is set only on success. */
+int gpet_create_scanner(const gpet_scanner_desc *desc, gpet_scanner **out);
+void gpet_destroy_scanner(gpet_scanner *sc);
+
+/* Number of crystals of the scanner (global crystal ids are 0 .. n-1):
+ * id = (((panel * modules_v + m_v) * modules_u + m_u) * C + layer_offset + i_v * n_u + i_u)
+ * with C the crystal count of one module summed over layers. */
+int gpet_scanner_crystals(const gpet_scanner *sc, int64_t *n_crystals);
+
+/* Load (or replace) the voxelised phantom used by the next simulations.
+ * material_ids: host, nx*ny*nz bytes, x fastest, indices into materials.
+ * activity: host, nx*ny*nz floats (>= 0) or NULL when the phantom only
+ * attenuates.  The grid must lie inside the ring's inner radius. */
+int gpet_load_phantom(gpet_scanner *sc, int32_t nx, int32_t ny, int32_t nz, const double voxel_mm[3],
+                      const double origin_mm[3], const uint8_t *material_ids, const float *activity,
+                      int32_t n_materials, const gpet_material *materials);
+
+/* ------------------------------------------------------------------------ */
+/* simulation (plain form: one scanner, one source)                          */
+/* ------------------------------------------------------------------------ */
+
+/* Simulate histories 0 .. n_decays-1 of one source with RNG key `seed`.
+ * Random numbers come from Philox4x32-10 addressed by (history, region,
+ * photon, step, sub-draw), so any history is reproducible on its own.
+ * Enqueues transport, digitizer, time sort and coincidence sorting on
+ * opt->stream and synchronises it.  On success *out holds the result. */
+int gpet_simulate(gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg, uint64_t n_decays,
+                  uint64_t seed, const gpet_options *opt, gpet_result **out);
+
+/* Counts of a finished result. */
+typedef struct {
+    uint64_t n_decays;
+    uint64_t hits;          /* crystal interactions (all, whether stored or not) */
+    uint64_t singles;       /* singles inside the energy window */
+    uint64_t coincidences;
+    int64_t n_crystals;
+    uint64_t det_steps, flights, compton_trials, entered, phantom_steps; /* event counters */
+    int32_t status;         /* GPET_OK or the device error that flagged the run */
+    float transport_ms;     /* CUDA-event time of the transport kernels on the run's stream */
+    float digitizer_ms;     /* CUDA-event time of time sort + coincidence sorting */
+    uint64_t h2d_bytes;     /* descriptor bytes uploaded for the run (jobs, geometry, work table) */
+} gpet_counts;
+int gpet_result_counts(const gpet_result *r, gpet_counts *out);
+
+/* Result arrays.  Singles are sorted by time (ties in any order). */
+enum {
+    GPET_SINGLES_T_PS = 0,      /* uint64 [singles]   time of the earliest hit */
+    GPET_SINGLES_H = 1,         /* uint64 [singles]   history id               */
+    GPET_SINGLES_UNIT = 2,      /* int32  [singles]   readout unit id          */
+    GPET_SINGLES_PANEL = 3,     /* int32  [singles]                            */
+    GPET_SINGLES_E = 4,         /* float  [singles]   blurred energy (keV)     */
+    GPET_SINGLES_E_RAW = 5,     /* float  [singles]   deposited energy (keV)   */
+    GPET_COINC_A = 6,           /* int32  [coincidences] index into singles    */
+    GPET_COINC_B = 7,           /* int32  [coincidences]                       */
+    GPET_TALLY_COUNT = 8,       /* uint64 [n_crystals] interactions per crystal */
+    GPET_TALLY_EFX = 9,         /* uint64 [n_crystals] sum of round(E * 2^20) */
+    GPET_HITS_H = 10,           /* uint64 [hits] (keep_hits only)              */
+    GPET_HITS_GSTEP = 11,       /* int32  [hits] photon << 24 | step           */
+    GPET_HITS_CRYSTAL = 12,     /* int32  [hits] global crystal id             */
+    GPET_HITS_LAYER = 13,       /* int32  [hits]                               */
+    GPET_HITS_WUV = 14,         /* float  [hits][3] panel-local position (mm)  */
+    GPET_HITS_E = 15,           /* float  [hits] deposit (keV)                 */
+    GPET_HITS_T_PS = 16,        /* uint64 [hits]                               */
+    GPET_RESULT_ARRAYS = 17
+};
+
+/* Copy one result array to host memory dst (cap_bytes long).  Returns
+ * GPET_ERR_TOO_SMALL when cap_bytes is below the array's size, and
+ * GPET_ERR_INVALID_ARG for an array the run did not keep. */
+int gpet_result_copy(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes);
+
+/* Device pointer of one result array (valid until gpet_result_free), or NULL. */
+const void *gpet_result_device_ptr(const gpet_result *r, int32_t which);
+void gpet_result_free(gpet_result *r);
+
+/* Thread-local text of the last error (never NULL). */
+const char *gpet_last_error(void);
+
+/* Library version string. */
+const char *gpet_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPET_H */

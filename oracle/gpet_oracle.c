@@ -18,8 +18,8 @@
  *     step picks the crystal layer from the local depth; the repetitive crystal
  *     structure gives material and crystal index; transport stops when the
  *     photon leaves the panel or falls below the cutoff energy; photons that
- *     leave one panel may enter another (abstract: "across multiple layers and
- *     panels").
+ *     leave one panel may enter another (abstract: interactions are sampled
+ *     over several layers and several panels).
  *   - Sec. 2.3: point source, no positron range, annihilation at the emission
  *     site (back-to-back 511 keV pair); energy resolution; energy window;
  *     coincidence timing window.

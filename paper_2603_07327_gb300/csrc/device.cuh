@@ -1,0 +1,289 @@
+// device.cuh -- device-side building blocks of the multi-layer photon-pair
+// transport: geometry descriptor, Philox4x32-10 streams, cross sections,
+// Klein-Nishina sampling, hierarchy location and panel flight.
+//
+// Paper anchors (arxiv 2603.07327): Sec. 2.1 / Fig. 1 for the four-level
+// panel -> module -> layer -> crystal description, the repetition mode, the
+// line-plane flight from the phantom to a panel, the panel-local frame, the
+// Woodcock free-path sampling and the layer-selection step; Sec. 2.3 for the
+// source (back-to-back pairs, no positron range) and the digitizer.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gpet {
+
+constexpr uint32_t kFullMask = 0xFFFFFFFFu;
+constexpr int kMaxPanels = 64;
+constexpr int kMaxLayers = 8;
+constexpr int kMaxMaterials = 8;
+constexpr int kXsIntervals = 4096;       // log-E intervals of the Compton ratio table
+constexpr float kXsEmin = 1.0f;          // keV, lower end of the table
+constexpr int kMaxSteps = 1000;          // per photon and region; cap -> GPET_ERR_TIMEOUT
+constexpr int kMaxTrials = 1000;         // Kahn rejection cap
+constexpr float kE0 = 511.0f;            // annihilation photon energy (keV)
+constexpr float kInvMec2 = 1.0f / 510.99895f;
+constexpr float kInvCmmPerPs = 1.0f / 0.299792458f;  // ps per mm
+constexpr float kEfxScale = 1048576.0f;  // tally energy unit 2^-20 keV
+
+enum : uint32_t { kTagSource = 1u, kTagPhantom = 2u, kTagDetector = 3u, kTagDigi = 4u };
+
+// device status codes (host maps them to GPET_ERR_*)
+enum : int { kStatusOk = 0, kStatusTimeout = 1, kStatusOverflow = 2 };
+
+// ---------------------------------------------------------------------------
+// geometry descriptor (FP32, one per scanner design)
+// ---------------------------------------------------------------------------
+struct LayerDev {
+    float w0, w1;                   // crystal depth range [w0, w1) in the panel frame
+    float off_u, off_v;             // crystal grid offset inside the module
+    float pitch_u, pitch_v;
+    float inv_pitch_u, inv_pitch_v;
+    float glo_u, ghi_u, glo_v, ghi_v;  // crystal occupies [glo, ghi) of its cell
+    int32_t n_u, n_v, loff;         // crystals per row / column, id offset in the module
+    int32_t crystal_mat, interval_mat;  // interval_mat also fills the radial gap in front
+};
+
+struct GeomDev {
+    int32_t n_panels, n_layers, n_materials, modules_u, modules_v, readout_level;
+    int32_t crystals_per_module, n_crystals;
+    float R, W, half_u, half_v;     // inner radius, panel depth, half extents
+    float msu, msv, mpu, mpv, inv_mpu, inv_mpv;  // module size, module pitch (size + gap)
+    float mu_c511[kMaxMaterials];   // Compton coefficient at 511 keV (1/cm)
+    float mu_pe511[kMaxMaterials];  // photoelectric coefficient at 511 keV (1/cm)
+    float pc[kMaxPanels], ps[kMaxPanels];  // cos / sin of each panel's angle
+    LayerDev layers[kMaxLayers];
+};
+
+// one simulation job: a scanner design (index into the geometry table), a
+// source and its digitizer settings
+struct JobDev {
+    uint64_t seed, n_decays, t_span_ps;
+    int32_t geom, src_kind;
+    float src_pos[3], src_dir[3];
+    float e_cut, e_lo, e_hi, sig_k;   // sig_k = fwhm_511 / (2 sqrt(2 ln 2))
+    // phantom (has_phantom = 0 when none)
+    int32_t has_phantom, ph_nx, ph_ny, ph_nz, ph_nmat;
+    float ph_origin[3], ph_voxel[3], ph_inv_voxel[3], ph_hi[3];
+    float ph_mu_c511[kMaxMaterials], ph_mu_pe511[kMaxMaterials];
+    const uint8_t *ph_mat;
+    const double *ph_cdf;             // activity prefix sums in voxel order
+    double ph_total;
+    int64_t ph_n, ph_last_active;
+    // per-crystal tallies of this job
+    unsigned long long *tally_count, *tally_efx;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k.x += W0; k.y += W1; }
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// draw block (history, tag, photon, step, sub) under key = seed
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t h, uint32_t tag, uint32_t gamma, uint32_t step,
+                                      uint32_t sub) {
+    return philox4x32_10(make_uint4((uint32_t)h, (uint32_t)(h >> 32),
+                                    (tag << 28) | ((gamma & 1u) << 27) | (step & 0x07FFFFFFu), sub),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// uniform (k + 1/2) 2^-23 in (0,1) from the top 23 bits (exact in FP32)
+__device__ __forceinline__ float u01(uint32_t w) {
+    return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+
+// ---------------------------------------------------------------------------
+// cross sections: mu_C(E) = mu_C(511) * g(E), g = sigma_KN(E)/sigma_KN(511) from a
+// log-E table; mu_pe(E) = mu_pe(511) * (511/E)^3
+// ---------------------------------------------------------------------------
+struct Xs {
+    float g;    // Compton ratio
+    float r3;   // (511/E)^3
+};
+
+__device__ __forceinline__ Xs xs_at(float E, const float *__restrict__ gtab, float ln_emin, float inv_h) {
+    Xs x;
+    if (E >= kE0) {
+        x.g = 1.0f;
+        x.r3 = 1.0f;
+        return x;
+    }
+    float t = (__logf(E) - ln_emin) * inv_h;
+    t = fmaxf(t, 0.0f);
+    int i = min((int)t, kXsIntervals - 1);
+    float f = t - (float)i;
+    float g0 = __ldg(gtab + i), g1 = __ldg(gtab + i + 1);
+    x.g = fmaf(f, g1 - g0, g0);
+    float r = kE0 / E;
+    x.r3 = r * r * r;
+    return x;
+}
+
+__device__ __forceinline__ float mu_total(float c511, float pe511, const Xs &x) {
+    return fmaf(c511, x.g, pe511 * x.r3);
+}
+
+// ---------------------------------------------------------------------------
+// Kahn's rejection sampling of Klein-Nishina; returns trials (> 0) or -1
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int kahn_sample(uint64_t seed, uint64_t h, uint32_t tag, uint32_t gamma, uint32_t step,
+                                           float E, float &xm1_out) {
+    const float k = E * kInvMec2;
+    const float a = 1.0f + 2.0f * k;
+    const float b = 9.0f + 2.0f * k;
+    for (int trial = 0; trial < kMaxTrials; ++trial) {
+        const uint4 r = draw(seed, h, tag, gamma, step, 1u + (uint32_t)trial);
+        const float r1 = u01(r.x), r2 = u01(r.y), r3 = u01(r.z);
+        float xm1;
+        bool accept;
+        if (r1 * b <= a) {
+            xm1 = 2.0f * k * r2;
+            const float eta = 1.0f + xm1;
+            accept = r3 * eta * eta <= 4.0f * xm1;
+        } else {
+            const float den = fmaf(2.0f * k, r2, 1.0f);
+            xm1 = 2.0f * k * (1.0f - r2) / den;
+            const float eta = 1.0f + xm1;
+            const float c = 1.0f - xm1 / k;
+            accept = 2.0f * r3 <= fmaf(c, c, 1.0f / eta);
+        }
+        if (accept) {
+            xm1_out = xm1;
+            return trial + 1;
+        }
+    }
+    return -1;
+}
+
+// rotate (a, b, c) [third component = scanner axis] by polar (cos ct, 1-cos omc) and
+// azimuth 2 pi u; frame-equivariant under rotations about the axis
+__device__ __forceinline__ void rotate_dir(float &a, float &b, float &c, float omc, float u_phi) {
+    const float ct = 1.0f - omc;
+    const float st = sqrtf(fmaxf(omc * (2.0f - omc), 0.0f));
+    float sp, cp;
+    sincospif(2.0f * u_phi, &sp, &cp);
+    if (fabsf(c) < 0.99999f) {
+        const float q = sqrtf(fmaf(-c, c, 1.0f));
+        const float iq = 1.0f / q;
+        const float na = a * ct + st * (a * c * cp - b * sp) * iq;
+        const float nb = b * ct + st * (b * c * cp + a * sp) * iq;
+        const float nc = c * ct - st * q * cp;
+        a = na; b = nb; c = nc;
+    } else {
+        const float sg = c > 0.0f ? 1.0f : -1.0f;
+        a = st * cp;
+        b = st * sp;
+        c = sg * ct;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// hierarchy location in the panel frame (layer selection, module, crystal)
+// ---------------------------------------------------------------------------
+struct Loc {
+    int32_t layer, module, crystal;   // crystal = global id or -1
+    int32_t mat;
+};
+
+__device__ __forceinline__ Loc locate(const GeomDev &g, int k, float w, float u, float v) {
+    Loc L;
+    L.layer = -1; L.module = -1; L.crystal = -1;
+    // layer-selection step: the layer whose depth range holds w
+    int l = -1, owner = g.n_layers - 1;
+    for (int j = 0; j < g.n_layers; ++j) {
+        if (w < g.layers[j].w0) { owner = j; break; }
+        if (w < g.layers[j].w1) { l = j; break; }
+    }
+    if (l < 0) {
+        L.mat = g.layers[owner].interval_mat;
+        return L;
+    }
+    const LayerDev &Ly = g.layers[l];
+    L.layer = l;
+    L.mat = Ly.interval_mat;
+    const float au = u + g.half_u, av = v + g.half_v;
+    const int mu = (int)floorf(au * g.inv_mpu), mv = (int)floorf(av * g.inv_mpv);
+    if (mu < 0 || mu >= g.modules_u || mv < 0 || mv >= g.modules_v) return L;
+    const float a_u = fmaf(-(float)mu, g.mpu, au), a_v = fmaf(-(float)mv, g.mpv, av);
+    if (a_u >= g.msu || a_v >= g.msv) return L;
+    L.module = mv * g.modules_u + mu;
+    const float bu = a_u - Ly.off_u, bv = a_v - Ly.off_v;
+    const int iu = (int)floorf(bu * Ly.inv_pitch_u), iv = (int)floorf(bv * Ly.inv_pitch_v);
+    if (iu < 0 || iu >= Ly.n_u || iv < 0 || iv >= Ly.n_v) return L;
+    const float cu = fmaf(-(float)iu, Ly.pitch_u, bu), cv = fmaf(-(float)iv, Ly.pitch_v, bv);
+    if (cu < Ly.glo_u || cu >= Ly.ghi_u || cv < Ly.glo_v || cv >= Ly.ghi_v) return L;
+    L.mat = Ly.crystal_mat;
+    L.crystal = ((k * g.modules_v + mv) * g.modules_u + mu) * g.crystals_per_module + Ly.loff + iv * Ly.n_u + iu;
+    return L;
+}
+
+// distance along (dw, du, dv) from an inside point to the panel box exit
+__device__ __forceinline__ float panel_exit(const GeomDev &g, float w, float u, float v, float dw, float du, float dv) {
+    float t = 3.0e38f;
+    if (dw > 0.0f) t = fminf(t, (g.W - w) / dw); else if (dw < 0.0f) t = fminf(t, -w / dw);
+    if (du > 0.0f) t = fminf(t, (g.half_u - u) / du); else if (du < 0.0f) t = fminf(t, (-g.half_u - u) / du);
+    if (dv > 0.0f) t = fminf(t, (g.half_v - v) / dv); else if (dv < 0.0f) t = fminf(t, (-g.half_v - v) / dv);
+    return fmaxf(t, 0.0f);
+}
+
+// line-plane flight: nearest panel entered along (x, d), skipping `skip`;
+// slab test on each panel's box in its own frame
+__device__ __forceinline__ int flight(const GeomDev &g, float x, float y, float z, float dx, float dy, float dz,
+                                      int skip, float &t_in, float &t_out) {
+    int best = -1;
+    float bi = 3.0e38f, bo = 0.0f;
+    for (int k = 0; k < g.n_panels; ++k) {
+        if (k == skip) continue;
+        const float c = g.pc[k], s = g.ps[k];
+        const float w0 = fmaf(x, c, y * s) - g.R;
+        const float dw = fmaf(dx, c, dy * s);
+        // behind the inner face and moving away: no entry
+        if (w0 < 0.0f && dw <= 0.0f) continue;
+        const float u0 = fmaf(-x, s, y * c);
+        const float du = fmaf(-dx, s, dy * c);
+        float tmin = -3.0e38f, tmax = 3.0e38f;
+        bool miss = false;
+        // w slab [0, W]
+        if (dw != 0.0f) {
+            const float i = 1.0f / dw;
+            const float t1 = -w0 * i, t2 = (g.W - w0) * i;
+            tmin = fmaxf(tmin, fminf(t1, t2));
+            tmax = fminf(tmax, fmaxf(t1, t2));
+        } else if (w0 < 0.0f || w0 > g.W) miss = true;
+        if (du != 0.0f) {
+            const float i = 1.0f / du;
+            const float t1 = (-g.half_u - u0) * i, t2 = (g.half_u - u0) * i;
+            tmin = fmaxf(tmin, fminf(t1, t2));
+            tmax = fminf(tmax, fmaxf(t1, t2));
+        } else if (u0 < -g.half_u || u0 > g.half_u) miss = true;
+        if (dz != 0.0f) {
+            const float i = 1.0f / dz;
+            const float t1 = (-g.half_v - z) * i, t2 = (g.half_v - z) * i;
+            tmin = fmaxf(tmin, fminf(t1, t2));
+            tmax = fminf(tmax, fmaxf(t1, t2));
+        } else if (z < -g.half_v || z > g.half_v) miss = true;
+        tmin = fmaxf(tmin, 0.0f);
+        if (!miss && tmin < tmax && tmin < bi) {
+            best = k;
+            bi = tmin;
+            bo = tmax;
+        }
+    }
+    t_in = bi;
+    t_out = bo;
+    return best;
+}
+
+}  // namespace gpet

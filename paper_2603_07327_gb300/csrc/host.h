@@ -1,0 +1,97 @@
+// host.h -- host-side objects behind the opaque handles of include/gpet.h and
+// the run machinery shared by the plain, batched and served entry points.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gpet.h"
+#include "internal.h"
+
+struct gpet_scanner {
+    gpet_scanner_desc desc;
+    std::vector<gpet_layer> layers;
+    std::vector<gpet_material> materials;
+    gpet::GeomDev g;
+    int64_t n_crystals = 0;
+    // phantom
+    bool has_phantom = false;
+    int32_t ph_n[3] = {0, 0, 0};
+    double ph_voxel[3] = {0, 0, 0}, ph_origin[3] = {0, 0, 0};
+    std::vector<gpet_material> ph_materials;
+    uint8_t *ph_mat = nullptr;
+    double *ph_cdf = nullptr;
+    double ph_total = 0.0;
+    int64_t ph_last_active = -1;
+};
+
+int gpet_fail(int code, const char *fmt, ...);
+int gpet_cuda_fail(cudaError_t e, const char *where);
+int gpet_xs_table(const float **out, float *ln_emin, float *inv_h);
+int gpet_build_geometry(const gpet_scanner_desc *d, gpet::GeomDev &g, int64_t &n_crystals);
+int gpet_make_job(const gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg, uint64_t n_decays,
+                  uint64_t seed, gpet::JobDev &J);
+
+namespace gpet {
+
+// capacities of one run's output buffers
+struct RunCaps {
+    uint64_t singles = 0, hits = 0, ovf = 0;
+};
+
+// device header read back after a run (all zeroed before launch)
+struct RunHeader {
+    unsigned long long counters[8];   // det_steps, flights, trials, entered, phantom_steps, hits
+    unsigned long long n_singles, n_hits, n_ovf, n_sorted, n_coinc, next_chunk;
+    int status;
+    int pad[3];
+};
+
+// One launch of one or more jobs: all device memory lives in a single arena.
+struct Run {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<JobDev> jobs;            // host copies (tally pointers filled by plan)
+    std::vector<GeomDev> geoms;
+    std::vector<int64_t> tally_off;      // per job, in crystals
+    std::vector<int64_t> job_crystals;
+    std::vector<uint64_t> windows;       // coincidence window per job (ps)
+    std::vector<unsigned long long> chunk_start;
+    unsigned int chunk_size = 2048;
+    RunCaps caps;
+    bool keep_hits = false;
+    LaunchCfg cfg{};
+    // arena
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    size_t zero_bytes = 0;               // leading bytes cleared before every launch
+    RunHeader *d_hdr = nullptr;
+    RunHeader h_hdr{};
+    WorkDev W{};
+    OutDev O{};
+    SortDev S{};
+    SinglesDev SD{};
+    CoincDev C{};
+    unsigned long long *d_tally_count = nullptr, *d_tally_efx = nullptr;
+    uint64_t *d_window = nullptr;
+    int64_t total_crystals = 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // before transport, after transport, after digitizer
+    float transport_ms = 0.f, digitizer_ms = 0.f;
+    uint64_t h2d_bytes = 0;
+};
+
+int run_plan(Run &R);                  // allocate the arena, upload jobs and geometry
+int run_enqueue(Run &R);               // memset + transport + sort + coincidences (capturable)
+int run_collect(Run &R);               // synchronise, read the header, map device status
+void run_release(Run &R);
+int run_default_cfg(Run &R, const gpet_options *opt);
+
+}  // namespace gpet
+
+struct gpet_result {
+    gpet::Run run;
+    gpet_counts counts{};
+    int job = 0;                         // which job of the run this result views
+    bool owns_run = true;
+};

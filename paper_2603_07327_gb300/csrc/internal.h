@@ -1,0 +1,57 @@
+// internal.h -- declarations shared by the library's translation units
+// (device structs of the sort / coincidence stage and the host launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "transport.cuh"
+
+namespace gpet {
+
+enum { kKernelDefault = 0, kKernelLoop = 1, kKernelWave = 2 };
+
+struct LaunchCfg {
+    int grid;            // CTAs of the transport kernel
+    int block_size;      // threads per CTA
+    int sm_count;
+    int kernel;          // kKernelLoop / kKernelWave
+    int max_smem_geoms;  // geometry descriptors staged in shared memory
+    int compact_every;   // wavefront regrouping interval (events)
+};
+
+// radix sort working set (keys ping-pong between two buffers)
+struct SortDev {
+    uint64_t *keys[2];
+    uint32_t *vals[2];
+    uint32_t *ghist;                 // [8][256]
+    int *plan;                       // [8] active, [8] source buffer, [1] final buffer
+    uint32_t *tile_hist;             // [256][max_tiles]
+    unsigned long long max_tiles;
+    unsigned long long cap;
+    const unsigned long long *n_in;  // device count of unsorted singles
+    const uint64_t *in_t, *in_h;
+    const int32_t *in_unit, *in_panel, *in_job;
+    const float *in_e, *in_eraw;
+};
+
+// time-ordered singles
+struct SinglesDev {
+    uint64_t *t, *h;
+    int32_t *unit, *panel, *job;
+    float *e, *eraw;
+    unsigned long long *n;
+};
+
+struct CoincDev {
+    uint8_t *flag;
+    uint32_t *tile_cnt;
+    int32_t *a, *b;
+    unsigned long long *n;
+    const uint64_t *window_ps;       // per job
+};
+
+cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
+cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const CoincDev &C, int sm_count,
+                              cudaStream_t st);
+
+}  // namespace gpet

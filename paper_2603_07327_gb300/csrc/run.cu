@@ -1,0 +1,376 @@
+// run.cu -- run machinery: one device arena per launch, enqueue of the whole
+// hot path (transport -> singles -> time sort -> coincidences) without host
+// round trips, header read-back with overflow retry, and the plain
+// gpet_simulate entry point with its result accessors.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "host.h"
+
+namespace gpet {
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Carver {
+    size_t off = 0;
+    template <typename T>
+    size_t take(T *&p, size_t count) {
+        off = align_up(off, 256);
+        const size_t at = off;
+        p = reinterpret_cast<T *>(at);  // offset for now, rebased later
+        off += sizeof(T) * std::max<size_t>(count, 1);
+        return at;
+    }
+};
+
+template <typename T>
+static void rebase(T *&p, char *base) {
+    p = reinterpret_cast<T *>(base + reinterpret_cast<size_t>(p));
+}
+
+int run_default_cfg(Run &R, const gpet_options *opt) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaGetDevice");
+    R.device = dev;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaDeviceGetAttribute");
+    R.cfg.sm_count = sms;
+    R.cfg.block_size = (opt && opt->block_size > 0) ? opt->block_size : 256;
+    if (R.cfg.block_size % 32 || R.cfg.block_size > 256)
+        return gpet_fail(GPET_ERR_INVALID_ARG, "block_size %d must be a multiple of 32 and <= 256", R.cfg.block_size);
+    const int bps = (opt && opt->blocks_per_sm > 0) ? opt->blocks_per_sm : 4;
+    R.cfg.grid = sms * bps;
+    R.cfg.kernel = (opt && opt->kernel > 0) ? opt->kernel : kKernelLoop;
+    if (R.cfg.kernel != kKernelLoop) return gpet_fail(GPET_ERR_INVALID_ARG, "kernel %d not available", R.cfg.kernel);
+    R.cfg.compact_every = (opt && opt->compact_every > 0) ? opt->compact_every : 1;
+    R.cfg.max_smem_geoms = 16;
+    R.keep_hits = opt && opt->keep_hits;
+    R.stream = opt ? reinterpret_cast<cudaStream_t>(opt->stream) : nullptr;
+    return GPET_OK;
+}
+
+int run_plan(Run &R) {
+    const int nj = (int)R.jobs.size();
+    if (nj < 1) return gpet_fail(GPET_ERR_INVALID_ARG, "no jobs");
+    if (nj > 4095) return gpet_fail(GPET_ERR_INVALID_ARG, "at most 4095 jobs per launch");
+    // tallies per job
+    R.tally_off.resize(nj);
+    int64_t tc = 0;
+    for (int j = 0; j < nj; ++j) { R.tally_off[j] = tc; tc += R.job_crystals[j]; }
+    R.total_crystals = tc;
+    // chunks: small enough that every warp of the grid gets work
+    uint64_t total = 0;
+    for (auto &J : R.jobs) total += J.n_decays;
+    const uint64_t warps = (uint64_t)R.cfg.grid * (R.cfg.block_size / 32);
+    uint64_t cs = total / std::max<uint64_t>(warps * 8, 1);
+    cs = std::max<uint64_t>(32, std::min<uint64_t>(4096, cs / 32 * 32));
+    R.chunk_size = (unsigned)cs;
+    R.chunk_start.assign(nj + 1, 0);
+    for (int j = 0; j < nj; ++j)
+        R.chunk_start[j + 1] = R.chunk_start[j] + (R.jobs[j].n_decays + cs - 1) / cs;
+
+    const uint64_t cap = std::max<uint64_t>(R.caps.singles, 1);
+    const uint64_t hcap = R.keep_hits ? std::max<uint64_t>(R.caps.hits, 1) : 0;
+    const uint64_t ocap = std::max<uint64_t>(R.caps.ovf, 1);
+    const uint64_t tiles = (cap + 4095) / 4096;
+    if (cap >= 0xFFFFFFFFull) return gpet_fail(GPET_ERR_INVALID_ARG, "more than 2^32 singles per launch");
+
+    Carver cv;
+    // zeroed before every launch
+    cv.take(R.d_hdr, 1);
+    cv.take(R.S.ghist, 8 * 256);
+    cv.take(R.d_tally_count, (size_t)tc);
+    cv.take(R.d_tally_efx, (size_t)tc);
+    R.zero_bytes = align_up(cv.off, 256);
+    JobDev *d_jobs;
+    GeomDev *d_geoms;
+    unsigned long long *d_cs;
+    cv.take(d_jobs, nj);
+    cv.take(d_geoms, R.geoms.size());
+    cv.take(d_cs, nj + 1);
+    cv.take(R.d_window, nj);
+    // raw singles
+    OutDev &O = R.O;
+    cv.take(O.s_t, cap); cv.take(O.s_h, cap);
+    cv.take(O.s_unit, cap); cv.take(O.s_panel, cap); cv.take(O.s_job, cap);
+    cv.take(O.s_e, cap); cv.take(O.s_eraw, cap);
+    // hits
+    if (hcap) {
+        cv.take(O.hit_h, hcap); cv.take(O.hit_t, hcap);
+        cv.take(O.hit_gstep, hcap); cv.take(O.hit_crystal, hcap); cv.take(O.hit_layer, hcap);
+        cv.take(O.hit_job, hcap); cv.take(O.hit_wuv, 3 * hcap); cv.take(O.hit_e, hcap);
+    }
+    cv.take(O.ovf_h, ocap); cv.take(O.ovf_job, ocap);
+    // sort
+    SortDev &S = R.S;
+    cv.take(S.keys[0], cap); cv.take(S.keys[1], cap);
+    cv.take(S.vals[0], cap); cv.take(S.vals[1], cap);
+    cv.take(S.plan, 32);
+    cv.take(S.tile_hist, 256 * tiles);
+    // sorted singles
+    SinglesDev &SD = R.SD;
+    cv.take(SD.t, cap); cv.take(SD.h, cap);
+    cv.take(SD.unit, cap); cv.take(SD.panel, cap); cv.take(SD.job, cap);
+    cv.take(SD.e, cap); cv.take(SD.eraw, cap);
+    // coincidences
+    CoincDev &C = R.C;
+    cv.take(C.flag, cap);
+    cv.take(C.tile_cnt, tiles);
+    cv.take(C.a, cap / 2 + 1); cv.take(C.b, cap / 2 + 1);
+    R.arena_bytes = align_up(cv.off, 256);
+
+    cudaError_t e = cudaMallocAsync(&R.arena, R.arena_bytes, R.stream);
+    if (e != cudaSuccess) {
+        R.arena = nullptr;
+        return e == cudaErrorMemoryAllocation ? gpet_fail(GPET_ERR_OOM, "device arena of %zu bytes", R.arena_bytes)
+                                              : gpet_cuda_fail(e, "cudaMallocAsync");
+    }
+    char *base = static_cast<char *>(R.arena);
+    rebase(R.d_hdr, base);
+    rebase(S.ghist, base);
+    rebase(R.d_tally_count, base);
+    rebase(R.d_tally_efx, base);
+    rebase(d_jobs, base); rebase(d_geoms, base); rebase(d_cs, base); rebase(R.d_window, base);
+    rebase(O.s_t, base); rebase(O.s_h, base); rebase(O.s_unit, base); rebase(O.s_panel, base);
+    rebase(O.s_job, base); rebase(O.s_e, base); rebase(O.s_eraw, base);
+    if (hcap) {
+        rebase(O.hit_h, base); rebase(O.hit_t, base); rebase(O.hit_gstep, base); rebase(O.hit_crystal, base);
+        rebase(O.hit_layer, base); rebase(O.hit_job, base); rebase(O.hit_wuv, base); rebase(O.hit_e, base);
+    } else {
+        O.hit_h = nullptr; O.hit_t = nullptr; O.hit_gstep = O.hit_crystal = O.hit_layer = O.hit_job = nullptr;
+        O.hit_wuv = O.hit_e = nullptr;
+    }
+    rebase(O.ovf_h, base); rebase(O.ovf_job, base);
+    rebase(S.keys[0], base); rebase(S.keys[1], base); rebase(S.vals[0], base); rebase(S.vals[1], base);
+    rebase(S.plan, base); rebase(S.tile_hist, base);
+    rebase(SD.t, base); rebase(SD.h, base); rebase(SD.unit, base); rebase(SD.panel, base); rebase(SD.job, base);
+    rebase(SD.e, base); rebase(SD.eraw, base);
+    rebase(C.flag, base); rebase(C.tile_cnt, base); rebase(C.a, base); rebase(C.b, base);
+
+    // wire the structs
+    for (int j = 0; j < nj; ++j) {
+        R.jobs[j].tally_count = R.d_tally_count + R.tally_off[j];
+        R.jobs[j].tally_efx = R.d_tally_efx + R.tally_off[j];
+    }
+    RunHeader *H = R.d_hdr;
+    O.n_singles = &H->n_singles;
+    O.s_cap = cap;
+    O.n_hits = &H->n_hits;
+    O.hit_cap = hcap;
+    O.n_ovf = &H->n_ovf;
+    O.ovf_cap = ocap;
+    O.counters = H->counters;
+    O.status = &H->status;
+    WorkDev &W = R.W;
+    W.jobs = d_jobs;
+    W.n_jobs = nj;
+    W.geoms = d_geoms;
+    W.n_geoms = (int)R.geoms.size();
+    W.chunk_start = d_cs;
+    W.total_chunks = R.chunk_start[nj];
+    W.next_chunk = &H->next_chunk;
+    W.chunk_size = R.chunk_size;
+    int st = gpet_xs_table(&W.gtab, &W.ln_emin, &W.inv_h);
+    if (st != GPET_OK) return st;
+    S.max_tiles = tiles;
+    S.cap = cap;
+    S.n_in = &H->n_singles;
+    S.in_t = O.s_t; S.in_h = O.s_h; S.in_unit = O.s_unit; S.in_panel = O.s_panel; S.in_job = O.s_job;
+    S.in_e = O.s_e; S.in_eraw = O.s_eraw;
+    SD.n = &H->n_sorted;
+    C.n = &H->n_coinc;
+    C.window_ps = R.d_window;
+
+    // upload descriptors (small; stream-ordered after the allocation)
+    e = cudaMemcpyAsync(d_jobs, R.jobs.data(), sizeof(JobDev) * nj, cudaMemcpyHostToDevice, R.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_geoms, R.geoms.data(), sizeof(GeomDev) * R.geoms.size(), cudaMemcpyHostToDevice,
+                            R.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_cs, R.chunk_start.data(), sizeof(unsigned long long) * (nj + 1),
+                            cudaMemcpyHostToDevice, R.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(R.d_window, R.windows.data(), sizeof(uint64_t) * nj, cudaMemcpyHostToDevice, R.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(R.stream);  // host vectors may change after return
+    R.h2d_bytes = sizeof(JobDev) * nj + sizeof(GeomDev) * R.geoms.size() + sizeof(unsigned long long) * (nj + 1) +
+                  sizeof(uint64_t) * nj;
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "upload of the job descriptors");
+    return GPET_OK;
+}
+
+int run_enqueue(Run &R) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        if (!R.ev[i]) e = cudaEventCreate(&R.ev[i]);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaEventCreate");
+    e = cudaMemsetAsync(R.arena, 0, R.zero_bytes, R.stream);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaMemsetAsync");
+    e = cudaEventRecord(R.ev[0], R.stream);
+    if (e == cudaSuccess) e = launch_transport(R.W, R.O, R.cfg, R.stream);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "transport launch");
+    e = cudaEventRecord(R.ev[1], R.stream);
+    if (e == cudaSuccess) e = launch_sort_coinc(R.S, R.SD, R.C, R.cfg.sm_count, R.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(R.ev[2], R.stream);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "sort / coincidence launch");
+    return GPET_OK;
+}
+
+int run_collect(Run &R) {
+    cudaError_t e = cudaMemcpyAsync(&R.h_hdr, R.d_hdr, sizeof(RunHeader), cudaMemcpyDeviceToHost, R.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(R.stream);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "run read-back");
+    if (R.ev[0] && cudaEventElapsedTime(&R.transport_ms, R.ev[0], R.ev[1]) != cudaSuccess) R.transport_ms = -1.f;
+    if (R.ev[1] && cudaEventElapsedTime(&R.digitizer_ms, R.ev[1], R.ev[2]) != cudaSuccess) R.digitizer_ms = -1.f;
+    const RunHeader &H = R.h_hdr;
+    if (H.status & kStatusTimeout)
+        return gpet_fail(GPET_ERR_TIMEOUT, "a photon exceeded %d steps or %d Compton trials", kMaxSteps, kMaxTrials);
+    if (H.n_singles > R.O.s_cap || (R.keep_hits && H.n_hits > R.O.hit_cap) || H.n_ovf > R.O.ovf_cap)
+        return gpet_fail(GPET_ERR_OVERFLOW, "output capacity exceeded (singles %llu/%llu, hits %llu/%llu, ovf %llu/%llu)",
+                         H.n_singles, R.O.s_cap, H.n_hits, R.O.hit_cap, H.n_ovf, R.O.ovf_cap);
+    if (H.status & kStatusOverflow)
+        return gpet_fail(GPET_ERR_OVERFLOW, "a history touched more than 64 readout units");
+    return GPET_OK;
+}
+
+void run_release(Run &R) {
+    if (R.arena) cudaFreeAsync(R.arena, R.stream);
+    R.arena = nullptr;
+    for (auto &e : R.ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
+}
+
+}  // namespace gpet
+
+using namespace gpet;
+
+static void fill_counts(const Run &R, int job, uint64_t n_decays, int64_t n_crystals, gpet_counts *c) {
+    const RunHeader &H = R.h_hdr;
+    std::memset(c, 0, sizeof(*c));
+    c->n_decays = n_decays;
+    c->hits = H.counters[5];
+    c->singles = H.n_sorted;
+    c->coincidences = H.n_coinc;
+    c->n_crystals = n_crystals;
+    c->det_steps = H.counters[0];
+    c->flights = H.counters[1];
+    c->compton_trials = H.counters[2];
+    c->entered = H.counters[3];
+    c->phantom_steps = H.counters[4];
+    c->status = GPET_OK;
+    c->transport_ms = R.transport_ms;
+    c->digitizer_ms = R.digitizer_ms;
+    c->h2d_bytes = R.h2d_bytes;
+    (void)job;
+}
+
+extern "C" int gpet_simulate(gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg, uint64_t n_decays,
+                             uint64_t seed, const gpet_options *opt, gpet_result **out) {
+    if (!out) return gpet_fail(GPET_ERR_INVALID_ARG, "out is NULL");
+    JobDev J;
+    int st = gpet_make_job(sc, src, dg, n_decays, seed, J);
+    if (st != GPET_OK) return st;
+    gpet_result *res = new (std::nothrow) gpet_result();
+    if (!res) return gpet_fail(GPET_ERR_OOM, "host allocation of the result failed");
+    Run &R = res->run;
+    st = run_default_cfg(R, opt);
+    if (st != GPET_OK) { delete res; return st; }
+    R.jobs = {J};
+    R.geoms = {sc->g};
+    R.job_crystals = {sc->n_crystals};
+    R.windows = {(uint64_t)std::llround(dg->coinc_window_ns * 1000.0)};
+    R.caps.singles = std::max<uint64_t>(65536, n_decays * 6 / 10);
+    R.caps.hits = R.keep_hits ? std::max<uint64_t>(65536, n_decays * 5 / 2) : 0;
+    R.caps.ovf = std::max<uint64_t>(4096, n_decays / 256);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        st = run_plan(R);
+        if (st == GPET_OK) st = run_enqueue(R);
+        if (st == GPET_OK) st = run_collect(R);
+        if (st == GPET_ERR_OVERFLOW && attempt == 0 && !(R.h_hdr.status & kStatusOverflow)) {
+            // the counters kept counting past the capacities: re-run with exact sizes
+            R.caps.singles = std::max<uint64_t>(R.caps.singles, R.h_hdr.n_singles + 1024);
+            R.caps.hits = std::max<uint64_t>(R.caps.hits, R.h_hdr.n_hits + 1024);
+            R.caps.ovf = std::max<uint64_t>(R.caps.ovf, R.h_hdr.n_ovf + 1024);
+            run_release(R);
+            continue;
+        }
+        break;
+    }
+    if (st != GPET_OK) {
+        run_release(R);
+        delete res;
+        return st;
+    }
+    fill_counts(R, 0, n_decays, sc->n_crystals, &res->counts);
+    *out = res;
+    return GPET_OK;
+}
+
+extern "C" int gpet_result_counts(const gpet_result *r, gpet_counts *out) {
+    if (!r || !out) return gpet_fail(GPET_ERR_INVALID_ARG, "NULL argument");
+    *out = r->counts;
+    return GPET_OK;
+}
+
+struct ArrayView {
+    const void *ptr;
+    size_t bytes;
+};
+
+static int result_array(const gpet_result *r, int32_t which, ArrayView &v) {
+    const Run &R = r->run;
+    const uint64_t ns = R.h_hdr.n_sorted, nc = R.h_hdr.n_coinc;
+    const uint64_t nh = std::min<uint64_t>(R.h_hdr.n_hits, R.O.hit_cap);
+    const int j = r->job;
+    switch (which) {
+        case GPET_SINGLES_T_PS: v = {R.SD.t, ns * 8}; break;
+        case GPET_SINGLES_H: v = {R.SD.h, ns * 8}; break;
+        case GPET_SINGLES_UNIT: v = {R.SD.unit, ns * 4}; break;
+        case GPET_SINGLES_PANEL: v = {R.SD.panel, ns * 4}; break;
+        case GPET_SINGLES_E: v = {R.SD.e, ns * 4}; break;
+        case GPET_SINGLES_E_RAW: v = {R.SD.eraw, ns * 4}; break;
+        case GPET_COINC_A: v = {R.C.a, nc * 4}; break;
+        case GPET_COINC_B: v = {R.C.b, nc * 4}; break;
+        case GPET_TALLY_COUNT: v = {R.d_tally_count + R.tally_off[j], (size_t)R.job_crystals[j] * 8}; break;
+        case GPET_TALLY_EFX: v = {R.d_tally_efx + R.tally_off[j], (size_t)R.job_crystals[j] * 8}; break;
+        case GPET_HITS_H: v = {R.O.hit_h, nh * 8}; break;
+        case GPET_HITS_GSTEP: v = {R.O.hit_gstep, nh * 4}; break;
+        case GPET_HITS_CRYSTAL: v = {R.O.hit_crystal, nh * 4}; break;
+        case GPET_HITS_LAYER: v = {R.O.hit_layer, nh * 4}; break;
+        case GPET_HITS_WUV: v = {R.O.hit_wuv, nh * 12}; break;
+        case GPET_HITS_E: v = {R.O.hit_e, nh * 4}; break;
+        case GPET_HITS_T_PS: v = {R.O.hit_t, nh * 8}; break;
+        default: return gpet_fail(GPET_ERR_INVALID_ARG, "unknown result array %d", which);
+    }
+    if (which >= GPET_HITS_H && !R.keep_hits)
+        return gpet_fail(GPET_ERR_INVALID_ARG, "hits were not kept (gpet_options.keep_hits = 0)");
+    return GPET_OK;
+}
+
+extern "C" int gpet_result_copy(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes) {
+    if (!r || (!dst && cap_bytes)) return gpet_fail(GPET_ERR_INVALID_ARG, "NULL argument");
+    ArrayView v;
+    int st = result_array(r, which, v);
+    if (st != GPET_OK) return st;
+    if (cap_bytes < v.bytes)
+        return gpet_fail(GPET_ERR_TOO_SMALL, "array %d needs %zu bytes, got %zu", which, v.bytes, cap_bytes);
+    if (v.bytes == 0) return GPET_OK;
+    cudaError_t e = cudaMemcpy(dst, v.ptr, v.bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "result copy");
+    return GPET_OK;
+}
+
+extern "C" const void *gpet_result_device_ptr(const gpet_result *r, int32_t which) {
+    if (!r) return nullptr;
+    ArrayView v;
+    if (result_array(r, which, v) != GPET_OK) return nullptr;
+    return v.ptr;
+}
+
+extern "C" void gpet_result_free(gpet_result *r) {
+    if (!r) return;
+    if (r->owns_run) run_release(r->run);
+    delete r;
+}

@@ -1,0 +1,323 @@
+// sort.cu -- digitizer back end: LSD radix sort of singles by 64-bit time key,
+// gather into time order, coincidence sorting (Sec. 2.3 timing window).
+//
+// Keys are (job << 52) | t_ps, so a batch of jobs sorts as independent
+// segments.  The sort is a least-significant-digit radix sort with 8-bit
+// digits: one fused pass builds the eight digit histograms, a plan kernel
+// drops the passes whose digit is the same for every key (high time bytes,
+// unused job bits), and every remaining pass is tile histogram -> per-digit
+// scan -> stable scatter.  Stable ranks inside a tile come from warp
+// __match_any_sync groups in input order.  The element count is read on the
+// device, so the whole chain is enqueued without a host round trip.
+#include "internal.h"
+
+namespace gpet {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kTile = kSortThreads * kSortItems;  // 4096 keys per tile
+constexpr int kPasses = 8;
+
+__device__ __forceinline__ uint32_t lane_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ unsigned long long sort_n(const SortDev &S) {
+    const unsigned long long n = *S.n_in;
+    return n < S.cap ? n : S.cap;
+}
+
+// keys + values + the eight digit histograms (smem, then global atomics)
+__global__ void __launch_bounds__(kSortThreads) k_make_keys(SortDev S) {
+    __shared__ uint32_t h[kPasses][256];
+    for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const unsigned long long n = sort_n(S);
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint64_t key = ((uint64_t)(uint32_t)S.in_job[i] << 52) | S.in_t[i];
+        S.keys[0][i] = key;
+        S.vals[0][i] = (uint32_t)i;
+#pragma unroll
+        for (int p = 0; p < kPasses; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 0xFF], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x) {
+        const uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(S.ghist + i, v);
+    }
+}
+
+// which passes run, and which buffer each one reads
+__global__ void k_plan(SortDev S) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned long long n = sort_n(S);
+    int cur = 0;
+    for (int p = 0; p < kPasses; ++p) {
+        uint32_t mx = 0;
+        for (int d = 0; d < 256; ++d) mx = max(mx, S.ghist[p * 256 + d]);
+        const int active = (n > 1 && (unsigned long long)mx < n) ? 1 : 0;
+        S.plan[p] = active;
+        S.plan[kPasses + p] = cur;
+        if (active) cur ^= 1;
+    }
+    S.plan[2 * kPasses] = cur;  // buffer holding the sorted result
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_tile_hist(SortDev S, int p) {
+    if (!S.plan[p]) return;
+    const int src = S.plan[kPasses + p];
+    const unsigned long long n = sort_n(S);
+    const unsigned long long tiles = (n + kTile - 1) / kTile;
+    __shared__ uint32_t h[256];
+    const uint64_t *keys = S.keys[src];
+    for (unsigned long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+        __syncthreads();
+        const unsigned long long b = t * kTile;
+        for (int j = 0; j < kSortItems; ++j) {
+            const unsigned long long i = b + (unsigned long long)j * kSortThreads + threadIdx.x;
+            if (i < n) atomicAdd(&h[(keys[i] >> (8 * p)) & 0xFF], 1u);
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < 256; d += blockDim.x) S.tile_hist[(size_t)d * S.max_tiles + t] = h[d];
+        __syncthreads();
+    }
+}
+
+// block-wide exclusive scan of one value per thread (blockDim = 1024)
+__device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t &total, uint32_t *sw) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFullMask, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sw[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? sw[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFullMask, w, o);
+            if (lane >= o) w += y;
+        }
+        sw[lane] = w;  // inclusive warp prefix
+    }
+    __syncthreads();
+    const uint32_t warp_base = wid ? sw[wid - 1] : 0;
+    total = sw[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return warp_base + x - v;
+}
+
+// per digit: base of the digit + exclusive scan over tiles -> scatter offsets
+__global__ void __launch_bounds__(1024) k_digit_scan(SortDev S, int p) {
+    if (!S.plan[p]) return;
+    __shared__ uint32_t sw[32];
+    const int d = blockIdx.x;
+    const unsigned long long n = sort_n(S);
+    const unsigned long long tiles = (n + kTile - 1) / kTile;
+    uint32_t base = 0;
+    for (int e = 0; e < d; ++e) base += S.ghist[p * 256 + e];
+    uint32_t *row = S.tile_hist + (size_t)d * S.max_tiles;
+    for (unsigned long long c = 0; c < tiles; c += blockDim.x) {
+        const unsigned long long t = c + threadIdx.x;
+        const uint32_t v = t < tiles ? row[t] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exscan(v, tot, sw);
+        if (t < tiles) row[t] = base + ex;
+        base += tot;
+    }
+}
+
+// stable scatter of one tile: ranks in (warp, round, lane) order == input order
+__global__ void __launch_bounds__(kSortThreads) k_scatter(SortDev S, int p) {
+    if (!S.plan[p]) return;
+    const int src = S.plan[kPasses + p];
+    const unsigned long long n = sort_n(S);
+    const unsigned long long tiles = (n + kTile - 1) / kTile;
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ uint32_t wh[kWarps][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint64_t *kin = S.keys[src];
+    const uint32_t *vin = S.vals[src];
+    uint64_t *kout = S.keys[src ^ 1];
+    uint32_t *vout = S.vals[src ^ 1];
+    for (unsigned long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+        for (int i = threadIdx.x; i < kWarps * 256; i += blockDim.x) (&wh[0][0])[i] = 0;
+        __syncthreads();
+        const unsigned long long wb = t * kTile + (unsigned long long)w * (32 * kSortItems);
+        uint64_t k[kSortItems];
+        uint32_t v[kSortItems];
+        uint32_t rank[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const unsigned long long i = wb + (unsigned long long)j * 32 + lane;
+            const bool ok = i < n;
+            k[j] = ok ? kin[i] : 0ull;
+            v[j] = ok ? vin[i] : 0u;
+            const uint32_t d = ok ? (uint32_t)((k[j] >> (8 * p)) & 0xFF) : 256u;
+            const uint32_t peers = __match_any_sync(kFullMask, d);
+            const uint32_t before = (d < 256u) ? wh[w][d] : 0u;
+            rank[j] = before + __popc(peers & lane_lt());
+            __syncwarp();
+            if (d < 256u && (peers & lane_lt()) == 0) wh[w][d] = before + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit: tile offset + exclusive prefix over the warps
+        for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+            uint32_t off = S.tile_hist[(size_t)d * S.max_tiles + t];
+#pragma unroll
+            for (int ww = 0; ww < kWarps; ++ww) {
+                const uint32_t c = wh[ww][d];
+                wh[ww][d] = off;
+                off += c;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const unsigned long long i = wb + (unsigned long long)j * 32 + lane;
+            if (i < n) {
+                const uint32_t d = (uint32_t)((k[j] >> (8 * p)) & 0xFF);
+                const uint32_t pos = wh[w][d] + rank[j];
+                kout[pos] = k[j];
+                vout[pos] = v[j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// singles into time order
+__global__ void k_gather(SortDev S, SinglesDev out) {
+    const unsigned long long n = sort_n(S);
+    const int fin = S.plan[2 * kPasses];
+    const uint32_t *perm = S.vals[fin];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t j = perm[i];
+        out.t[i] = S.in_t[j];
+        out.h[i] = S.in_h[j];
+        out.unit[i] = S.in_unit[j];
+        out.panel[i] = S.in_panel[j];
+        out.job[i] = S.in_job[j];
+        out.e[i] = S.in_e[j];
+        out.eraw[i] = S.in_eraw[j];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *out.n = n;
+}
+
+// Coincidence sorting.  A cluster is a maximal run of time-sorted singles of
+// one job whose consecutive gaps are <= window; windows never cross cluster
+// ends, so each cluster is processed alone by the thread at its start: the
+// earliest unconsumed single opens [t0, t0 + window]; exactly two singles in
+// different panels make a coincidence; all singles in the window are consumed.
+__global__ void k_coinc_flags(SinglesDev s, CoincDev C) {
+    const unsigned long long n = *s.n;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint64_t ti = s.t[i];
+        const int ji = s.job[i];
+        const uint64_t W = C.window_ps[ji];
+        const bool start = i == 0 || s.job[i - 1] != ji || ti - s.t[i - 1] > W;
+        if (!start) continue;
+        unsigned long long a = i;
+        for (;;) {
+            unsigned long long b = a;
+            const uint64_t ta = s.t[a];
+            while (b + 1 < n && s.job[b + 1] == ji && s.t[b + 1] - ta <= W) ++b;
+            if (b == a + 1 && s.panel[a] != s.panel[b]) C.flag[a] = 1;
+            // the cluster ends where the next gap exceeds the window
+            if (b + 1 >= n || s.job[b + 1] != ji || s.t[b + 1] - s.t[b] > W) break;
+            a = b + 1;
+        }
+    }
+}
+
+// compaction of flagged indices, in index order: counts per tile, one
+// scan block, writes
+__global__ void __launch_bounds__(1024) k_coinc_count(SinglesDev s, CoincDev C) {
+    __shared__ uint32_t sw[32];
+    const unsigned long long n = *s.n;
+    const unsigned long long tiles = (n + 4095) / 4096;
+    for (unsigned long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+        uint32_t c = 0;
+        for (int j = 0; j < 4; ++j) {
+            const unsigned long long i = t * 4096 + (unsigned long long)j * 1024 + threadIdx.x;
+            if (i < n) c += C.flag[i];
+        }
+        uint32_t tot;
+        block_exscan(c, tot, sw);
+        if (threadIdx.x == 0) C.tile_cnt[t] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_coinc_scan(SinglesDev s, CoincDev C) {
+    __shared__ uint32_t sw[32];
+    const unsigned long long n = *s.n;
+    const unsigned long long tiles = (n + 4095) / 4096;
+    uint32_t base = 0;
+    for (unsigned long long c = 0; c < tiles; c += blockDim.x) {
+        const unsigned long long t = c + threadIdx.x;
+        const uint32_t v = t < tiles ? C.tile_cnt[t] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exscan(v, tot, sw);
+        if (t < tiles) C.tile_cnt[t] = base + ex;
+        base += tot;
+    }
+    if (threadIdx.x == 0) *C.n = base;
+}
+
+__global__ void __launch_bounds__(1024) k_coinc_write(SinglesDev s, CoincDev C) {
+    __shared__ uint32_t sw[32];
+    const unsigned long long n = *s.n;
+    const unsigned long long tiles = (n + 4095) / 4096;
+    for (unsigned long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+        uint32_t base = C.tile_cnt[t];
+        for (int j = 0; j < 4; ++j) {
+            const unsigned long long i = t * 4096 + (unsigned long long)j * 1024 + threadIdx.x;
+            const uint32_t f = i < n ? C.flag[i] : 0u;
+            uint32_t tot;
+            const uint32_t ex = block_exscan(f, tot, sw);
+            if (f) {
+                C.a[base + ex] = (int32_t)i;
+                C.b[base + ex] = (int32_t)(i + 1);
+            }
+            base += tot;
+        }
+    }
+}
+
+cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const CoincDev &C, int sm_count,
+                              cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(S.ghist, 0, sizeof(uint32_t) * kPasses * 256, st);
+    if (e != cudaSuccess) return e;
+    const int grid = sm_count * 4;
+    k_make_keys<<<grid, kSortThreads, 0, st>>>(S);
+    k_plan<<<1, 32, 0, st>>>(S);
+    for (int p = 0; p < kPasses; ++p) {
+        const int tg = (int)(S.max_tiles < (unsigned long long)sm_count * 8 ? S.max_tiles : (unsigned long long)sm_count * 8);
+        k_tile_hist<<<tg, kSortThreads, 0, st>>>(S, p);
+        k_digit_scan<<<256, 1024, 0, st>>>(S, p);
+        k_scatter<<<tg, kSortThreads, 0, st>>>(S, p);
+    }
+    k_gather<<<grid, 256, 0, st>>>(S, out);
+    // a cluster's flags are written by the thread at its start, possibly past
+    // its own grid-stride range: clear them all before the flag kernel
+    e = cudaMemsetAsync(C.flag, 0, S.cap ? S.cap : 1, st);
+    if (e != cudaSuccess) return e;
+    k_coinc_flags<<<grid, 256, 0, st>>>(out, C);
+    const int cg = (int)(S.max_tiles < (unsigned long long)sm_count * 4 ? S.max_tiles : (unsigned long long)sm_count * 4);
+    k_coinc_count<<<cg, 1024, 0, st>>>(out, C);
+    k_coinc_scan<<<1, 1024, 0, st>>>(out, C);
+    k_coinc_write<<<cg, 1024, 0, st>>>(out, C);
+    return cudaGetLastError();
+}
+
+}  // namespace gpet

@@ -1,0 +1,204 @@
+// transport.cu -- photon-pair transport kernels.
+//
+//   k_transport_loop  : persistent CTAs; every lane owns one history and runs
+//                       one event per loop iteration; idle lanes are refilled
+//                       warp-wide (one atomic per chunk of histories).
+//   k_transport_wave  : wavefront form (see transport_wave.cu).
+//   k_transport_redo  : exact fallback for the rare history whose on-chip
+//                       singles list overflowed: re-simulated alone with a
+//                       long list (the RNG is addressed by history id, so the
+//                       replay is bit for bit the same history).
+#include "internal.h"
+#include "transport.cuh"
+
+namespace gpet {
+
+__device__ __forceinline__ void flush_counters(const OutDev &O, const Counters &c) {
+    const uint32_t v[6] = {c.det_steps, c.flights, c.trials, c.entered, c.ph_steps, c.hits};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const uint32_t x = __reduce_add_sync(kFullMask, v[i]);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(O.counters + i, (unsigned long long)x);
+    }
+}
+
+// job owning global chunk c (chunk_start is an (n_jobs + 1)-entry prefix sum)
+__device__ __forceinline__ int chunk_job(const WorkDev &W, unsigned long long c) {
+    int lo = 0, hi = W.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (W.chunk_start[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Warp-wide refill: lanes in `need` receive consecutive history ids from the
+// warp's current chunk, fetching new chunks (one atomic each) as needed.
+__device__ __forceinline__ void warp_refill(const WorkDev &W, uint32_t need, uint64_t &pool_next, uint64_t &pool_end,
+                                            int &pool_job, bool &exhausted, bool &got, uint64_t &h, int &job) {
+    const int lane = threadIdx.x & 31;
+    got = false;
+    while (need && !exhausted) {
+        const uint64_t avail = pool_end - pool_next;
+        if (avail == 0) {
+            unsigned long long c = 0;
+            if (lane == 0) c = atomicAdd(W.next_chunk, 1ull);
+            c = __shfl_sync(kFullMask, c, 0);
+            if (c >= W.total_chunks) {
+                exhausted = true;
+                break;
+            }
+            pool_job = chunk_job(W, c);
+            const uint64_t h0 = (uint64_t)(c - W.chunk_start[pool_job]) * W.chunk_size;
+            const uint64_t nd = W.jobs[pool_job].n_decays;
+            pool_next = h0;
+            pool_end = min(h0 + (uint64_t)W.chunk_size, nd);
+            continue;
+        }
+        const uint32_t cnt = (uint32_t)__popc(need);
+        const uint32_t take = avail < cnt ? (uint32_t)avail : cnt;
+        const uint32_t rank = (uint32_t)__popc(need & lanemask_lt());
+        if (((need >> lane) & 1u) && rank < take) {
+            got = true;
+            h = pool_next + rank;
+            job = pool_job;
+        }
+        pool_next += take;
+        for (uint32_t i = 0; i < take; ++i) need &= need - 1u;  // drop the served (lowest) lanes
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int ng_smem) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    GeomDev *sgeom = reinterpret_cast<GeomDev *>(smem);
+    uint32_t *sl_unit = reinterpret_cast<uint32_t *>(sgeom + ng_smem);
+    float *sl_e = reinterpret_cast<float *>(sl_unit + S * blockDim.x);
+    uint32_t *sl_dt = reinterpret_cast<uint32_t *>(sl_e + S * blockDim.x);
+    stage_geometry(W, sgeom, ng_smem);
+    __syncthreads();
+
+    const SinglesList SL{sl_unit + threadIdx.x, sl_e + threadIdx.x, sl_dt + threadIdx.x, (int)blockDim.x};
+    PState s;
+    s.phase = kPhIdle;
+    s.job = 0;
+    Counters cnt = {0, 0, 0, 0, 0, 0};
+    uint64_t pool_next = 0, pool_end = 0;
+    int pool_job = 0;
+    bool exhausted = false;
+    int status = kStatusOk;
+
+    for (;;) {
+        const uint32_t need = __ballot_sync(kFullMask, s.phase == kPhIdle);
+        if (need) {
+            bool got;
+            uint64_t h = 0;
+            int job = 0;
+            warp_refill(W, need, pool_next, pool_end, pool_job, exhausted, got, h, job);
+            if (got) {
+                s.h = h;
+                s.job = job;
+                s.phase = kPhSource;
+            }
+        }
+        if (__all_sync(kFullMask, s.phase == kPhIdle)) break;  // only when the queue is exhausted
+
+        const JobDev &J = W.jobs[s.job];
+        const GeomDev &g = J.geom < ng_smem ? sgeom[J.geom] : W.geoms[J.geom];
+        int st = kStatusOk;
+        switch (s.phase) {
+            case kPhSource: ev_source(J, s); break;
+            case kPhPhantom: st = ev_phantom(J, W, s, cnt); break;
+            case kPhFlight: ev_flight(J, g, s, cnt); break;
+            case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, S, cnt); break;
+            default: break;
+        }
+        if (st != kStatusOk) {          // iteration cap hit: abandon the history, flag the run
+            status |= st;
+            s.phase = kPhIdle;
+        }
+        const bool fin = s.phase == kPhFinish;
+        if (__any_sync(kFullMask, fin)) {
+            ev_finish(W.jobs, W.geoms, O, s, fin, SL, kFullMask);
+            if (fin) s.phase = kPhIdle;
+        }
+    }
+    flush_counters(O, cnt);
+    if (status) atomicOr(O.status, status);
+}
+
+// Re-simulate the histories listed in O.ovf_* with a 64-entry singles list in
+// local memory.  Tallies and hits were already counted by the main kernel, so
+// only the singles are emitted here.
+__global__ void __launch_bounds__(128) k_transport_redo(WorkDev W, OutDev O) {
+    constexpr int S = 64;
+    uint32_t l_unit[S];
+    float l_e[S];
+    uint32_t l_dt[S];
+    const SinglesList SL{l_unit, l_e, l_dt, 1};
+    const unsigned long long n = min(*O.n_ovf, O.ovf_cap);
+    Counters cnt = {0, 0, 0, 0, 0, 0};
+    int status = kStatusOk;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long base0 = (unsigned long long)blockIdx.x * blockDim.x;
+    for (unsigned long long base = base0; base < n; base += stride) {
+        const unsigned long long i = base + threadIdx.x;
+        PState s;
+        s.phase = kPhIdle;
+        s.job = 0;
+        if (i < n) {
+            s.h = O.ovf_h[i];
+            s.job = O.ovf_job[i];
+            s.phase = kPhSource;
+            const JobDev &J = W.jobs[s.job];
+            const GeomDev &g = W.geoms[J.geom];
+            while (s.phase != kPhFinish && s.phase != kPhIdle) {
+                int st = kStatusOk;
+                switch (s.phase) {
+                    case kPhSource: ev_source(J, s); break;
+                    case kPhPhantom: st = ev_phantom(J, W, s, cnt); break;
+                    case kPhFlight: ev_flight(J, g, s, cnt); break;
+                    case kPhPanel: st = ev_panel<false>(J, g, W, O, s, SL, S, cnt); break;
+                    default: break;
+                }
+                if (st != kStatusOk) { status |= st; s.phase = kPhIdle; }
+            }
+            if (s.ovf) { status |= kStatusOverflow; s.phase = kPhIdle; }
+        }
+        __syncwarp();
+        const bool fin = s.phase == kPhFinish;
+        ev_finish(W.jobs, W.geoms, O, s, fin, SL, kFullMask);
+    }
+    if (status) atomicOr(O.status, status);
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static size_t loop_smem(int ng_smem, int block, int S) {
+    return (size_t)ng_smem * sizeof(GeomDev) + (size_t)S * block * 12;
+}
+
+cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
+    constexpr int S = 8;
+    const int block = cfg.block_size;
+    const int ng = min(W.n_geoms, cfg.max_smem_geoms);
+    const size_t smem = loop_smem(ng, block, S);
+    {
+        cudaError_t e = cudaFuncSetAttribute(k_transport_loop<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        // persistent grid: never more CTAs than can be resident at once
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_loop<S>, block, smem);
+        if (e != cudaSuccess) return e;
+        const int per_sm = max(1, min(occ, cfg.grid / max(cfg.sm_count, 1)));
+        k_transport_loop<S><<<cfg.sm_count * per_sm, block, smem, st>>>(W, O, ng);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_transport_redo<<<cfg.sm_count, 128, 0, st>>>(W, O);
+    return cudaGetLastError();
+}
+
+}  // namespace gpet

@@ -1,0 +1,407 @@
+// transport.cuh -- per-history photon-pair transport as a set of events that
+// advance one history by one step.  Both transport kernels (the per-lane event
+// loop and the warp-regrouping wavefront) run these same events, so they
+// produce identical histories.
+//
+// Paper anchors (arxiv 2603.07327): Sec. 2.1 (flight by line-plane
+// intersection, panel-local frame, Woodcock stepping until the photon leaves
+// the panel or drops below the cutoff, layer selection, crystal / layer /
+// module / panel labels, singles readout level), Sec. 2.3 (back-to-back pairs,
+// no positron range, energy blur and window), abstract (transport across
+// layers and panels).
+#pragma once
+
+#include "device.cuh"
+
+namespace gpet {
+
+enum : uint32_t { kPhIdle = 0, kPhSource = 1, kPhPhantom = 2, kPhFlight = 3, kPhPanel = 4, kPhFinish = 5 };
+
+// per-history singles list: unit ids, energy sums, earliest time offset
+// (t - t0 in ps); `stride` separates consecutive entries of one history
+struct SinglesList {
+    uint32_t *unit;
+    float *e;
+    uint32_t *dt;
+    int stride;
+};
+
+// outputs shared by all jobs of a launch
+struct OutDev {
+    // kept singles (SoA); count in *n_singles (may exceed cap -> overflow, host re-runs)
+    uint64_t *s_t, *s_h;
+    int32_t *s_unit, *s_panel, *s_job;
+    float *s_e, *s_eraw;
+    unsigned long long *n_singles;
+    unsigned long long s_cap;
+    // optional crystal interactions
+    uint64_t *hit_h, *hit_t;
+    int32_t *hit_gstep, *hit_crystal, *hit_layer, *hit_job;
+    float *hit_wuv, *hit_e;
+    unsigned long long *n_hits;   // slots taken when storing hits
+    unsigned long long hit_cap;   // 0 = do not store
+    // histories whose singles list overflowed: re-simulated by the fallback kernel
+    uint64_t *ovf_h;
+    int32_t *ovf_job;
+    unsigned long long *n_ovf;
+    unsigned long long ovf_cap;
+    // event counters: det_steps, flights, compton_trials, entered, phantom_steps, hits
+    unsigned long long *counters;
+    int *status;
+};
+
+struct WorkDev {
+    const JobDev *jobs;
+    int n_jobs;
+    const GeomDev *geoms;                   // deduplicated geometry table
+    int n_geoms;
+    const unsigned long long *chunk_start;  // n_jobs + 1 prefix sums of chunks per job
+    unsigned long long total_chunks;
+    unsigned long long *next_chunk;        // global work counter
+    unsigned int chunk_size;
+    const float *gtab;                      // Compton ratio table, kXsIntervals + 1 nodes
+    float ln_emin, inv_h;
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// copy the first ng geometry descriptors into shared memory
+__device__ __forceinline__ void stage_geometry(const WorkDev &W, GeomDev *sg, int ng) {
+    constexpr int words = (int)(sizeof(GeomDev) / 4);
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(W.geoms);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(sg);
+    for (int i = threadIdx.x; i < ng * words; i += blockDim.x) dst[i] = src[i];
+}
+
+struct PState {
+    uint64_t h, t0;
+    float x, y, z, dx, dy, dz;      // global frame, or panel frame (w, u, v) when panel >= 0
+    float x0, y0, z0, ox, oy, oz;   // decay point and photon-0 direction
+    float E, path, trem;
+    int32_t job, panel, last;
+    uint32_t sph, sdet, gamma, phase, nsing, ovf;
+};
+
+struct Counters {
+    uint32_t det_steps, flights, trials, entered, ph_steps, hits;
+};
+
+__device__ __forceinline__ void to_global(const GeomDev &g, PState &s) {
+    const float c = g.pc[s.panel], sn = g.ps[s.panel];
+    const float rw = g.R + s.x;
+    const float gx = rw * c - s.y * sn, gy = rw * sn + s.y * c;
+    const float gdx = s.dx * c - s.dy * sn, gdy = s.dx * sn + s.dy * c;
+    s.x = gx; s.y = gy;
+    s.dx = gdx; s.dy = gdy;
+}
+
+__device__ __forceinline__ bool in_phantom(const JobDev &J, float x, float y, float z) {
+    return x >= J.ph_origin[0] && x < J.ph_hi[0] && y >= J.ph_origin[1] && y < J.ph_hi[1] && z >= J.ph_origin[2] &&
+           z < J.ph_hi[2];
+}
+
+__device__ __forceinline__ void start_photon(const JobDev &J, PState &s) {
+    const float sg = s.gamma == 0 ? 1.0f : -1.0f;
+    s.x = s.x0; s.y = s.y0; s.z = s.z0;
+    s.dx = sg * s.ox; s.dy = sg * s.oy; s.dz = sg * s.oz;
+    s.E = kE0;
+    s.path = 0.0f;
+    s.sph = 0; s.sdet = 0;
+    s.panel = -1; s.last = -1;
+    s.phase = (J.has_phantom && in_phantom(J, s.x, s.y, s.z)) ? kPhPhantom : kPhFlight;
+}
+
+__device__ __forceinline__ void photon_done(const JobDev &J, PState &s) {
+    if (s.gamma == 0) {
+        s.gamma = 1;
+        start_photon(J, s);
+    } else {
+        s.phase = kPhFinish;
+    }
+}
+
+// smallest voxel with cdf > target (binary search on the FP64 prefix sums)
+__device__ __forceinline__ int64_t pick_voxel(const JobDev &J, double target) {
+    if (target >= J.ph_total) return J.ph_last_active;
+    int64_t lo = 0, hi = J.ph_n - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(J.ph_cdf + mid) > target) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// decay of history h (Sec. 2.3): time, annihilation point, photon-0 direction
+__device__ __forceinline__ void ev_source(const JobDev &J, PState &s) {
+    const uint4 r = draw(J.seed, s.h, kTagSource, 0u, 0u, 0u);
+    const uint64_t r64 = ((uint64_t)r.x << 32) | r.y;
+    s.t0 = __umul64hi(J.t_span_ps, r64);
+    if (J.src_kind == 1) {
+        const uint4 q = draw(J.seed, s.h, kTagSource, 0u, 0u, 1u);
+        const uint4 zq = draw(J.seed, s.h, kTagSource, 0u, 0u, 2u);
+        const uint64_t r53 = ((uint64_t)q.x << 21) | (q.y >> 11);
+        const double target = (double)r53 * 0x1p-53 * J.ph_total;
+        const int64_t vi = pick_voxel(J, target);
+        const int64_t ix = vi % J.ph_nx, iy = (vi / J.ph_nx) % J.ph_ny, iz = vi / ((int64_t)J.ph_nx * J.ph_ny);
+        s.x0 = fmaf((float)ix + u01(q.z), J.ph_voxel[0], J.ph_origin[0]);
+        s.y0 = fmaf((float)iy + u01(q.w), J.ph_voxel[1], J.ph_origin[1]);
+        s.z0 = fmaf((float)iz + u01(zq.x), J.ph_voxel[2], J.ph_origin[2]);
+    } else {
+        s.x0 = J.src_pos[0]; s.y0 = J.src_pos[1]; s.z0 = J.src_pos[2];
+    }
+    if (J.src_kind == 2) {
+        s.ox = J.src_dir[0]; s.oy = J.src_dir[1]; s.oz = J.src_dir[2];
+    } else {
+        const float ct = 2.0f * u01(r.z) - 1.0f;
+        const float st = sqrtf((1.0f - ct) * (1.0f + ct));
+        float sp, cp;
+        sincospif(2.0f * u01(r.w), &sp, &cp);
+        s.ox = st * cp; s.oy = st * sp; s.oz = ct;
+    }
+    s.gamma = 0;
+    s.nsing = 0;
+    s.ovf = 0;
+    start_photon(J, s);
+}
+
+// one Woodcock step in the voxel phantom
+__device__ __forceinline__ int ev_phantom(const JobDev &J, const WorkDev &W, PState &s, Counters &cnt) {
+    if (s.sph >= (uint32_t)kMaxSteps) return kStatusTimeout;
+    const uint4 r = draw(J.seed, s.h, kTagPhantom, s.gamma, s.sph, 0u);
+    const uint32_t step_id = s.sph++;
+    cnt.ph_steps++;
+    // distance to the grid box exit
+    float t_out = 3.0e38f;
+    if (s.dx > 0.f) t_out = fminf(t_out, (J.ph_hi[0] - s.x) / s.dx); else if (s.dx < 0.f) t_out = fminf(t_out, (J.ph_origin[0] - s.x) / s.dx);
+    if (s.dy > 0.f) t_out = fminf(t_out, (J.ph_hi[1] - s.y) / s.dy); else if (s.dy < 0.f) t_out = fminf(t_out, (J.ph_origin[1] - s.y) / s.dy);
+    if (s.dz > 0.f) t_out = fminf(t_out, (J.ph_hi[2] - s.z) / s.dz); else if (s.dz < 0.f) t_out = fminf(t_out, (J.ph_origin[2] - s.z) / s.dz);
+    t_out = fmaxf(t_out, 0.0f);
+    const Xs xs = xs_at(s.E, W.gtab, W.ln_emin, W.inv_h);
+    float mu_maj = 0.0f;
+    for (int m = 0; m < J.ph_nmat; ++m) mu_maj = fmaxf(mu_maj, mu_total(J.ph_mu_c511[m], J.ph_mu_pe511[m], xs));
+    const float step = mu_maj > 0.0f ? -logf(u01(r.x)) * (10.0f / mu_maj) : 3.0e38f;
+    if (step >= t_out) {
+        s.x = fmaf(t_out, s.dx, s.x); s.y = fmaf(t_out, s.dy, s.y); s.z = fmaf(t_out, s.dz, s.z);
+        s.path += t_out;
+        s.phase = kPhFlight;
+        return kStatusOk;
+    }
+    s.x = fmaf(step, s.dx, s.x); s.y = fmaf(step, s.dy, s.y); s.z = fmaf(step, s.dz, s.z);
+    s.path += step;
+    int ix = (int)floorf((s.x - J.ph_origin[0]) * J.ph_inv_voxel[0]);
+    int iy = (int)floorf((s.y - J.ph_origin[1]) * J.ph_inv_voxel[1]);
+    int iz = (int)floorf((s.z - J.ph_origin[2]) * J.ph_inv_voxel[2]);
+    ix = min(max(ix, 0), J.ph_nx - 1); iy = min(max(iy, 0), J.ph_ny - 1); iz = min(max(iz, 0), J.ph_nz - 1);
+    const int m = __ldg(J.ph_mat + ((int64_t)iz * J.ph_ny + iy) * J.ph_nx + ix);
+    const float pe = J.ph_mu_pe511[m] * xs.r3;
+    const float mu_m = fmaf(J.ph_mu_c511[m], xs.g, pe);
+    if (u01(r.y) * mu_maj >= mu_m) return kStatusOk;          // virtual
+    if (u01(r.z) * mu_m < pe) { photon_done(J, s); return kStatusOk; }   // photoelectric
+    float xm1;
+    const int nt = kahn_sample(J.seed, s.h, kTagPhantom, s.gamma, step_id, s.E, xm1);
+    if (nt < 0) return kStatusTimeout;
+    cnt.trials += (uint32_t)nt;
+    const float omc = xm1 / (s.E * kInvMec2);
+    rotate_dir(s.dx, s.dy, s.dz, omc, u01(r.w));
+    const float Ep = s.E / (1.0f + xm1);
+    if (Ep < J.e_cut) { photon_done(J, s); return kStatusOk; }
+    s.E = Ep;
+    return kStatusOk;
+}
+
+// flight to the next panel by line-plane intersection
+__device__ __forceinline__ void ev_flight(const JobDev &J, const GeomDev &g, PState &s, Counters &cnt) {
+    cnt.flights++;
+    float t_in, t_out;
+    const int k = flight(g, s.x, s.y, s.z, s.dx, s.dy, s.dz, s.last, t_in, t_out);
+    if (k < 0) { photon_done(J, s); return; }
+    cnt.entered++;
+    // entry point, then the panel-local frame (w, u, v)
+    const float ex = fmaf(t_in, s.dx, s.x), ey = fmaf(t_in, s.dy, s.y), ez = fmaf(t_in, s.dz, s.z);
+    s.path += t_in;
+    const float c = g.pc[k], sn = g.ps[k];
+    const float w = fmaf(ex, c, ey * sn) - g.R;
+    const float u = fmaf(-ex, sn, ey * c);
+    const float dw = fmaf(s.dx, c, s.dy * sn), du = fmaf(-s.dx, sn, s.dy * c);
+    s.x = w; s.y = u; s.z = ez;
+    s.dx = dw; s.dy = du;
+    s.trem = t_out - t_in;
+    s.panel = k;
+    s.phase = kPhPanel;
+}
+
+// record energy `dep` deposited in crystal L.crystal into the history's singles list
+__device__ __forceinline__ void add_single(const GeomDev &g, PState &s, const SinglesList &SL, int max_entries,
+                                           int crystal, int module, float dep, uint32_t dtp) {
+    uint32_t unit;
+    if (g.readout_level == 0) unit = (uint32_t)s.panel;
+    else if (g.readout_level == 1) unit = (uint32_t)(s.panel * g.modules_u * g.modules_v + module);
+    else unit = (uint32_t)crystal;
+    for (uint32_t j = 0; j < s.nsing; ++j) {
+        if (SL.unit[j * SL.stride] == unit) {
+            SL.e[j * SL.stride] += dep;
+            SL.dt[j * SL.stride] = min(SL.dt[j * SL.stride], dtp);
+            return;
+        }
+    }
+    if ((int)s.nsing < max_entries) {
+        SL.unit[s.nsing * SL.stride] = unit;
+        SL.e[s.nsing * SL.stride] = dep;
+        SL.dt[s.nsing * SL.stride] = dtp;
+        s.nsing++;
+    } else {
+        s.ovf = 1;
+    }
+}
+
+// one Woodcock step inside the current panel (layer selection, interaction, hit)
+template <bool kTallies>
+__device__ __forceinline__ int ev_panel(const JobDev &J, const GeomDev &g, const WorkDev &W, const OutDev &O,
+                                        PState &s, const SinglesList &SL, int max_entries, Counters &cnt) {
+    if (s.sdet >= (uint32_t)kMaxSteps) return kStatusTimeout;
+    const uint4 r = draw(J.seed, s.h, kTagDetector, s.gamma, s.sdet, 0u);
+    const uint32_t step_id = s.sdet++;
+    cnt.det_steps++;
+    const Xs xs = xs_at(s.E, W.gtab, W.ln_emin, W.inv_h);
+    float mu_maj = 0.0f;
+    for (int m = 0; m < g.n_materials; ++m) mu_maj = fmaxf(mu_maj, mu_total(g.mu_c511[m], g.mu_pe511[m], xs));
+    const float step = mu_maj > 0.0f ? -logf(u01(r.x)) * (10.0f / mu_maj) : 3.0e38f;
+    if (step >= s.trem) {                      // leaves the panel: back to flight
+        s.x = fmaf(s.trem, s.dx, s.x); s.y = fmaf(s.trem, s.dy, s.y); s.z = fmaf(s.trem, s.dz, s.z);
+        s.path += s.trem;
+        to_global(g, s);
+        s.last = s.panel;
+        s.panel = -1;
+        s.phase = kPhFlight;
+        return kStatusOk;
+    }
+    s.x = fmaf(step, s.dx, s.x); s.y = fmaf(step, s.dy, s.y); s.z = fmaf(step, s.dz, s.z);
+    s.path += step;
+    s.trem -= step;
+    const Loc L = locate(g, s.panel, s.x, s.y, s.z);
+    const float pe = g.mu_pe511[L.mat] * xs.r3;
+    const float mu_m = fmaf(g.mu_c511[L.mat], xs.g, pe);
+    if (u01(r.y) * mu_maj >= mu_m) return kStatusOk;   // virtual
+    float dep;
+    bool dead = false;
+    if (u01(r.z) * mu_m < pe) {                        // photoelectric
+        dep = s.E;
+        dead = true;
+    } else {                                           // Compton (Klein-Nishina)
+        float xm1;
+        const int nt = kahn_sample(J.seed, s.h, kTagDetector, s.gamma, step_id, s.E, xm1);
+        if (nt < 0) return kStatusTimeout;
+        cnt.trials += (uint32_t)nt;
+        const float omc = xm1 / (s.E * kInvMec2);
+        // local frame (w, u, v) is a rotation of (x, y, z) about the axis
+        rotate_dir(s.dx, s.dy, s.dz, omc, u01(r.w));
+        const float Ep = s.E / (1.0f + xm1);
+        if (Ep < J.e_cut) {
+            dep = s.E;
+            dead = true;
+        } else {
+            dep = s.E * xm1 / (1.0f + xm1);
+            s.E = Ep;
+        }
+    }
+    if (L.crystal >= 0) {
+        cnt.hits++;
+        const uint32_t dtp = (uint32_t)floorf(s.path * kInvCmmPerPs);
+        if (kTallies) {
+            atomicAdd(J.tally_count + L.crystal, 1ull);
+            atomicAdd(J.tally_efx + L.crystal, (unsigned long long)__float2ull_rn(dep * kEfxScale));
+            if (O.hit_cap) {
+                const unsigned long long slot = atomicAdd(O.n_hits, 1ull);
+                if (slot < O.hit_cap) {
+                    O.hit_h[slot] = s.h;
+                    O.hit_t[slot] = s.t0 + dtp;
+                    O.hit_gstep[slot] = (int32_t)((s.gamma << 24) | step_id);
+                    O.hit_crystal[slot] = L.crystal;
+                    O.hit_layer[slot] = L.layer;
+                    O.hit_job[slot] = s.job;
+                    O.hit_wuv[3 * slot] = s.x;
+                    O.hit_wuv[3 * slot + 1] = s.y;
+                    O.hit_wuv[3 * slot + 2] = s.z;
+                    O.hit_e[slot] = dep;
+                }
+            }
+        }
+        add_single(g, s, SL, max_entries, L.crystal, L.module, dep, dtp);
+    }
+    if (dead) { photon_done(J, s); return kStatusOk; }
+    s.trem = panel_exit(g, s.x, s.y, s.z, s.dx, s.dy, s.dz);
+    return kStatusOk;
+}
+
+
+// digitizer for one finished history: blur, window, warp-aggregated append
+// (call with the lanes of `mask` converged; `active` lanes own a history)
+__device__ __forceinline__ void ev_finish(const JobDev *__restrict__ jobs, const GeomDev *__restrict__ geoms,
+                                          const OutDev &O, const PState &s, bool active, const SinglesList &SL,
+                                          uint32_t mask) {
+    const int lane = threadIdx.x & 31;
+    const JobDev *J = active ? &jobs[s.job] : nullptr;
+    const bool ovf = active && s.ovf;
+    const uint32_t n = (active && !ovf) ? s.nsing : 0u;
+    // histories whose list overflowed go to the fallback list instead
+    {
+        const uint32_t b = __ballot_sync(mask, ovf);
+        if (b) {
+            unsigned long long base = 0;
+            const int leader = __ffs(b) - 1;
+            if (lane == leader) base = atomicAdd(O.n_ovf, (unsigned long long)__popc(b));
+            base = __shfl_sync(mask, base, leader);
+            if (ovf) {
+                const unsigned long long slot = base + __popc(b & lanemask_lt());
+                if (slot < O.ovf_cap) { O.ovf_h[slot] = s.h; O.ovf_job[slot] = s.job; }
+            }
+        }
+    }
+    const uint32_t nmax = __reduce_max_sync(mask, n);
+    for (uint32_t j = 0; j < nmax; ++j) {
+        bool keep = false;
+        float e = 0.f, eb = 0.f;
+        uint32_t unit = 0, dt = 0;
+        if (j < n) {
+            unit = SL.unit[j * SL.stride];
+            e = SL.e[j * SL.stride];
+            dt = SL.dt[j * SL.stride];
+            const uint4 q = philox4x32_10(make_uint4((uint32_t)s.h, (uint32_t)(s.h >> 32), kTagDigi << 28, unit),
+                                          make_uint2((uint32_t)J->seed, (uint32_t)(J->seed >> 32)));
+            float cp = cospif(2.0f * u01(q.y));
+            const float n01 = sqrtf(-2.0f * logf(u01(q.x))) * cp;
+            const float sigma = J->sig_k * sqrtf(kE0 * e);
+            eb = fmaf(sigma, n01, e);
+            keep = eb >= J->e_lo && eb <= J->e_hi;
+        }
+        const uint32_t b = __ballot_sync(mask, keep);
+        if (!b) continue;
+        unsigned long long base = 0;
+        const int leader = __ffs(b) - 1;
+        if (lane == leader) base = atomicAdd(O.n_singles, (unsigned long long)__popc(b));
+        base = __shfl_sync(mask, base, leader);
+        if (keep) {
+            const unsigned long long slot = base + __popc(b & lanemask_lt());
+            if (slot < O.s_cap) {
+                const GeomDev &g = geoms[J->geom];
+                int panel;
+                if (g.readout_level == 0) panel = (int)unit;
+                else if (g.readout_level == 1) panel = (int)(unit / (uint32_t)(g.modules_u * g.modules_v));
+                else panel = (int)(unit / (uint32_t)(g.crystals_per_module * g.modules_u * g.modules_v));
+                O.s_t[slot] = s.t0 + dt;
+                O.s_h[slot] = s.h;
+                O.s_unit[slot] = (int32_t)unit;
+                O.s_panel[slot] = panel;
+                O.s_job[slot] = s.job;
+                O.s_e[slot] = eb;
+                O.s_eraw[slot] = e;
+            }
+        }
+    }
+}
+
+}  // namespace gpet
