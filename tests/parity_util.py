@@ -61,9 +61,17 @@ def compare_hits(gpu, orc, n_histories):
     rel_e = np.abs(g["e"] - o["e"]) / np.maximum(o["e"], 1e-30)
     pos = np.max(np.abs(np.stack([g["w"] - o["w"], g["u"] - o["u"], g["v"] - o["v"]])), axis=0) if len(g) else np.zeros(0)
     dt = np.abs(g["t"] - o["t"])
+    worst = None
+    if len(g):
+        k = np.argsort(pos)[-3:][::-1]
+        worst = [dict(h=int(g["h"][i]), gamma=int(g["gamma"][i]), step=int(g["step"][i]), crystal=int(g["crystal"][i]),
+                      gpu=(float(g["w"][i]), float(g["u"][i]), float(g["v"][i])),
+                      orc=(float(o["w"][i]), float(o["u"][i]), float(o["v"][i])), e=float(o["e"][i]),
+                      dev=float(pos[i])) for i in k]
     return dict(bad=bad, frac_identical=1.0 - len(bad) / max(n_histories, 1), n_compared=len(g),
                 max_rel_e=float(rel_e.max()) if len(g) else 0.0, max_pos=float(pos.max()) if len(g) else 0.0,
-                max_dt=int(dt.max()) if len(g) else 0, n_gpu=len(gpu), n_orc=len(orc))
+                max_dt=int(dt.max()) if len(g) else 0, n_gpu=len(gpu), n_orc=len(orc), worst_pos=worst,
+                p999_pos=float(np.quantile(pos, 0.999)) if len(g) else 0.0)
 
 
 def compare_singles(gs, os_, bad, e_lo, e_hi):
