@@ -211,6 +211,14 @@ int gpet_build_geometry(const gpet_scanner_desc *d, GeomDev &g, int64_t &n_cryst
         g.mu_c511[m] = (float)mu_c511(M);
         g.mu_pe511[m] = (float)(M.mu_total_511_cm * M.photo_frac_511);
     }
+    // ring culling parameters (see flight() in device.cuh)
+    const double rout = std::sqrt((d->inner_radius_mm + w) * (d->inner_radius_mm + w) + 0.25 * U * U);
+    g.R2 = (float)(d->inner_radius_mm * d->inner_radius_mm);
+    g.rout2 = (float)(rout * rout * (1.0 + 1e-6));
+    g.beta = (float)std::atan2(0.5 * U, d->inner_radius_mm);
+    g.phi0 = (float)d->first_angle_rad;
+    g.dphi = (float)(2.0 * M_PI / d->n_panels);
+    g.inv_dphi = (float)(d->n_panels / (2.0 * M_PI));
     std::vector<double> ang(d->n_panels);
     for (int k = 0; k < d->n_panels; ++k) {
         ang[k] = d->first_angle_rad + 2.0 * M_PI * k / d->n_panels;

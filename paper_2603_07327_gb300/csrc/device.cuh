@@ -53,6 +53,9 @@ struct GeomDev {
     float mu_c511[kMaxMaterials];   // Compton coefficient at 511 keV (1/cm)
     float mu_pe511[kMaxMaterials];  // photoelectric coefficient at 511 keV (1/cm)
     float pc[kMaxPanels], ps[kMaxPanels];  // cos / sin of each panel's angle
+    // ring culling: every panel box lies in the annulus R^2 <= r^2 <= rout2 and
+    // inside its angular sector |phi - phi_k| <= beta (phi_k = phi0 + k dphi)
+    float R2, rout2, beta, phi0, dphi, inv_dphi;
     LayerDev layers[kMaxLayers];
 };
 
@@ -238,19 +241,16 @@ __device__ __forceinline__ float panel_exit(const GeomDev &g, float w, float u, 
     return fmaxf(t, 0.0f);
 }
 
-// line-plane flight: nearest panel entered along (x, d), skipping `skip`;
-// slab test on each panel's box in its own frame
-__device__ __forceinline__ int flight(const GeomDev &g, float x, float y, float z, float dx, float dy, float dz,
-                                      int skip, float &t_in, float &t_out) {
-    int best = -1;
-    float bi = 3.0e38f, bo = 0.0f;
-    for (int k = 0; k < g.n_panels; ++k) {
-        if (k == skip) continue;
+// slab test of the ray against panel k's box in its own frame; keeps the
+// nearest entry (ties to the lower panel index)
+__device__ __forceinline__ void panel_slab(const GeomDev &g, int k, float x, float y, float z, float dx, float dy,
+                                           float dz, int &best, float &bi, float &bo) {
+    {
         const float c = g.pc[k], s = g.ps[k];
         const float w0 = fmaf(x, c, y * s) - g.R;
         const float dw = fmaf(dx, c, dy * s);
         // behind the inner face and moving away: no entry
-        if (w0 < 0.0f && dw <= 0.0f) continue;
+        if (w0 < 0.0f && dw <= 0.0f) return;
         const float u0 = fmaf(-x, s, y * c);
         const float du = fmaf(-dx, s, dy * c);
         float tmin = -3.0e38f, tmax = 3.0e38f;
@@ -275,10 +275,57 @@ __device__ __forceinline__ int flight(const GeomDev &g, float x, float y, float 
             tmax = fminf(tmax, fmaxf(t1, t2));
         } else if (z < -g.half_v || z > g.half_v) miss = true;
         tmin = fmaxf(tmin, 0.0f);
-        if (!miss && tmin < tmax && tmin < bi) {
+        if (!miss && tmin < tmax && (tmin < bi || (tmin == bi && k < best))) {
             best = k;
             bi = tmin;
             bo = tmax;
+        }
+    }
+}
+
+// Line-plane flight (Sec. 2.1): nearest panel entered along (x, d), skipping
+// `skip`.  A ray that starts inside the circle of radius R (every inner face
+// is tangent to it) crosses the annulus holding all panel boxes exactly once,
+// and its azimuth is monotonic along the way; only panels whose angular
+// sector meets that azimuth interval can be entered, so only those are
+// slab-tested (same result as testing all panels).  Other rays test all.
+__device__ __forceinline__ int flight(const GeomDev &g, float x, float y, float z, float dx, float dy, float dz,
+                                      int skip, float &t_in, float &t_out) {
+    int best = -1;
+    float bi = 3.0e38f, bo = 0.0f;
+    const float c0 = fmaf(x, x, y * y);
+    const float a = fmaf(dx, dx, dy * dy);
+    if (c0 < g.R2 * 0.9999f && g.n_panels > 2) {
+        if (a <= 0.0f) {
+            t_in = bi;
+            t_out = bo;
+            return -1;  // parallel to the axis inside the ring: never reaches a panel
+        }
+        const float b = fmaf(x, dx, y * dy);
+        // exit distances of the circles R and R_out (stable roots, c0 < R^2)
+        const float d1 = g.R2 - c0, d2 = g.rout2 - c0;
+        const float s1 = sqrtf(fmaf(b, b, a * d1)), s2 = sqrtf(fmaf(b, b, a * d2));
+        const float t1 = b > 0.0f ? d1 / (b + s1) : (s1 - b) / a;
+        const float t2 = b > 0.0f ? d2 / (b + s2) : (s2 - b) / a;
+        const float p1 = atan2f(fmaf(t1, dy, y), fmaf(t1, dx, x)) - g.phi0;
+        float p2 = atan2f(fmaf(t2, dy, y), fmaf(t2, dx, x)) - g.phi0;
+        // unwrap p2 next to p1 (the swept interval is shorter than pi)
+        if (p2 - p1 > 3.14159265f) p2 -= 6.28318531f;
+        else if (p1 - p2 > 3.14159265f) p2 += 6.28318531f;
+        // panel k can be entered only if its centre angle k*dphi lies within beta
+        // of the swept interval; 1e-3 rad of margin covers FP32 rounding
+        const float lo = fminf(p1, p2) - g.beta - 1e-3f, hi = fmaxf(p1, p2) + g.beta + 1e-3f;
+        const int jlo = (int)ceilf(lo * g.inv_dphi), jhi = (int)floorf(hi * g.inv_dphi);
+        for (int j = jlo; j <= jhi && j < jlo + g.n_panels; ++j) {
+            int k = j % g.n_panels;
+            if (k < 0) k += g.n_panels;
+            if (k == skip) continue;
+            panel_slab(g, k, x, y, z, dx, dy, dz, best, bi, bo);
+        }
+    } else {
+        for (int k = 0; k < g.n_panels; ++k) {
+            if (k == skip) continue;
+            panel_slab(g, k, x, y, z, dx, dy, dz, best, bi, bo);
         }
     }
     t_in = bi;

@@ -51,6 +51,7 @@ struct CoincDev {
 };
 
 cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
+cudaError_t launch_transport_wave(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
 cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const CoincDev &C, int sm_count,
                               cudaStream_t st);
 

@@ -44,8 +44,10 @@ int run_default_cfg(Run &R, const gpet_options *opt) {
     const int bps = (opt && opt->blocks_per_sm > 0) ? opt->blocks_per_sm : 4;
     R.cfg.grid = sms * bps;
     R.cfg.kernel = (opt && opt->kernel > 0) ? opt->kernel : kKernelLoop;
-    if (R.cfg.kernel != kKernelLoop) return gpet_fail(GPET_ERR_INVALID_ARG, "kernel %d not available", R.cfg.kernel);
+    if (R.cfg.kernel != kKernelLoop && R.cfg.kernel != kKernelWave)
+        return gpet_fail(GPET_ERR_INVALID_ARG, "kernel %d not in {1, 2}", R.cfg.kernel);
     R.cfg.compact_every = (opt && opt->compact_every > 0) ? opt->compact_every : 1;
+    if (R.cfg.compact_every > 64) return gpet_fail(GPET_ERR_INVALID_ARG, "compact_every must be <= 64");
     R.cfg.max_smem_geoms = 16;
     R.keep_hits = opt && opt->keep_hits;
     R.stream = opt ? reinterpret_cast<cudaStream_t>(opt->stream) : nullptr;

@@ -3,7 +3,7 @@
 //   k_transport_loop  : persistent CTAs; every lane owns one history and runs
 //                       one event per loop iteration; idle lanes are refilled
 //                       warp-wide (one atomic per chunk of histories).
-//   k_transport_wave  : wavefront form (see transport_wave.cu).
+//   k_transport_wave  : wavefront form with warp-ballot regrouping (transport_wave.cu).
 //   k_transport_redo  : exact fallback for the rare history whose on-chip
 //                       singles list overflowed: re-simulated alone with a
 //                       long list (the RNG is addressed by history id, so the
@@ -184,7 +184,10 @@ cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg 
     const int block = cfg.block_size;
     const int ng = min(W.n_geoms, cfg.max_smem_geoms);
     const size_t smem = loop_smem(ng, block, S);
-    {
+    if (cfg.kernel == kKernelWave) {
+        cudaError_t e = launch_transport_wave(W, O, cfg, st);
+        if (e != cudaSuccess) return e;
+    } else {
         cudaError_t e = cudaFuncSetAttribute(k_transport_loop<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;

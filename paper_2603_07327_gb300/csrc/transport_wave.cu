@@ -1,0 +1,250 @@
+// transport_wave.cu -- wavefront transport kernel with warp-ballot regrouping.
+//
+// Each warp keeps a pool of 64 history slots in shared memory (structure of
+// arrays, one 32-bit word per field and slot).  Every iteration the warp
+//   1. refills idle slots with new history ids from the chunked work queue,
+//   2. ballots the phase of all 64 slots (decay, phantom step, flight, panel
+//      step) and picks the most populated phase,
+//   3. maps its 32 lanes onto the slots in that phase (__fns over the ballot
+//      masks), so every lane runs the same event code,
+//   4. runs up to `compact_every` events of that phase per lane, stores the
+//      state back, and emits the singles of histories that finished.
+// The events are the ones of the per-lane kernel (transport.cuh), so the two
+// kernels produce the same histories bit for bit.
+#include "internal.h"
+#include "transport.cuh"
+
+namespace gpet {
+
+constexpr int kWaveWarps = 4;           // warps per CTA
+constexpr int kPool = 64;               // slots per warp
+constexpr int kWaveS = 6;               // singles-list entries per history (overflow -> redo kernel)
+constexpr int kWords = 23;              // 32-bit words of state per slot
+
+// shared-memory footprint of one warp's pool
+struct WarpPool {
+    uint32_t st[kWords][kPool];
+    uint32_t sl_unit[kWaveS * kPool];
+    float sl_e[kWaveS * kPool];
+    uint32_t sl_dt[kWaveS * kPool];
+};
+
+enum : int {
+    kWh0 = 0, kWh1, kWt0, kWt1, kWx, kWy, kWz, kWdx, kWdy, kWdz, kWx0, kWy0, kWz0, kWox, kWoy, kWoz, kWE, kWpath,
+    kWtrem, kWjob, kWpack, kWsteps
+};
+
+__device__ __forceinline__ uint32_t pool_phase(const WarpPool &P, int q) { return (P.st[kWpack][q] >> 16) & 7u; }
+
+__device__ __forceinline__ void pool_set_phase(WarpPool &P, int q, uint32_t ph) {
+    P.st[kWpack][q] = (P.st[kWpack][q] & ~(7u << 16)) | (ph << 16);
+}
+
+// packed word: [0:7) panel+1, [7:14) last+1, [14] gamma, [16:19) phase, [19:24) nsing, [24] ovf
+__device__ __forceinline__ void pool_load(const WarpPool &P, int q, PState &s) {
+    s.h = ((uint64_t)P.st[kWh1][q] << 32) | P.st[kWh0][q];
+    s.t0 = ((uint64_t)P.st[kWt1][q] << 32) | P.st[kWt0][q];
+    s.x = __uint_as_float(P.st[kWx][q]);
+    s.y = __uint_as_float(P.st[kWy][q]);
+    s.z = __uint_as_float(P.st[kWz][q]);
+    s.dx = __uint_as_float(P.st[kWdx][q]);
+    s.dy = __uint_as_float(P.st[kWdy][q]);
+    s.dz = __uint_as_float(P.st[kWdz][q]);
+    s.x0 = __uint_as_float(P.st[kWx0][q]);
+    s.y0 = __uint_as_float(P.st[kWy0][q]);
+    s.z0 = __uint_as_float(P.st[kWz0][q]);
+    s.ox = __uint_as_float(P.st[kWox][q]);
+    s.oy = __uint_as_float(P.st[kWoy][q]);
+    s.oz = __uint_as_float(P.st[kWoz][q]);
+    s.E = __uint_as_float(P.st[kWE][q]);
+    s.path = __uint_as_float(P.st[kWpath][q]);
+    s.trem = __uint_as_float(P.st[kWtrem][q]);
+    s.job = (int32_t)P.st[kWjob][q];
+    const uint32_t pk = P.st[kWpack][q];
+    s.panel = (int32_t)(pk & 0x7Fu) - 1;
+    s.last = (int32_t)((pk >> 7) & 0x7Fu) - 1;
+    s.gamma = (pk >> 14) & 1u;
+    s.phase = (pk >> 16) & 7u;
+    s.nsing = (pk >> 19) & 31u;
+    s.ovf = (pk >> 24) & 1u;
+    const uint32_t sw = P.st[kWsteps][q];
+    s.sph = sw & 0xFFFFu;
+    s.sdet = sw >> 16;
+}
+
+__device__ __forceinline__ void pool_store(WarpPool &P, int q, const PState &s) {
+    P.st[kWh0][q] = (uint32_t)s.h;
+    P.st[kWh1][q] = (uint32_t)(s.h >> 32);
+    P.st[kWt0][q] = (uint32_t)s.t0;
+    P.st[kWt1][q] = (uint32_t)(s.t0 >> 32);
+    P.st[kWx][q] = __float_as_uint(s.x);
+    P.st[kWy][q] = __float_as_uint(s.y);
+    P.st[kWz][q] = __float_as_uint(s.z);
+    P.st[kWdx][q] = __float_as_uint(s.dx);
+    P.st[kWdy][q] = __float_as_uint(s.dy);
+    P.st[kWdz][q] = __float_as_uint(s.dz);
+    P.st[kWx0][q] = __float_as_uint(s.x0);
+    P.st[kWy0][q] = __float_as_uint(s.y0);
+    P.st[kWz0][q] = __float_as_uint(s.z0);
+    P.st[kWox][q] = __float_as_uint(s.ox);
+    P.st[kWoy][q] = __float_as_uint(s.oy);
+    P.st[kWoz][q] = __float_as_uint(s.oz);
+    P.st[kWE][q] = __float_as_uint(s.E);
+    P.st[kWpath][q] = __float_as_uint(s.path);
+    P.st[kWtrem][q] = __float_as_uint(s.trem);
+    P.st[kWjob][q] = (uint32_t)s.job;
+    P.st[kWpack][q] = (uint32_t)(s.panel + 1) | ((uint32_t)(s.last + 1) << 7) | (s.gamma << 14) | (s.phase << 16) |
+                      (s.nsing << 19) | (s.ovf << 24);
+    P.st[kWsteps][q] = (s.sph & 0xFFFFu) | (s.sdet << 16);
+}
+
+// warp-wide refill of the idle slots of one half of the pool (see transport.cu)
+__device__ void warp_refill_wave(const WorkDev &W, uint32_t need, uint64_t &pool_next, uint64_t &pool_end,
+                                 int &pool_job, bool &exhausted, bool &got, uint64_t &h, int &job) {
+    const int lane = threadIdx.x & 31;
+    got = false;
+    while (need && !exhausted) {
+        const uint64_t avail = pool_end - pool_next;
+        if (avail == 0) {
+            unsigned long long c = 0;
+            if (lane == 0) c = atomicAdd(W.next_chunk, 1ull);
+            c = __shfl_sync(kFullMask, c, 0);
+            if (c >= W.total_chunks) {
+                exhausted = true;
+                break;
+            }
+            int lo = 0, hi = W.n_jobs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (W.chunk_start[mid] <= c) lo = mid; else hi = mid - 1;
+            }
+            pool_job = lo;
+            const uint64_t h0 = (uint64_t)(c - W.chunk_start[lo]) * W.chunk_size;
+            pool_next = h0;
+            pool_end = min(h0 + (uint64_t)W.chunk_size, W.jobs[lo].n_decays);
+            continue;
+        }
+        const uint32_t cnt = (uint32_t)__popc(need);
+        const uint32_t take = avail < cnt ? (uint32_t)avail : cnt;
+        const uint32_t rank = (uint32_t)__popc(need & lanemask_lt());
+        if (((need >> lane) & 1u) && rank < take) {
+            got = true;
+            h = pool_next + rank;
+            job = pool_job;
+        }
+        pool_next += take;
+        for (uint32_t i = 0; i < take; ++i) need &= need - 1u;
+    }
+}
+
+__global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, OutDev O, int ng_smem, int repeat) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    GeomDev *sgeom = reinterpret_cast<GeomDev *>(smem);
+    WarpPool *pools = reinterpret_cast<WarpPool *>(sgeom + ng_smem);
+    stage_geometry(W, sgeom, ng_smem);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WarpPool &P = pools[wid];
+    P.st[kWpack][lane] = 0;        // phase idle
+    P.st[kWpack][lane + 32] = 0;
+    __syncthreads();
+
+    Counters cnt = {0, 0, 0, 0, 0, 0};
+    uint64_t pool_next = 0, pool_end = 0;
+    int pool_job = 0;
+    bool exhausted = false;
+    int status = kStatusOk;
+
+    for (;;) {
+        // 1. refill idle slots (two halves of 32)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int q = half * 32 + lane;
+            const uint32_t need = __ballot_sync(kFullMask, pool_phase(P, q) == kPhIdle);
+            if (need && !exhausted) {
+                bool got;
+                uint64_t h = 0;
+                int job = 0;
+                warp_refill_wave(W, need, pool_next, pool_end, pool_job, exhausted, got, h, job);
+                if (got) {
+                    P.st[kWh0][q] = (uint32_t)h;
+                    P.st[kWh1][q] = (uint32_t)(h >> 32);
+                    P.st[kWjob][q] = (uint32_t)job;
+                    P.st[kWpack][q] = (uint32_t)kPhSource << 16;
+                }
+            }
+        }
+        __syncwarp();
+        // 2. phase census over the 64 slots
+        const uint32_t ph0 = pool_phase(P, lane), ph1 = pool_phase(P, lane + 32);
+        uint32_t best_b0 = 0, best_b1 = 0;
+        int best_n = 0;
+        uint32_t best_p = kPhIdle;
+#pragma unroll
+        for (uint32_t p = kPhSource; p <= kPhPanel; ++p) {
+            const uint32_t b0 = __ballot_sync(kFullMask, ph0 == p), b1 = __ballot_sync(kFullMask, ph1 == p);
+            const int n = __popc(b0) + __popc(b1);
+            if (n > best_n) { best_n = n; best_b0 = b0; best_b1 = b1; best_p = p; }
+        }
+        if (best_n == 0) break;  // every slot idle after a refill: the queue is exhausted
+        // 3. lanes onto the slots of that phase
+        const int n0 = __popc(best_b0);
+        const bool active = lane < best_n;
+        int q = 0;
+        if (active) q = lane < n0 ? (int)__fns(best_b0, 0, lane + 1) : 32 + (int)__fns(best_b1, 0, lane - n0 + 1);
+        // 4. events
+        PState s;
+        s.phase = kPhIdle;
+        s.job = 0;
+        const SinglesList SL{P.sl_unit + q, P.sl_e + q, P.sl_dt + q, kPool};
+        if (active) {
+            pool_load(P, q, s);
+            const JobDev &J = W.jobs[s.job];
+            const GeomDev &g = J.geom < ng_smem ? sgeom[J.geom] : W.geoms[J.geom];
+            for (int r = 0; r < repeat && s.phase == best_p; ++r) {
+                int st = kStatusOk;
+                switch (best_p) {
+                    case kPhSource: ev_source(J, s); break;
+                    case kPhPhantom: st = ev_phantom(J, W, s, cnt); break;
+                    case kPhFlight: ev_flight(J, g, s, cnt); break;
+                    case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, kWaveS, cnt); break;
+                    default: break;
+                }
+                if (st != kStatusOk) {
+                    status |= st;
+                    s.phase = kPhIdle;
+                }
+            }
+        }
+        __syncwarp();
+        const bool fin = active && s.phase == kPhFinish;
+        if (__any_sync(kFullMask, fin)) {
+            ev_finish(W.jobs, W.geoms, O, s, fin, SL, kFullMask);
+            if (fin) s.phase = kPhIdle;
+        }
+        if (active) pool_store(P, q, s);
+        __syncwarp();
+    }
+    // flush counters (all lanes converged here)
+    const uint32_t v[6] = {cnt.det_steps, cnt.flights, cnt.trials, cnt.entered, cnt.ph_steps, cnt.hits};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const uint32_t x = __reduce_add_sync(kFullMask, v[i]);
+        if (lane == 0 && x) atomicAdd(O.counters + i, (unsigned long long)x);
+    }
+    if (status) atomicOr(O.status, status);
+}
+
+cudaError_t launch_transport_wave(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
+    const int ng = min(W.n_geoms, cfg.max_smem_geoms);
+    const size_t smem = (size_t)ng * sizeof(GeomDev) + sizeof(WarpPool) * kWaveWarps;
+    cudaError_t e = cudaFuncSetAttribute(k_transport_wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_wave, kWaveWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    const int per_sm = max(1, occ);
+    k_transport_wave<<<cfg.sm_count * per_sm, kWaveWarps * 32, smem, st>>>(W, O, ng, max(1, cfg.compact_every));
+    return cudaGetLastError();
+}
+
+}  // namespace gpet

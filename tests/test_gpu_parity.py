@@ -41,7 +41,7 @@ def check_parity(G, oracle, res, orc, n, dg, min_hist_frac=0.9999):
     hc = PU.compare_hits(gh, oh, n)
     assert hc["frac_identical"] >= min_hist_frac, hc
     assert hc["max_rel_e"] <= PU.E_REL, hc
-    assert hc["max_pos"] <= PU.POS_ABS, {k: v for k, v in hc.items() if k != "bad"}
+    assert hc["max_pos"] <= PU.POS_ABS, "worst hits: " + repr(hc["worst_pos"]) + f" p99.9={hc['p999_pos']}"
     assert hc["max_dt"] <= PU.T_ABS, hc
     bad = hc["bad"]
     gs = res.singles()
@@ -84,14 +84,46 @@ CASES = {
 }
 
 
+CASES["near_ring_offcentre"] = (lambda: W.config2_scanner("B"), lambda: W.point_source((45.0, 10.0, -12.0)), None,
+                                100_000, 21)
+
+KERNELS = {"loop": 1, "wave": 2}
+
+
+@pytest.mark.parametrize("kernel", sorted(KERNELS))
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_parity_small(G, oracle, name):
+def test_parity_small(G, oracle, name, kernel):
     mk_sc, mk_src, mk_ph, n, seed = CASES[name]
     sc, src = mk_sc(), mk_src()
     ph = mk_ph() if mk_ph else None
     dg = W.digitizer()
-    res, orc = run_both(G, oracle, sc, src, dg, n, seed, phantom=ph)
+    res, orc = run_both(G, oracle, sc, src, dg, n, seed, phantom=ph, kernel=KERNELS[kernel])
     check_parity(G, oracle, res, orc, n, dg)
+
+
+@pytest.mark.parametrize("compact_every", [1, 4])
+def test_kernels_agree_bit_for_bit(G, compact_every):
+    """The per-lane loop and the regrouping wavefront run the same events, so
+    hits, singles, coincidences and tallies are identical (as sets)."""
+    ph = W.hot_rod_phantom()
+    for sc, src, n in ((W.config2_scanner("B"), W.point_source((3.0, -2.0, 11.0)), 300_000),
+                       (W.config3_scanner(), W.phantom_source(), 60_000)):
+        out = []
+        for k in (1, 2):
+            r = G.simulate(sc, src, W.digitizer(), n, 77, phantom=ph if src["kind"] == 1 else None, keep_hits=True,
+                           kernel=k, compact_every=compact_every)
+            h = PU.gpu_hits_table(r.hits())
+            s = r.singles()
+            order = np.lexsort((s["unit"], s["h"]))
+            a, b = r.coincidences()
+            coinc = PU.coincidence_set(s["h"], s["unit"], a, b)
+            out.append((h, {k2: v[order] for k2, v in s.items()}, coinc, r.tallies()))
+        (h1, s1, c1, t1), (h2, s2, c2, t2) = out
+        assert np.array_equal(h1, h2)
+        for key in s1:
+            assert np.array_equal(s1[key], s2[key]), key
+        assert c1 == c2
+        assert np.array_equal(t1[0], t2[0]) and np.array_equal(t1[1], t2[1])
 
 
 def test_module_and_panel_readout(G, oracle):
@@ -134,14 +166,17 @@ def test_capacity_overflow_retry(G, oracle):
 
 
 def test_singles_list_overflow_is_resimulated(G, oracle):
-    """Very fine crystals: many histories touch more than 8 crystals; those are
-    re-simulated by the fallback kernel and must still match the oracle."""
-    sc = W.scanner(8, 40.0, [W.layer(64, 64, 0.2, 0.02, 10.0)])
+    """Fine crystals in a thick, nearly pure Compton scatterer: ~2.5 % of the
+    histories touch more than 8 crystals; those are re-simulated by the
+    fallback kernel and must still match the oracle."""
+    mats = [W.AIR, dict(mu_total_511_cm=2.0, photo_frac_511=0.01, electron_density_cm3=0.0)]
+    sc = W.scanner(8, 40.0, [W.layer(64, 64, 0.3, 0.02, 40.0)], materials=mats)
     dg = W.digitizer(e_lo=0.0, e_hi=5000.0)
-    res, orc = run_both(G, oracle, sc, W.point_source(), dg, 50_000, 4)
-    per = np.bincount(np.unique(orc["hits"]["h"].astype(np.int64) * 10**6 + orc["hits"]["crystal"]) // 10**6)
-    assert (per > 8).sum() >= 5  # the fallback path is exercised
-    check_parity(G, oracle, res, orc, 50_000, dg)
+    n = 20_000
+    res, orc = run_both(G, oracle, sc, W.point_source(), dg, n, 4)
+    per = np.bincount(np.unique(orc["hits"]["h"].astype(np.int64) * 10**7 + orc["hits"]["crystal"]) // 10**7)
+    assert (per > 8).sum() >= 100  # the fallback path is exercised
+    check_parity(G, oracle, res, orc, n, dg)
 
 
 def test_full_size_sampled_histories(G, oracle):
