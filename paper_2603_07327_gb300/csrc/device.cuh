@@ -178,7 +178,9 @@ __device__ __forceinline__ void rotate_dir(float &a, float &b, float &c, float o
     float sp, cp;
     sincospif(2.0f * u_phi, &sp, &cp);
     if (fabsf(c) < 0.99999f) {
-        const float q = sqrtf(fmaf(-c, c, 1.0f));
+        // transverse norm from the transverse components (= sqrt(1 - c^2) for a
+        // unit vector, without the cancellation of 1 - c^2 near the axis)
+        const float q = sqrtf(fmaf(a, a, b * b));
         const float iq = 1.0f / q;
         const float na = a * ct + st * (a * c * cp - b * sp) * iq;
         const float nb = b * ct + st * (b * c * cp + a * sp) * iq;
@@ -283,6 +285,24 @@ __device__ __forceinline__ void panel_slab(const GeomDev &g, int k, float x, flo
     }
 }
 
+// atan2 from the odd polynomial of Abramowitz & Stegun 4.4.47 (|error| <= 1e-5
+// rad on [-1, 1]) with octant reduction; used only to pick candidate panels,
+// where a 1e-3 rad margin absorbs its error
+__device__ __forceinline__ float atan2_as(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+    const float t2 = t * t;
+    float r = fmaf(t2, 0.0208351f, -0.0851330f);
+    r = fmaf(t2, r, 0.1801410f);
+    r = fmaf(t2, r, -0.3302995f);
+    r = fmaf(t2, r, 0.9998660f);
+    r *= t;
+    if (ay > ax) r = 1.57079633f - r;
+    if (x < 0.0f) r = 3.14159265f - r;
+    return y < 0.0f ? -r : r;
+}
+
 // Line-plane flight (Sec. 2.1): nearest panel entered along (x, d), skipping
 // `skip`.  A ray that starts inside the circle of radius R (every inner face
 // is tangent to it) crosses the annulus holding all panel boxes exactly once,
@@ -305,10 +325,18 @@ __device__ __forceinline__ int flight(const GeomDev &g, float x, float y, float 
         // exit distances of the circles R and R_out (stable roots, c0 < R^2)
         const float d1 = g.R2 - c0, d2 = g.rout2 - c0;
         const float s1 = sqrtf(fmaf(b, b, a * d1)), s2 = sqrtf(fmaf(b, b, a * d2));
-        const float t1 = b > 0.0f ? d1 / (b + s1) : (s1 - b) / a;
-        const float t2 = b > 0.0f ? d2 / (b + s2) : (s2 - b) / a;
-        const float p1 = atan2f(fmaf(t1, dy, y), fmaf(t1, dx, x)) - g.phi0;
-        float p2 = atan2f(fmaf(t2, dy, y), fmaf(t2, dx, x)) - g.phi0;
+        const float t1 = b > 0.0f ? __fdividef(d1, b + s1) : __fdividef(s1 - b, a);
+        // axial early out: beyond the panels' axial extent when it reaches the
+        // annulus and moving away (1e-3 mm margin)
+        const float z1 = fmaf(t1, dz, z);
+        if ((z1 > g.half_v + 1e-3f && dz >= 0.0f) || (z1 < -g.half_v - 1e-3f && dz <= 0.0f)) {
+            t_in = bi;
+            t_out = bo;
+            return -1;
+        }
+        const float t2 = b > 0.0f ? __fdividef(d2, b + s2) : __fdividef(s2 - b, a);
+        const float p1 = atan2_as(fmaf(t1, dy, y), fmaf(t1, dx, x)) - g.phi0;
+        float p2 = atan2_as(fmaf(t2, dy, y), fmaf(t2, dx, x)) - g.phi0;
         // unwrap p2 next to p1 (the swept interval is shorter than pi)
         if (p2 - p1 > 3.14159265f) p2 -= 6.28318531f;
         else if (p1 - p2 > 3.14159265f) p2 += 6.28318531f;

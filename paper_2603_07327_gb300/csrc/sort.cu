@@ -50,20 +50,25 @@ __global__ void __launch_bounds__(kSortThreads) k_make_keys(SortDev S) {
     }
 }
 
-// which passes run, and which buffer each one reads
-__global__ void k_plan(SortDev S) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// which passes run, and which buffer each one reads (one warp per pass)
+__global__ void __launch_bounds__(kPasses * 32) k_plan(SortDev S) {
+    __shared__ int active[kPasses];
+    const int p = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long n = sort_n(S);
-    int cur = 0;
-    for (int p = 0; p < kPasses; ++p) {
-        uint32_t mx = 0;
-        for (int d = 0; d < 256; ++d) mx = max(mx, S.ghist[p * 256 + d]);
-        const int active = (n > 1 && (unsigned long long)mx < n) ? 1 : 0;
-        S.plan[p] = active;
-        S.plan[kPasses + p] = cur;
-        if (active) cur ^= 1;
+    uint32_t mx = 0;
+    for (int d = lane; d < 256; d += 32) mx = max(mx, S.ghist[p * 256 + d]);
+    mx = __reduce_max_sync(kFullMask, mx);
+    if (lane == 0) active[p] = (n > 1 && (unsigned long long)mx < n) ? 1 : 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int cur = 0;
+        for (int q = 0; q < kPasses; ++q) {
+            S.plan[q] = active[q];
+            S.plan[kPasses + q] = cur;
+            if (active[q]) cur ^= 1;
+        }
+        S.plan[2 * kPasses] = cur;  // buffer holding the sorted result
     }
-    S.plan[2 * kPasses] = cur;  // buffer holding the sorted result
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_tile_hist(SortDev S, int p) {
@@ -300,7 +305,7 @@ cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const Coi
     if (e != cudaSuccess) return e;
     const int grid = sm_count * 4;
     k_make_keys<<<grid, kSortThreads, 0, st>>>(S);
-    k_plan<<<1, 32, 0, st>>>(S);
+    k_plan<<<1, kPasses * 32, 0, st>>>(S);
     for (int p = 0; p < kPasses; ++p) {
         const int tg = (int)(S.max_tiles < (unsigned long long)sm_count * 8 ? S.max_tiles : (unsigned long long)sm_count * 8);
         k_tile_hist<<<tg, kSortThreads, 0, st>>>(S, p);
