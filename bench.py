@@ -185,13 +185,25 @@ def run_ours(args):
     stream = torch.cuda.current_stream().cuda_stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    def step(collect=None):
+    def plain_step(collect=None):
         for j in jobs:
             r = scanners[j["geometry"]].simulate(j["source"], dg, j["n"], j["seed"], stream=stream,
                                                  kernel=args.kernel)
             if collect is not None:
                 collect.append(r.counts())
             r.free()
+
+    batch = None
+    if args.form == "batched":
+        batch = G.Batch([dict(scanner=scanners[j["geometry"]], source=j["source"], digitizer=dg, n_decays=j["n"],
+                              seed=j["seed"]) for j in jobs], stream=stream, kernel=args.kernel)
+
+    def step(collect=None):
+        if batch is None:
+            return plain_step(collect)
+        batch.run()
+        if collect is not None:
+            collect.append(batch.counts())
 
     for _ in range(args.warmup):
         step()
@@ -234,15 +246,20 @@ def run_ours(args):
                 peak_note="152 SMs x 128 FP32/INT lanes x 2070 MHz (recipe unit counts and max clock)",
                 transport_share=tr_ms / (tr_ms + dg_ms))
 
-    # end to end through the C ABI: host descriptors in, results to host memory
-    import numpy as np
+    # end to end through the C ABI: host descriptors in (one batch call over the
+    # sweep), coincidences, singles and tallies of every job copied to host memory
     e2e_t0 = time.perf_counter()
     d2h = 0
     h2d = 0
-    for j in jobs:
-        r = scanners[j["geometry"]].simulate(j["source"], dg, j["n"], j["seed"], stream=stream, kernel=args.kernel)
-        c = r.counts()
-        h2d += c["h2d_bytes"]
+    if args.form == "batched":
+        res = G.simulate_batch([dict(scanner=scanners[j["geometry"]], source=j["source"], digitizer=dg,
+                                     n_decays=j["n"], seed=j["seed"]) for j in jobs], stream=stream,
+                               kernel=args.kernel)
+    else:
+        res = [scanners[j["geometry"]].simulate(j["source"], dg, j["n"], j["seed"], stream=stream, kernel=args.kernel)
+               for j in jobs]
+    for r in res:
+        h2d = max(h2d, r.counts()["h2d_bytes"]) if args.form == "batched" else h2d + r.counts()["h2d_bytes"]
         for arr in (r.array(G.SINGLES_T_PS), r.array(G.SINGLES_UNIT), r.array(G.SINGLES_E), r.array(G.COINC_A),
                     r.array(G.COINC_B), r.array(G.TALLY_COUNT), r.array(G.TALLY_EFX)):
             d2h += arr.nbytes
@@ -259,7 +276,9 @@ def run_ours(args):
                 dtype="f32", data="synthetic",
                 config=dict(workload="sensitivity sweep, 12-panel ring R=55 mm, 1x4 modules of 20x20 LYSO at 1.0 mm, "
                                      "geometry A (10 mm) + B (2x5 mm, 0.05 mm reflector), 61 axial positions x 1e7 pairs",
-                            form="plain: one gpet_simulate per position", pairs_per_step=pairs_per_step,
+                            form=("batched: one persistent launch over all 122 positions, CUDA-graph replay"
+                                  if args.form == "batched" else "plain: one gpet_simulate per position"),
+                            pairs_per_step=pairs_per_step,
                             l2="flushed between steps (256 MB write)", kernel=args.kernel or "default",
                             parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
                 wall_s=wall, gpu_launches=None, roofline=roof, clocks=clk,
@@ -269,9 +288,22 @@ def run_ours(args):
                 per_step_counts=dict(hits=sum(c["hits"] for c in counts) // args.steps,
                                      singles=sum(c["singles"] for c in counts) // args.steps,
                                      coincidences=sum(c["coincidences"] for c in counts) // args.steps))
-    # kernels launched per simulate: transport + redo + sort chain (keys, plan, 8 x 3 passes, gather,
-    # flags, count, scan, write)
-    line["gpu_launches"] = len(jobs) * (2 + 2 + 8 * 3 + 1 + 4) * args.steps
+    # kernels per launch: transport + redo, keys, plan, 8 x 3 radix passes, gather, 4 coincidence
+    # kernels, job statistics
+    per_launch = 2 + 2 + 8 * 3 + 1 + 4 + 1
+    line["gpu_launches"] = per_launch * args.steps * (1 if args.form == "batched" else len(jobs))
+    if args.form == "batched" and args.compare_plain:
+        # the plain per-position form on the same sweep, for the batched-vs-plain metric
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        plain_step()
+        torch.cuda.synchronize()
+        t0.record()
+        plain_step()
+        t1.record()
+        t1.synchronize()
+        line["plain_pairs_per_s"] = pairs_per_step / (t0.elapsed_time(t1) / 1000.0)
+        line["batched_over_plain"] = value / line["plain_pairs_per_s"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, _, _ = cpu_baseline()
         line["cpu_baseline"] = cb
@@ -289,6 +321,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--form", default="batched", choices=["batched", "plain"])
+    ap.add_argument("--compare-plain", action="store_true", default=True)
+    ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
     ap.add_argument("--pairs", type=int, default=PAIRS_PER_POSITION)
     ap.add_argument("--positions", type=int, default=N_POSITIONS)
     ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per transport launch from ncu")

@@ -195,7 +195,10 @@ typedef struct {
 } gpet_counts;
 int gpet_result_counts(const gpet_result *r, gpet_counts *out);
 
-/* Result arrays.  Singles are sorted by time (ties in any order). */
+/* Result arrays.  Singles are sorted by time (ties in any order).
+ * Coincidence indices copied by gpet_result_copy number the result's own
+ * singles; through gpet_result_device_ptr of a batch view they count from the
+ * first single of the whole batch. */
 enum {
     GPET_SINGLES_T_PS = 0,      /* uint64 [singles]   time of the earliest hit */
     GPET_SINGLES_H = 1,         /* uint64 [singles]   history id               */
@@ -225,6 +228,39 @@ int gpet_result_copy(const gpet_result *r, int32_t which, void *dst, size_t cap_
 /* Device pointer of one result array (valid until gpet_result_free), or NULL. */
 const void *gpet_result_device_ptr(const gpet_result *r, int32_t which);
 void gpet_result_free(gpet_result *r);
+
+/* ------------------------------------------------------------------------ */
+/* batched form: many designs and sources in one persistent launch           */
+/* ------------------------------------------------------------------------ */
+
+/* A batch runs n_jobs independent simulations -- job j is (scanners[j],
+ * sources[j], digitizers[j], n_decays[j], seeds[j]) exactly as gpet_simulate
+ * would run it -- in one persistent transport launch over a shared work
+ * queue, one time sort segmented by job and one coincidence pass.  The
+ * enqueue is captured into a CUDA graph at creation and replayed by
+ * gpet_batch_run.  A job's results are identical to gpet_simulate's for the
+ * same inputs (every random number is addressed by seed and history id).
+ * All arrays: host, n_jobs entries, copied.  Scanners must outlive the batch.
+ * n_jobs <= 4095.  opt->stream NULL: the batch creates its own stream. */
+typedef struct gpet_batch gpet_batch;
+int gpet_batch_create(int32_t n_jobs, gpet_scanner *const *scanners, const gpet_source *sources,
+                      const gpet_digitizer *digitizers, const uint64_t *n_decays, const uint64_t *seeds,
+                      const gpet_options *opt, gpet_batch **out);
+/* Replay the captured graph (the same simulations again) and synchronise. */
+int gpet_batch_run(gpet_batch *b);
+int gpet_batch_jobs(const gpet_batch *b, int32_t *n_jobs);
+/* Counts over the whole batch (event counters and stage times are batch-wide). */
+int gpet_batch_counts(const gpet_batch *b, gpet_counts *total);
+/* A view of job `job` of the last run: its singles, coincidences (indices
+ * into its own singles) and tallies.  Free with gpet_result_free; the view
+ * keeps the batch's device memory alive, and a later gpet_batch_run
+ * overwrites it with identical values. */
+int gpet_batch_result(const gpet_batch *b, int32_t job, gpet_result **out);
+void gpet_batch_destroy(gpet_batch *b);
+/* One-shot batch without a graph: outs[j] receives job j's result. */
+int gpet_simulate_batch(int32_t n_jobs, gpet_scanner *const *scanners, const gpet_source *sources,
+                        const gpet_digitizer *digitizers, const uint64_t *n_decays, const uint64_t *seeds,
+                        const gpet_options *opt, gpet_result **outs);
 
 /* Thread-local text of the last error (never NULL). */
 const char *gpet_last_error(void);

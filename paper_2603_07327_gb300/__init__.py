@@ -95,6 +95,16 @@ SIGNATURES = {
     "gpet_result_copy": (C.c_int, [_P, C.c_int32, _P, C.c_size_t]),
     "gpet_result_device_ptr": (_P, [_P, C.c_int32]),
     "gpet_result_free": (None, [_P]),
+    "gpet_batch_create": (C.c_int, [C.c_int32, C.POINTER(_P), C.POINTER(Source), C.POINTER(Digitizer),
+                                    C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(Options), C.POINTER(_P)]),
+    "gpet_batch_run": (C.c_int, [_P]),
+    "gpet_batch_jobs": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "gpet_batch_counts": (C.c_int, [_P, C.POINTER(Counts)]),
+    "gpet_batch_result": (C.c_int, [_P, C.c_int32, C.POINTER(_P)]),
+    "gpet_batch_destroy": (None, [_P]),
+    "gpet_simulate_batch": (C.c_int, [C.c_int32, C.POINTER(_P), C.POINTER(Source), C.POINTER(Digitizer),
+                                      C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(Options),
+                                      C.POINTER(_P)]),
     "gpet_last_error": (C.c_char_p, []),
     "gpet_version": (C.c_char_p, []),
 }
@@ -273,3 +283,62 @@ def simulate(scanner: dict, source: dict, digitizer: dict, n_decays: int, seed: 
         return sc.simulate(source, digitizer, n_decays, seed, **opts)
     finally:
         sc.close()
+
+
+def _job_arrays(jobs):
+    n = len(jobs)
+    scs = (C.c_void_p * n)(*[j["scanner"]._h.value for j in jobs])
+    srcs = (Source * n)(*[source_struct(j["source"]) for j in jobs])
+    dgs = (Digitizer * n)(*[digitizer_struct(j["digitizer"]) for j in jobs])
+    nd = (C.c_uint64 * n)(*[int(j["n_decays"]) for j in jobs])
+    sd = (C.c_uint64 * n)(*[int(j["seed"]) for j in jobs])
+    return n, scs, srcs, dgs, nd, sd
+
+
+class Batch:
+    """gpet_batch handle: jobs = list of dicts with keys scanner (a Scanner),
+    source, digitizer, n_decays, seed.  Created once (first run + graph
+    capture), replayed with run()."""
+
+    def __init__(self, jobs, **opts):
+        L = load()
+        self._jobs = jobs                      # keeps the Scanner handles alive
+        n, scs, srcs, dgs, nd, sd = _job_arrays(jobs)
+        self._h = C.c_void_p()
+        o = options_struct(**opts)
+        _check(L.gpet_batch_create(n, scs, srcs, dgs, nd, sd, C.byref(o), C.byref(self._h)))
+        self.n = n
+
+    def run(self):
+        _check(load().gpet_batch_run(self._h))
+
+    def counts(self) -> dict:
+        c = Counts()
+        _check(load().gpet_batch_counts(self._h, C.byref(c)))
+        return {k: getattr(c, k) for k, _ in Counts._fields_}
+
+    def result(self, job: int) -> Result:
+        out = C.c_void_p()
+        _check(load().gpet_batch_result(self._h, int(job), C.byref(out)))
+        return Result(out)
+
+    def close(self):
+        if self._h:
+            load().gpet_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def simulate_batch(jobs, **opts):
+    """One-shot batch (no graph): returns one Result per job."""
+    L = load()
+    n, scs, srcs, dgs, nd, sd = _job_arrays(jobs)
+    outs = (C.c_void_p * n)()
+    o = options_struct(**opts)
+    _check(L.gpet_simulate_batch(n, scs, srcs, dgs, nd, sd, C.byref(o), outs))
+    return [Result(C.c_void_p(outs[i])) for i in range(n)]

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -79,6 +80,11 @@ struct Run {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // before transport, after transport, after digitizer
     float transport_ms = 0.f, digitizer_ms = 0.f;
     uint64_t h2d_bytes = 0;
+    // per-job segments of the outputs (device, then host copies after collect)
+    JobStatsDev JS{};
+    std::vector<unsigned long long> s_off, c_off, job_hits;
+    bool own_stream = false;
+    ~Run();
 };
 
 int run_plan(Run &R);                  // allocate the arena, upload jobs and geometry
@@ -89,9 +95,24 @@ int run_default_cfg(Run &R, const gpet_options *opt);
 
 }  // namespace gpet
 
+// A result views one job of a run: the whole run for gpet_simulate, one job
+// of a batch for gpet_batch_result.  Runs are shared by their views.
 struct gpet_result {
-    gpet::Run run;
+    std::shared_ptr<gpet::Run> run;
     gpet_counts counts{};
-    int job = 0;                         // which job of the run this result views
-    bool owns_run = true;
+    int job = 0;
 };
+
+struct gpet_batch {
+    std::shared_ptr<gpet::Run> run;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uint64_t> n_decays;
+    std::vector<int64_t> n_crystals;
+    ~gpet_batch();
+};
+
+namespace gpet {
+void fill_counts(const Run &R, int job, uint64_t n_decays, int64_t n_crystals, gpet_counts *c);
+int run_with_retry(Run &R);            // plan + enqueue + collect, one exact-size re-run on overflow
+}

@@ -50,6 +50,15 @@ struct CoincDev {
     const uint64_t *window_ps;       // per job
 };
 
+struct JobStatsDev {
+    int n_jobs;
+    unsigned long long *s_off, *c_off;   // [n_jobs + 1]
+    unsigned long long *hits;            // [n_jobs]
+    const unsigned long long *tally_count;
+    const long long *tally_off, *tally_n; // [n_jobs]
+};
+
+cudaError_t launch_job_stats(const SinglesDev &s, const CoincDev &C, const JobStatsDev &J, cudaStream_t st);
 cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
 cudaError_t launch_transport_wave(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
 cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const CoincDev &C, int sm_count,

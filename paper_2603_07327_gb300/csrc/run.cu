@@ -122,6 +122,11 @@ int run_plan(Run &R) {
     cv.take(C.flag, cap);
     cv.take(C.tile_cnt, tiles);
     cv.take(C.a, cap / 2 + 1); cv.take(C.b, cap / 2 + 1);
+    // per-job statistics
+    JobStatsDev &JS = R.JS;
+    long long *d_toff, *d_tn;
+    cv.take(JS.s_off, nj + 1); cv.take(JS.c_off, nj + 1); cv.take(JS.hits, nj);
+    cv.take(d_toff, nj); cv.take(d_tn, nj);
     R.arena_bytes = align_up(cv.off, 256);
 
     cudaError_t e = cudaMallocAsync(&R.arena, R.arena_bytes, R.stream);
@@ -151,6 +156,11 @@ int run_plan(Run &R) {
     rebase(SD.t, base); rebase(SD.h, base); rebase(SD.unit, base); rebase(SD.panel, base); rebase(SD.job, base);
     rebase(SD.e, base); rebase(SD.eraw, base);
     rebase(C.flag, base); rebase(C.tile_cnt, base); rebase(C.a, base); rebase(C.b, base);
+    rebase(JS.s_off, base); rebase(JS.c_off, base); rebase(JS.hits, base); rebase(d_toff, base); rebase(d_tn, base);
+    JS.n_jobs = nj;
+    JS.tally_count = R.d_tally_count;
+    JS.tally_off = d_toff;
+    JS.tally_n = d_tn;
 
     // wire the structs
     for (int j = 0; j < nj; ++j) {
@@ -196,9 +206,12 @@ int run_plan(Run &R) {
                             cudaMemcpyHostToDevice, R.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(R.d_window, R.windows.data(), sizeof(uint64_t) * nj, cudaMemcpyHostToDevice, R.stream);
+    std::vector<long long> toff(R.tally_off.begin(), R.tally_off.end()), tn(R.job_crystals.begin(), R.job_crystals.end());
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_toff, toff.data(), sizeof(long long) * nj, cudaMemcpyHostToDevice, R.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tn, tn.data(), sizeof(long long) * nj, cudaMemcpyHostToDevice, R.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(R.stream);  // host vectors may change after return
     R.h2d_bytes = sizeof(JobDev) * nj + sizeof(GeomDev) * R.geoms.size() + sizeof(unsigned long long) * (nj + 1) +
-                  sizeof(uint64_t) * nj;
+                  sizeof(uint64_t) * nj + 2 * sizeof(long long) * nj;
     if (e != cudaSuccess) return gpet_cuda_fail(e, "upload of the job descriptors");
     return GPET_OK;
 }
@@ -215,13 +228,23 @@ int run_enqueue(Run &R) {
     if (e != cudaSuccess) return gpet_cuda_fail(e, "transport launch");
     e = cudaEventRecord(R.ev[1], R.stream);
     if (e == cudaSuccess) e = launch_sort_coinc(R.S, R.SD, R.C, R.cfg.sm_count, R.stream);
+    if (e == cudaSuccess) e = launch_job_stats(R.SD, R.C, R.JS, R.stream);
     if (e == cudaSuccess) e = cudaEventRecord(R.ev[2], R.stream);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "sort / coincidence launch");
     return GPET_OK;
 }
 
 int run_collect(Run &R) {
+    const size_t nj = R.jobs.size();
+    R.s_off.resize(nj + 1);
+    R.c_off.resize(nj + 1);
+    R.job_hits.resize(nj);
     cudaError_t e = cudaMemcpyAsync(&R.h_hdr, R.d_hdr, sizeof(RunHeader), cudaMemcpyDeviceToHost, R.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(R.s_off.data(), R.JS.s_off, 8 * (nj + 1), cudaMemcpyDeviceToHost, R.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(R.c_off.data(), R.JS.c_off, 8 * (nj + 1), cudaMemcpyDeviceToHost, R.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.job_hits.data(), R.JS.hits, 8 * nj, cudaMemcpyDeviceToHost, R.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(R.stream);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "run read-back");
     if (R.ev[0] && cudaEventElapsedTime(&R.transport_ms, R.ev[0], R.ev[1]) != cudaSuccess) R.transport_ms = -1.f;
@@ -244,17 +267,41 @@ void run_release(Run &R) {
         if (e) { cudaEventDestroy(e); e = nullptr; }
 }
 
-}  // namespace gpet
+Run::~Run() {
+    run_release(*this);
+    if (own_stream && stream) {
+        cudaStreamSynchronize(stream);
+        cudaStreamDestroy(stream);
+    }
+}
 
-using namespace gpet;
+int run_with_retry(Run &R) {
+    int st = GPET_OK;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        st = run_plan(R);
+        if (st == GPET_OK) st = run_enqueue(R);
+        if (st == GPET_OK) st = run_collect(R);
+        if (st == GPET_ERR_OVERFLOW && attempt == 0 && !(R.h_hdr.status & kStatusOverflow)) {
+            // the device counters kept counting past the capacities: re-run with exact sizes
+            R.caps.singles = std::max<uint64_t>(R.caps.singles, R.h_hdr.n_singles + 1024);
+            R.caps.hits = std::max<uint64_t>(R.caps.hits, R.h_hdr.n_hits + 1024);
+            R.caps.ovf = std::max<uint64_t>(R.caps.ovf, R.h_hdr.n_ovf + 1024);
+            run_release(R);
+            continue;
+        }
+        break;
+    }
+    if (st != GPET_OK) run_release(R);
+    return st;
+}
 
-static void fill_counts(const Run &R, int job, uint64_t n_decays, int64_t n_crystals, gpet_counts *c) {
+void fill_counts(const Run &R, int job, uint64_t n_decays, int64_t n_crystals, gpet_counts *c) {
     const RunHeader &H = R.h_hdr;
     std::memset(c, 0, sizeof(*c));
     c->n_decays = n_decays;
-    c->hits = H.counters[5];
-    c->singles = H.n_sorted;
-    c->coincidences = H.n_coinc;
+    c->hits = R.job_hits.empty() ? H.counters[5] : R.job_hits[job];
+    c->singles = R.s_off.empty() ? H.n_sorted : R.s_off[job + 1] - R.s_off[job];
+    c->coincidences = R.c_off.empty() ? H.n_coinc : R.c_off[job + 1] - R.c_off[job];
     c->n_crystals = n_crystals;
     c->det_steps = H.counters[0];
     c->flights = H.counters[1];
@@ -265,8 +312,11 @@ static void fill_counts(const Run &R, int job, uint64_t n_decays, int64_t n_crys
     c->transport_ms = R.transport_ms;
     c->digitizer_ms = R.digitizer_ms;
     c->h2d_bytes = R.h2d_bytes;
-    (void)job;
 }
+
+}  // namespace gpet
+
+using namespace gpet;
 
 extern "C" int gpet_simulate(gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg, uint64_t n_decays,
                              uint64_t seed, const gpet_options *opt, gpet_result **out) {
@@ -276,7 +326,8 @@ extern "C" int gpet_simulate(gpet_scanner *sc, const gpet_source *src, const gpe
     if (st != GPET_OK) return st;
     gpet_result *res = new (std::nothrow) gpet_result();
     if (!res) return gpet_fail(GPET_ERR_OOM, "host allocation of the result failed");
-    Run &R = res->run;
+    res->run = std::make_shared<Run>();
+    Run &R = *res->run;
     st = run_default_cfg(R, opt);
     if (st != GPET_OK) { delete res; return st; }
     R.jobs = {J};
@@ -286,22 +337,8 @@ extern "C" int gpet_simulate(gpet_scanner *sc, const gpet_source *src, const gpe
     R.caps.singles = std::max<uint64_t>(65536, n_decays * 6 / 10);
     R.caps.hits = R.keep_hits ? std::max<uint64_t>(65536, n_decays * 5 / 2) : 0;
     R.caps.ovf = std::max<uint64_t>(4096, n_decays / 256);
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        st = run_plan(R);
-        if (st == GPET_OK) st = run_enqueue(R);
-        if (st == GPET_OK) st = run_collect(R);
-        if (st == GPET_ERR_OVERFLOW && attempt == 0 && !(R.h_hdr.status & kStatusOverflow)) {
-            // the counters kept counting past the capacities: re-run with exact sizes
-            R.caps.singles = std::max<uint64_t>(R.caps.singles, R.h_hdr.n_singles + 1024);
-            R.caps.hits = std::max<uint64_t>(R.caps.hits, R.h_hdr.n_hits + 1024);
-            R.caps.ovf = std::max<uint64_t>(R.caps.ovf, R.h_hdr.n_ovf + 1024);
-            run_release(R);
-            continue;
-        }
-        break;
-    }
+    st = run_with_retry(R);
     if (st != GPET_OK) {
-        run_release(R);
         delete res;
         return st;
     }
@@ -322,19 +359,19 @@ struct ArrayView {
 };
 
 static int result_array(const gpet_result *r, int32_t which, ArrayView &v) {
-    const Run &R = r->run;
-    const uint64_t ns = R.h_hdr.n_sorted, nc = R.h_hdr.n_coinc;
-    const uint64_t nh = std::min<uint64_t>(R.h_hdr.n_hits, R.O.hit_cap);
+    const Run &R = *r->run;
     const int j = r->job;
+    const uint64_t s0 = R.s_off[j], ns = R.s_off[j + 1] - s0, c0 = R.c_off[j], nc = R.c_off[j + 1] - c0;
+    const uint64_t nh = std::min<uint64_t>(R.h_hdr.n_hits, R.O.hit_cap);
     switch (which) {
-        case GPET_SINGLES_T_PS: v = {R.SD.t, ns * 8}; break;
-        case GPET_SINGLES_H: v = {R.SD.h, ns * 8}; break;
-        case GPET_SINGLES_UNIT: v = {R.SD.unit, ns * 4}; break;
-        case GPET_SINGLES_PANEL: v = {R.SD.panel, ns * 4}; break;
-        case GPET_SINGLES_E: v = {R.SD.e, ns * 4}; break;
-        case GPET_SINGLES_E_RAW: v = {R.SD.eraw, ns * 4}; break;
-        case GPET_COINC_A: v = {R.C.a, nc * 4}; break;
-        case GPET_COINC_B: v = {R.C.b, nc * 4}; break;
+        case GPET_SINGLES_T_PS: v = {R.SD.t + s0, ns * 8}; break;
+        case GPET_SINGLES_H: v = {R.SD.h + s0, ns * 8}; break;
+        case GPET_SINGLES_UNIT: v = {R.SD.unit + s0, ns * 4}; break;
+        case GPET_SINGLES_PANEL: v = {R.SD.panel + s0, ns * 4}; break;
+        case GPET_SINGLES_E: v = {R.SD.e + s0, ns * 4}; break;
+        case GPET_SINGLES_E_RAW: v = {R.SD.eraw + s0, ns * 4}; break;
+        case GPET_COINC_A: v = {R.C.a + c0, nc * 4}; break;
+        case GPET_COINC_B: v = {R.C.b + c0, nc * 4}; break;
         case GPET_TALLY_COUNT: v = {R.d_tally_count + R.tally_off[j], (size_t)R.job_crystals[j] * 8}; break;
         case GPET_TALLY_EFX: v = {R.d_tally_efx + R.tally_off[j], (size_t)R.job_crystals[j] * 8}; break;
         case GPET_HITS_H: v = {R.O.hit_h, nh * 8}; break;
@@ -348,6 +385,8 @@ static int result_array(const gpet_result *r, int32_t which, ArrayView &v) {
     }
     if (which >= GPET_HITS_H && !R.keep_hits)
         return gpet_fail(GPET_ERR_INVALID_ARG, "hits were not kept (gpet_options.keep_hits = 0)");
+    if (which >= GPET_HITS_H && R.jobs.size() > 1)
+        return gpet_fail(GPET_ERR_INVALID_ARG, "hit lists are kept for single-job runs only");
     return GPET_OK;
 }
 
@@ -361,6 +400,14 @@ extern "C" int gpet_result_copy(const gpet_result *r, int32_t which, void *dst, 
     if (v.bytes == 0) return GPET_OK;
     cudaError_t e = cudaMemcpy(dst, v.ptr, v.bytes, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "result copy");
+    if (which == GPET_COINC_A || which == GPET_COINC_B) {
+        // device indices count from the run's first single; renumber from the view's
+        const int32_t s0 = (int32_t)r->run->s_off[r->job];
+        if (s0) {
+            int32_t *p = static_cast<int32_t *>(dst);
+            for (size_t i = 0; i < v.bytes / 4; ++i) p[i] -= s0;
+        }
+    }
     return GPET_OK;
 }
 
@@ -371,8 +418,4 @@ extern "C" const void *gpet_result_device_ptr(const gpet_result *r, int32_t whic
     return v.ptr;
 }
 
-extern "C" void gpet_result_free(gpet_result *r) {
-    if (!r) return;
-    if (r->owns_run) run_release(r->run);
-    delete r;
-}
+extern "C" void gpet_result_free(gpet_result *r) { delete r; }

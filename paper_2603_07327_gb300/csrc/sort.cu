@@ -299,6 +299,52 @@ __global__ void __launch_bounds__(1024) k_coinc_write(SinglesDev s, CoincDev C) 
     }
 }
 
+// Per-job statistics of a (batched) run: start of each job's segment in the
+// time-sorted singles and in the coincidences (both are ordered by job, the
+// high bits of the sort key), and the job's hit count from its tallies.
+__global__ void __launch_bounds__(256) k_job_stats(SinglesDev s, CoincDev C, JobStatsDev J) {
+    const int j = blockIdx.x;
+    const unsigned long long ns = *s.n, nc = *C.n;
+    if (threadIdx.x == 0) {
+        unsigned long long lo = 0, hi = ns;  // first single with job >= j
+        while (lo < hi) {
+            const unsigned long long mid = (lo + hi) >> 1;
+            if (s.job[mid] < j) lo = mid + 1; else hi = mid;
+        }
+        J.s_off[j] = lo;
+        lo = 0;
+        hi = nc;                             // first coincidence whose first single has job >= j
+        while (lo < hi) {
+            const unsigned long long mid = (lo + hi) >> 1;
+            if (s.job[C.a[mid]] < j) lo = mid + 1; else hi = mid;
+        }
+        J.c_off[j] = lo;
+        if (j == J.n_jobs - 1) {
+            J.s_off[J.n_jobs] = ns;
+            J.c_off[J.n_jobs] = nc;
+        }
+    }
+    // hits of job j = sum of its per-crystal counts
+    unsigned long long acc = 0;
+    const unsigned long long *t = J.tally_count + J.tally_off[j];
+    const long long nt = J.tally_n[j];
+    for (long long i = threadIdx.x; i < nt; i += blockDim.x) acc += t[i];
+    __shared__ unsigned long long red[8];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFullMask, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        J.hits[j] = tot;
+    }
+}
+
+cudaError_t launch_job_stats(const SinglesDev &s, const CoincDev &C, const JobStatsDev &J, cudaStream_t st) {
+    k_job_stats<<<J.n_jobs, 256, 0, st>>>(s, C, J);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const CoincDev &C, int sm_count,
                               cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(S.ghist, 0, sizeof(uint32_t) * kPasses * 256, st);

@@ -1,0 +1,83 @@
+"""Batched form: many designs and sources in one persistent launch (and its
+CUDA-graph replay) give, job by job, exactly the results of the plain call."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests import parity_util as PU
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2603_07327_gb300 import build as B
+    B.build()
+    import paper_2603_07327_gb300 as G
+    G.load()
+    return G
+
+
+def canon(r):
+    s = r.singles()
+    order = np.lexsort((s["unit"], s["h"]))
+    a, b = r.coincidences()
+    return ({k: v[order] for k, v in s.items()}, PU.coincidence_set(s["h"], s["unit"], a, b), r.tallies(),
+            r.counts())
+
+
+def assert_same(x, y):
+    (s1, c1, t1, k1), (s2, c2, t2, k2) = x, y
+    for key in s1:
+        assert np.array_equal(s1[key], s2[key]), key
+    assert c1 == c2
+    assert np.array_equal(t1[0], t2[0]) and np.array_equal(t1[1], t2[1])
+    assert k1["hits"] == k2["hits"] and k1["singles"] == k2["singles"] and k1["coincidences"] == k2["coincidences"]
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_batch_equals_alone(G, kernel):
+    designs = W.config4(n_designs=6, scale=0.05)
+    ph = W.hot_rod_phantom(scale=0.7)
+    jobs = []
+    for i, d in enumerate(designs):
+        sc = G.Scanner(d["scanner"], ph if i == 2 else None)
+        src = W.phantom_source() if i == 2 else d["source"]
+        jobs.append(dict(scanner=sc, source=src, digitizer=d["digitizer"], n_decays=d["n_decays"], seed=d["seed"]))
+    # a second job on the same scanner shares its geometry descriptor
+    jobs.append(dict(jobs[0], seed=999, n_decays=33))
+    alone = [canon(j["scanner"].simulate(j["source"], j["digitizer"], j["n_decays"], j["seed"], kernel=kernel))
+             for j in jobs]
+    one_shot = G.simulate_batch(jobs, kernel=kernel)
+    for a, r in zip(alone, one_shot):
+        assert_same(a, canon(r))
+    b = G.Batch(jobs, kernel=kernel)
+    first = [canon(b.result(i)) for i in range(len(jobs))]
+    for a, f in zip(alone, first):
+        assert_same(a, f)
+    b.run()                              # graph replay: the same simulations again
+    for a, i in zip(alone, range(len(jobs))):
+        assert_same(a, canon(b.result(i)))
+    tot = b.counts()
+    assert tot["singles"] == sum(x[3]["singles"] for x in alone)
+    assert tot["hits"] == sum(x[3]["hits"] for x in alone)
+    b.close()
+
+
+def test_batch_of_sweep_positions(G, oracle):
+    """Two geometries x several positions in one launch, job-by-job parity
+    against the oracle on sampled histories."""
+    scs = {g: G.Scanner(W.config2_scanner(g)) for g in ("A", "B")}
+    jobs = []
+    for g in ("A", "B"):
+        for i, z in enumerate((-30.0, -7.0, 0.0, 19.0)):
+            jobs.append(dict(scanner=scs[g], source=W.point_source((0.0, 0.0, z)), digitizer=W.digitizer(),
+                             n_decays=150_000, seed=2 + i + 1000 * (g == "B")))
+    res = G.simulate_batch(jobs, kernel=2)
+    for j, r in zip(jobs, res):
+        s = r.singles()
+        osim = oracle.simulate(j["scanner"].desc, j["source"], j["digitizer"], j["n_decays"], j["seed"], threads=8)
+        sc_ = PU.compare_singles(s, osim["singles"], set(), 350.0, 650.0)
+        # allow the rare FP32/FP64 history flip: singles of at most a few histories differ
+        assert abs(sc_["n_gpu"] - sc_["n_orc"]) <= 4 and sc_["n_common"] >= sc_["n_orc"] - 4, sc_
+        assert np.all(np.diff(s["t_ps"].astype(np.int64)) >= 0)
