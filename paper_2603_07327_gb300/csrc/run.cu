@@ -223,13 +223,15 @@ int run_enqueue(Run &R) {
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaEventCreate");
     e = cudaMemsetAsync(R.arena, 0, R.zero_bytes, R.stream);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaMemsetAsync");
-    e = cudaEventRecord(R.ev[0], R.stream);
+    // external records: under stream capture they become event-record nodes
+    // that the replayed graph really records (plain records would only order)
+    e = cudaEventRecordWithFlags(R.ev[0], R.stream, cudaEventRecordExternal);
     if (e == cudaSuccess) e = launch_transport(R.W, R.O, R.cfg, R.stream);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "transport launch");
-    e = cudaEventRecord(R.ev[1], R.stream);
+    e = cudaEventRecordWithFlags(R.ev[1], R.stream, cudaEventRecordExternal);
     if (e == cudaSuccess) e = launch_sort_coinc(R.S, R.SD, R.C, R.cfg.sm_count, R.stream);
     if (e == cudaSuccess) e = launch_job_stats(R.SD, R.C, R.JS, R.stream);
-    if (e == cudaSuccess) e = cudaEventRecord(R.ev[2], R.stream);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(R.ev[2], R.stream, cudaEventRecordExternal);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "sort / coincidence launch");
     return GPET_OK;
 }
@@ -247,8 +249,14 @@ int run_collect(Run &R) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(R.job_hits.data(), R.JS.hits, 8 * nj, cudaMemcpyDeviceToHost, R.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(R.stream);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "run read-back");
-    if (R.ev[0] && cudaEventElapsedTime(&R.transport_ms, R.ev[0], R.ev[1]) != cudaSuccess) R.transport_ms = -1.f;
-    if (R.ev[1] && cudaEventElapsedTime(&R.digitizer_ms, R.ev[1], R.ev[2]) != cudaSuccess) R.digitizer_ms = -1.f;
+    if (R.ev[0] && cudaEventElapsedTime(&R.transport_ms, R.ev[0], R.ev[1]) != cudaSuccess) {
+        R.transport_ms = -1.f;
+        cudaGetLastError();  // a missing stage time is not an error of the run: clear it
+    }
+    if (R.ev[1] && cudaEventElapsedTime(&R.digitizer_ms, R.ev[1], R.ev[2]) != cudaSuccess) {
+        R.digitizer_ms = -1.f;
+        cudaGetLastError();
+    }
     const RunHeader &H = R.h_hdr;
     if (H.status & kStatusTimeout)
         return gpet_fail(GPET_ERR_TIMEOUT, "a photon exceeded %d steps or %d Compton trials", kMaxSteps, kMaxTrials);

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int
             case kPhPhantom: st = ev_phantom(J, W, s, cnt); break;
             case kPhFlight: ev_flight(J, g, s, cnt); break;
             case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, S, cnt); break;
+            case kPhCompton: st = ev_compton<true>(J, g, O, s, SL, S, cnt); break;
             default: break;
         }
         if (st != kStatusOk) {          // iteration cap hit: abandon the history, flag the run
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(128) k_transport_redo(WorkDev W, OutDev O) {
                     case kPhPhantom: st = ev_phantom(J, W, s, cnt); break;
                     case kPhFlight: ev_flight(J, g, s, cnt); break;
                     case kPhPanel: st = ev_panel<false>(J, g, W, O, s, SL, S, cnt); break;
+                    case kPhCompton: st = ev_compton<false>(J, g, O, s, SL, S, cnt); break;
                     default: break;
                 }
                 if (st != kStatusOk) { status |= st; s.phase = kPhIdle; }

@@ -15,7 +15,11 @@
 
 namespace gpet {
 
-enum : uint32_t { kPhIdle = 0, kPhSource = 1, kPhPhantom = 2, kPhFlight = 3, kPhPanel = 4, kPhFinish = 5 };
+// history phases; a real Compton interaction is deferred to its own phase so
+// that the rejection sampling and rotation run as one wavefront
+enum : uint32_t {
+    kPhIdle = 0, kPhSource = 1, kPhPhantom = 2, kPhFlight = 3, kPhPanel = 4, kPhCompton = 5, kPhFinish = 6
+};
 
 // per-history singles list: unit ids, energy sums, earliest time offset
 // (t - t0 in ps); `stride` separates consecutive entries of one history
@@ -84,6 +88,10 @@ struct PState {
     float E, path, trem;
     int32_t job, panel, last;
     uint32_t sph, sdet, gamma, phase, nsing, ovf;
+    // pending Compton interaction: azimuth draw, crystal id (-1: none), module << 8 | layer
+    uint32_t cu;
+    int32_t icrys;
+    uint32_t imod;
 };
 
 struct Counters {
@@ -201,15 +209,10 @@ __device__ __forceinline__ int ev_phantom(const JobDev &J, const WorkDev &W, PSt
     const float mu_m = fmaf(J.ph_mu_c511[m], xs.g, pe);
     if (u01(r.y) * mu_maj >= mu_m) return kStatusOk;          // virtual
     if (u01(r.z) * mu_m < pe) { photon_done(J, s); return kStatusOk; }   // photoelectric
-    float xm1;
-    const int nt = kahn_sample(J.seed, s.h, kTagPhantom, s.gamma, step_id, s.E, xm1);
-    if (nt < 0) return kStatusTimeout;
-    cnt.trials += (uint32_t)nt;
-    const float omc = xm1 / (s.E * kInvMec2);
-    rotate_dir(s.dx, s.dy, s.dz, omc, u01(r.w));
-    const float Ep = s.E / (1.0f + xm1);
-    if (Ep < J.e_cut) { photon_done(J, s); return kStatusOk; }
-    s.E = Ep;
+    (void)step_id;
+    s.cu = r.w;                                                 // Compton: next phase
+    s.icrys = -1;
+    s.phase = kPhCompton;
     return kStatusOk;
 }
 
@@ -258,6 +261,35 @@ __device__ __forceinline__ void add_single(const GeomDev &g, PState &s, const Si
     }
 }
 
+// a crystal interaction: tallies, optional hit list, singles list of the history
+template <bool kTallies>
+__device__ __forceinline__ void record_hit(const JobDev &J, const GeomDev &g, const OutDev &O, PState &s,
+                                           const SinglesList &SL, int max_entries, Counters &cnt, int crystal,
+                                           int module, int layer, uint32_t step_id, float dep) {
+    cnt.hits++;
+    const uint32_t dtp = (uint32_t)floorf(s.path * kInvCmmPerPs);
+    if (kTallies) {
+        atomicAdd(J.tally_count + crystal, 1ull);
+        atomicAdd(J.tally_efx + crystal, (unsigned long long)__float2ull_rn(dep * kEfxScale));
+        if (O.hit_cap) {
+            const unsigned long long slot = atomicAdd(O.n_hits, 1ull);
+            if (slot < O.hit_cap) {
+                O.hit_h[slot] = s.h;
+                O.hit_t[slot] = s.t0 + dtp;
+                O.hit_gstep[slot] = (int32_t)((s.gamma << 24) | step_id);
+                O.hit_crystal[slot] = crystal;
+                O.hit_layer[slot] = layer;
+                O.hit_job[slot] = s.job;
+                O.hit_wuv[3 * slot] = s.x;
+                O.hit_wuv[3 * slot + 1] = s.y;
+                O.hit_wuv[3 * slot + 2] = s.z;
+                O.hit_e[slot] = dep;
+            }
+        }
+    }
+    add_single(g, s, SL, max_entries, crystal, module, dep, dtp);
+}
+
 // one Woodcock step inside the current panel (layer selection, interaction, hit)
 template <bool kTallies>
 __device__ __forceinline__ int ev_panel(const JobDev &J, const GeomDev &g, const WorkDev &W, const OutDev &O,
@@ -286,54 +318,51 @@ __device__ __forceinline__ int ev_panel(const JobDev &J, const GeomDev &g, const
     const float pe = g.mu_pe511[L.mat] * xs.r3;
     const float mu_m = fmaf(g.mu_c511[L.mat], xs.g, pe);
     if (u01(r.y) * mu_maj >= mu_m) return kStatusOk;   // virtual
-    float dep;
-    bool dead = false;
-    if (u01(r.z) * mu_m < pe) {                        // photoelectric
-        dep = s.E;
-        dead = true;
-    } else {                                           // Compton (Klein-Nishina)
-        float xm1;
-        const int nt = kahn_sample(J.seed, s.h, kTagDetector, s.gamma, step_id, s.E, xm1);
-        if (nt < 0) return kStatusTimeout;
-        cnt.trials += (uint32_t)nt;
-        const float omc = xm1 / (s.E * kInvMec2);
-        // local frame (w, u, v) is a rotation of (x, y, z) about the axis
-        rotate_dir(s.dx, s.dy, s.dz, omc, u01(r.w));
-        const float Ep = s.E / (1.0f + xm1);
-        if (Ep < J.e_cut) {
-            dep = s.E;
-            dead = true;
-        } else {
-            dep = s.E * xm1 / (1.0f + xm1);
-            s.E = Ep;
-        }
+    if (u01(r.z) * mu_m < pe) {                        // photoelectric: deposit everything
+        if (L.crystal >= 0)
+            record_hit<kTallies>(J, g, O, s, SL, max_entries, cnt, L.crystal, L.module, L.layer, step_id, s.E);
+        photon_done(J, s);
+        return kStatusOk;
     }
-    if (L.crystal >= 0) {
-        cnt.hits++;
-        const uint32_t dtp = (uint32_t)floorf(s.path * kInvCmmPerPs);
-        if (kTallies) {
-            atomicAdd(J.tally_count + L.crystal, 1ull);
-            atomicAdd(J.tally_efx + L.crystal, (unsigned long long)__float2ull_rn(dep * kEfxScale));
-            if (O.hit_cap) {
-                const unsigned long long slot = atomicAdd(O.n_hits, 1ull);
-                if (slot < O.hit_cap) {
-                    O.hit_h[slot] = s.h;
-                    O.hit_t[slot] = s.t0 + dtp;
-                    O.hit_gstep[slot] = (int32_t)((s.gamma << 24) | step_id);
-                    O.hit_crystal[slot] = L.crystal;
-                    O.hit_layer[slot] = L.layer;
-                    O.hit_job[slot] = s.job;
-                    O.hit_wuv[3 * slot] = s.x;
-                    O.hit_wuv[3 * slot + 1] = s.y;
-                    O.hit_wuv[3 * slot + 2] = s.z;
-                    O.hit_e[slot] = dep;
-                }
-            }
-        }
-        add_single(g, s, SL, max_entries, L.crystal, L.module, dep, dtp);
+    s.cu = r.w;                                        // Compton (Klein-Nishina): next phase
+    s.icrys = L.crystal;
+    s.imod = ((uint32_t)L.module << 8) | ((uint32_t)L.layer & 0xFFu);
+    s.phase = kPhCompton;
+    return kStatusOk;
+}
+
+// a deferred Compton interaction, in the phantom (panel < 0) or in a panel:
+// Kahn sampling of Klein-Nishina, rotation about the old direction, deposit,
+// hit record, cutoff
+template <bool kTallies>
+__device__ __forceinline__ int ev_compton(const JobDev &J, const GeomDev &g, const OutDev &O, PState &s,
+                                          const SinglesList &SL, int max_entries, Counters &cnt) {
+    const bool in_panel = s.panel >= 0;
+    const uint32_t step_id = (in_panel ? s.sdet : s.sph) - 1u;
+    float xm1;
+    const int nt = kahn_sample(J.seed, s.h, in_panel ? kTagDetector : kTagPhantom, s.gamma, step_id, s.E, xm1);
+    if (nt < 0) return kStatusTimeout;
+    cnt.trials += (uint32_t)nt;
+    const float omc = xm1 / (s.E * kInvMec2);
+    // the panel frame (w, u, v) is a rotation of (x, y, z) about the axis
+    rotate_dir(s.dx, s.dy, s.dz, omc, u01(s.cu));
+    const float Ep = s.E / (1.0f + xm1);
+    const bool dead = Ep < J.e_cut;
+    const float dep = dead ? s.E : s.E * xm1 / (1.0f + xm1);
+    if (!dead) s.E = Ep;
+    if (!in_panel) {
+        if (dead) photon_done(J, s); else s.phase = kPhPhantom;
+        return kStatusOk;
     }
-    if (dead) { photon_done(J, s); return kStatusOk; }
-    s.trem = panel_exit(g, s.x, s.y, s.z, s.dx, s.dy, s.dz);
+    if (s.icrys >= 0)
+        record_hit<kTallies>(J, g, O, s, SL, max_entries, cnt, s.icrys, (int)(s.imod >> 8), (int)(s.imod & 0xFFu),
+                             step_id, dep);
+    if (dead) {
+        photon_done(J, s);
+    } else {
+        s.trem = panel_exit(g, s.x, s.y, s.z, s.dx, s.dy, s.dz);
+        s.phase = kPhPanel;
+    }
     return kStatusOk;
 }
 

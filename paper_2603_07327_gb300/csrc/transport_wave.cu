@@ -4,7 +4,7 @@
 // arrays, one 32-bit word per field and slot).  Every iteration the warp
 //   1. refills idle slots with new history ids from the chunked work queue,
 //   2. ballots the phase of all 64 slots (decay, phantom step, flight, panel
-//      step) and picks the most populated phase,
+//      step, Compton interaction) and picks the most populated phase,
 //   3. maps its 32 lanes onto the slots in that phase (__fns over the ballot
 //      masks), so every lane runs the same event code,
 //   4. runs up to `compact_every` events of that phase per lane, stores the
@@ -19,7 +19,7 @@ namespace gpet {
 constexpr int kWaveWarps = 4;           // warps per CTA
 constexpr int kPool = 64;               // slots per warp
 constexpr int kWaveS = 6;               // singles-list entries per history (overflow -> redo kernel)
-constexpr int kWords = 23;              // 32-bit words of state per slot
+constexpr int kWords = 26;              // 32-bit words of state per slot
 
 // shared-memory footprint of one warp's pool
 struct WarpPool {
@@ -31,7 +31,7 @@ struct WarpPool {
 
 enum : int {
     kWh0 = 0, kWh1, kWt0, kWt1, kWx, kWy, kWz, kWdx, kWdy, kWdz, kWx0, kWy0, kWz0, kWox, kWoy, kWoz, kWE, kWpath,
-    kWtrem, kWjob, kWpack, kWsteps
+    kWtrem, kWjob, kWpack, kWsteps, kWcu, kWicrys, kWimod
 };
 
 __device__ __forceinline__ uint32_t pool_phase(const WarpPool &P, int q) { return (P.st[kWpack][q] >> 16) & 7u; }
@@ -70,6 +70,9 @@ __device__ __forceinline__ void pool_load(const WarpPool &P, int q, PState &s) {
     const uint32_t sw = P.st[kWsteps][q];
     s.sph = sw & 0xFFFFu;
     s.sdet = sw >> 16;
+    s.cu = P.st[kWcu][q];
+    s.icrys = (int32_t)P.st[kWicrys][q];
+    s.imod = P.st[kWimod][q];
 }
 
 __device__ __forceinline__ void pool_store(WarpPool &P, int q, const PState &s) {
@@ -96,6 +99,9 @@ __device__ __forceinline__ void pool_store(WarpPool &P, int q, const PState &s) 
     P.st[kWpack][q] = (uint32_t)(s.panel + 1) | ((uint32_t)(s.last + 1) << 7) | (s.gamma << 14) | (s.phase << 16) |
                       (s.nsing << 19) | (s.ovf << 24);
     P.st[kWsteps][q] = (s.sph & 0xFFFFu) | (s.sdet << 16);
+    P.st[kWcu][q] = s.cu;
+    P.st[kWicrys][q] = (uint32_t)s.icrys;
+    P.st[kWimod][q] = s.imod;
 }
 
 // warp-wide refill of the idle slots of one half of the pool (see transport.cu)
@@ -180,7 +186,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
         int best_n = 0;
         uint32_t best_p = kPhIdle;
 #pragma unroll
-        for (uint32_t p = kPhSource; p <= kPhPanel; ++p) {
+        for (uint32_t p = kPhSource; p <= kPhCompton; ++p) {
             const uint32_t b0 = __ballot_sync(kFullMask, ph0 == p), b1 = __ballot_sync(kFullMask, ph1 == p);
             const int n = __popc(b0) + __popc(b1);
             if (n > best_n) { best_n = n; best_b0 = b0; best_b1 = b1; best_p = p; }
@@ -207,6 +213,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
                     case kPhPhantom: st = ev_phantom(J, W, s, cnt); break;
                     case kPhFlight: ev_flight(J, g, s, cnt); break;
                     case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, kWaveS, cnt); break;
+                    case kPhCompton: st = ev_compton<true>(J, g, O, s, SL, kWaveS, cnt); break;
                     default: break;
                 }
                 if (st != kStatusOk) {
