@@ -31,9 +31,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import workloads as W  # noqa: E402
 
-METRIC = "pairs tracked/s/GB300"
+METRIC = "pairs tracked/s/GB300 batched vs plain; p50/p99 served-request latency"
 N_POSITIONS = 61
 PAIRS_PER_POSITION = 10_000_000
 
@@ -161,6 +163,78 @@ def run_reference(args):
                 e2e=dict(value=value, unit="pairs/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_served(G, args):
+    """The served stream: 2000 requests arriving as a Poisson process (50/s),
+    each a design drawn like the batched sweep, half point sources and half
+    the hot-rod phantom scaled 0.5-1x, 1e5-5e7 pairs; admitted under a 150 GB
+    HBM budget.  Returns latency percentiles, aggregate and offered pairs/s and
+    the pairs/s of sequential plain launches of the same requests."""
+    import threading
+    reqs = W.config5(n_requests=args.served_requests)
+    base = W.hot_rod_phantom()
+
+    def make(r):
+        ph = None
+        if r["phantom"] is not None:
+            vs = 0.5 * r["phantom"][1]
+            ph = dict(base, voxel=(vs, vs, vs), origin=(-30 * vs, -30 * vs, -50 * vs))
+        return G.Scanner(r["scanner"], ph)
+
+    srv = G.Server(hbm_budget_bytes=150 * 10**9, workers=2, kernel=args.kernel)
+    # warm the server path once (kernels, pools)
+    w = make(reqs[0])
+    srv.wait(srv.submit(w, reqs[0]["source"], reqs[0]["digitizer"], 100_000, 1))
+    ids, scanners = [None] * len(reqs), [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submit_all():
+        for i, r in enumerate(reqs):
+            dt = r["arrival_s"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            scanners[i] = make(r)   # the request's design (and phantom) is built at arrival
+            ids[i] = srv.submit(scanners[i], r["source"], r["digitizer"], r["n_decays"], r["seed"])
+
+    lat = []
+
+    def collect_all():
+        # results are taken (and their device memory released) as they complete
+        for k in range(len(reqs)):
+            while ids[k] is None:
+                time.sleep(0.001)
+            res = srv.wait(ids[k])
+            lat.append(res.counts()["latency_ms"])
+            res.free()
+
+    th = threading.Thread(target=submit_all)
+    tc = threading.Thread(target=collect_all)
+    th.start()
+    tc.start()
+    th.join()
+    tc.join()
+    t_last = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    pairs = sum(r["n_decays"] for r in reqs)
+    span = reqs[-1]["arrival_s"]
+    # sequential plain launches of the first requests, same designs, back to back
+    k = min(len(reqs), args.served_plain_sample)
+    sc_plain = [scanners[i] for i in range(k)]
+    tp = time.perf_counter()
+    for i in range(k):
+        sc_plain[i].simulate(reqs[i]["source"], reqs[i]["digitizer"], reqs[i]["n_decays"], reqs[i]["seed"],
+                             kernel=args.kernel).free()
+    tp = time.perf_counter() - tp
+    pairs_plain = sum(reqs[i]["n_decays"] for i in range(k))
+    lat = sorted(lat)
+    return dict(requests=len(reqs), p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                max_ms=float(lat[-1]), pairs=pairs, pairs_per_s=pairs / t_last, offered_pairs_per_s=pairs / span,
+                wall_s=t_last, launches=st["launches"], max_jobs_per_launch=st["max_jobs_per_launch"],
+                peak_hbm_bytes=st["peak_bytes"], hbm_budget_bytes=150 * 10**9,
+                sequential_plain_pairs_per_s=pairs_plain / tp, sequential_plain_sample=k,
+                arrivals="Poisson, mean 50 req/s, seed 5")
 
 
 def run_ours(args):
@@ -304,6 +378,8 @@ def run_ours(args):
         t1.synchronize()
         line["plain_pairs_per_s"] = pairs_per_step / (t0.elapsed_time(t1) / 1000.0)
         line["batched_over_plain"] = value / line["plain_pairs_per_s"]
+    if rank == 0 and args.served:
+        line["served"] = run_served(G, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, _, _ = cpu_baseline()
         line["cpu_baseline"] = cb
@@ -328,6 +404,10 @@ def main():
     ap.add_argument("--positions", type=int, default=N_POSITIONS)
     ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per transport launch from ncu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--served", action="store_true", default=True)
+    ap.add_argument("--no-served", dest="served", action="store_false")
+    ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--served-plain-sample", type=int, default=300)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

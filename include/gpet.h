@@ -137,7 +137,11 @@ typedef struct {
     int32_t blocks_per_sm;   /* resident CTAs per SM (0 = tuned default)                   */
     int32_t kernel;          /* 0 = tuned default, 1 = per-lane event loop, 2 = wavefront  */
     int32_t compact_every;   /* wavefront regrouping interval in events (0 = default)      */
+    int32_t pool_depth;      /* wavefront histories per lane in shared memory, 2..4 (0 = 2)  */
     void *stream;            /* cudaStream_t */
+    uint64_t h_begin, h_end; /* run only histories [h_begin, h_end) of the n_decays run (a shard);
+                                h_end = 0 means n_decays.  Decay times keep the whole run's span,
+                                so shards of one run merge exactly (tallies add, singles concatenate) */
 } gpet_options;
 
 typedef struct gpet_scanner gpet_scanner;
@@ -192,6 +196,8 @@ typedef struct {
     float transport_ms;     /* CUDA-event time of the transport kernels on the run's stream */
     float digitizer_ms;     /* CUDA-event time of time sort + coincidence sorting */
     uint64_t h2d_bytes;     /* descriptor bytes uploaded for the run (jobs, geometry, work table) */
+    uint64_t wave_iterations, wave_lanes; /* wavefront kernel: regrouping steps and lanes they fed */
+    double latency_ms;      /* served requests: submission to result ready (0 otherwise) */
 } gpet_counts;
 int gpet_result_counts(const gpet_result *r, gpet_counts *out);
 
@@ -261,6 +267,61 @@ void gpet_batch_destroy(gpet_batch *b);
 int gpet_simulate_batch(int32_t n_jobs, gpet_scanner *const *scanners, const gpet_source *sources,
                         const gpet_digitizer *digitizers, const uint64_t *n_decays, const uint64_t *seeds,
                         const gpet_options *opt, gpet_result **outs);
+
+/* ------------------------------------------------------------------------ */
+/* autotuner                                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Time the candidate launch forms of the transport kernel -- the per-lane
+ * event loop at 1 or 2 CTAs per SM, the wavefront kernel with regrouping
+ * every 1, 2, 4 or 8 events -- on a pilot run (pilot_decays >= 1000, seed)
+ * of the caller's workload, and return the fastest in *best (its transport
+ * time in *best_ms, may be NULL).  The choice is remembered for the scanner's
+ * design class (panels, layers, phantom) on this device's SM count; later
+ * launches with gpet_options.kernel = 0 use it.  Runs the pilot on the
+ * legacy default stream. */
+int gpet_autotune(gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg, uint64_t pilot_decays,
+                  uint64_t seed, gpet_options *best, float *best_ms);
+
+/* ------------------------------------------------------------------------ */
+/* serving loop: continuous batching of simulation requests                  */
+/* ------------------------------------------------------------------------ */
+
+/* A server accepts simulation requests from any host thread while earlier
+ * ones run.  Worker threads (each with its own stream) repeatedly admit the
+ * queued requests that fit the device-memory budget, first come first
+ * served, and run them together as one batched launch; the batches of
+ * different workers overlap on the GPU.  A request's device memory counts
+ * against the budget from admission until its result is freed, so a client
+ * that keeps results while it waits for later requests can stall admission:
+ * free results once read.  A request's result equals gpet_simulate's for the
+ * same inputs. */
+typedef struct gpet_server gpet_server;
+typedef struct {
+    size_t hbm_budget_bytes;      /* device memory the server may hold for admitted requests */
+    int32_t workers;              /* batching threads, one stream each (0 = 2, at most 8) */
+    int32_t max_jobs_per_launch;  /* requests per batched launch (0 = 256, at most 4095) */
+    gpet_options launch;          /* kernel options of every launch (stream, keep_hits ignored) */
+} gpet_server_config;
+typedef struct {
+    uint64_t submitted, completed, rejected, launches, max_jobs_per_launch, pairs_completed;
+    uint64_t bytes_in_use, peak_bytes, queued;
+} gpet_server_stats;
+int gpet_server_create(const gpet_server_config *cfg, gpet_server **out);
+/* Queue one request.  The scanner (and its phantom) must stay alive until the
+ * request's result has been taken.  block = 0: GPET_ERR_BUSY when the budget
+ * cannot take it now; block = 1: it waits in the queue.  GPET_ERR_OOM when it
+ * alone exceeds the budget.  *req_id identifies it for poll / wait. */
+int gpet_server_submit(gpet_server *s, gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg,
+                       uint64_t n_decays, uint64_t seed, int32_t block, uint64_t *req_id);
+/* *out = NULL while the request runs; its result (ownership passes to the
+ * caller, latency in gpet_counts.latency_ms) once done; the request's error
+ * code if it failed.  A taken request id is forgotten. */
+int gpet_server_poll(gpet_server *s, uint64_t req_id, gpet_result **out);
+int gpet_server_wait(gpet_server *s, uint64_t req_id, gpet_result **out);
+int gpet_server_stats_get(gpet_server *s, gpet_server_stats *out);
+/* Finish the queued requests, stop the workers, free untaken results. */
+void gpet_server_destroy(gpet_server *s);
 
 /* Thread-local text of the last error (never NULL). */
 const char *gpet_last_error(void);

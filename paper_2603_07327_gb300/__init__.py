@@ -70,7 +70,8 @@ class Digitizer(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("keep_hits", C.c_int32), ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("kernel", C.c_int32), ("compact_every", C.c_int32), ("stream", C.c_void_p)]
+                ("kernel", C.c_int32), ("compact_every", C.c_int32), ("pool_depth", C.c_int32),
+                ("stream", C.c_void_p), ("h_begin", C.c_uint64), ("h_end", C.c_uint64)]
 
 
 class Counts(C.Structure):
@@ -78,7 +79,18 @@ class Counts(C.Structure):
                 ("coincidences", C.c_uint64), ("n_crystals", C.c_int64), ("det_steps", C.c_uint64),
                 ("flights", C.c_uint64), ("compton_trials", C.c_uint64), ("entered", C.c_uint64),
                 ("phantom_steps", C.c_uint64), ("status", C.c_int32), ("transport_ms", C.c_float),
-                ("digitizer_ms", C.c_float), ("h2d_bytes", C.c_uint64)]
+                ("digitizer_ms", C.c_float), ("h2d_bytes", C.c_uint64), ("wave_iterations", C.c_uint64),
+                ("wave_lanes", C.c_uint64), ("latency_ms", C.c_double)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("workers", C.c_int32), ("max_jobs_per_launch", C.c_int32),
+                ("launch", Options)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "rejected", "launches", "max_jobs_per_launch",
+                                          "pairs_completed", "bytes_in_use", "peak_bytes", "queued")]
 
 
 # every entry point declared in include/gpet.h: name -> (restype, argtypes)
@@ -105,6 +117,15 @@ SIGNATURES = {
     "gpet_simulate_batch": (C.c_int, [C.c_int32, C.POINTER(_P), C.POINTER(Source), C.POINTER(Digitizer),
                                       C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(Options),
                                       C.POINTER(_P)]),
+    "gpet_autotune": (C.c_int, [_P, C.POINTER(Source), C.POINTER(Digitizer), C.c_uint64, C.c_uint64,
+                                C.POINTER(Options), C.POINTER(C.c_float)]),
+    "gpet_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(_P)]),
+    "gpet_server_submit": (C.c_int, [_P, _P, C.POINTER(Source), C.POINTER(Digitizer), C.c_uint64, C.c_uint64,
+                                     C.c_int32, C.POINTER(C.c_uint64)]),
+    "gpet_server_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(_P)]),
+    "gpet_server_wait": (C.c_int, [_P, C.c_uint64, C.POINTER(_P)]),
+    "gpet_server_stats_get": (C.c_int, [_P, C.POINTER(ServerStats)]),
+    "gpet_server_destroy": (None, [_P]),
     "gpet_last_error": (C.c_char_p, []),
     "gpet_version": (C.c_char_p, []),
 }
@@ -163,9 +184,10 @@ def digitizer_struct(dg):
     return Digitizer(dg["fwhm_at_511"], dg["e_lo"], dg["e_hi"], dg["window_ns"], dg["e_cut"])
 
 
-def options_struct(keep_hits=False, block_size=0, blocks_per_sm=0, kernel=0, compact_every=0, stream=None):
+def options_struct(keep_hits=False, block_size=0, blocks_per_sm=0, kernel=0, compact_every=0, pool_depth=0,
+                   stream=None, h_begin=0, h_end=0):
     return Options(int(bool(keep_hits)), int(block_size), int(blocks_per_sm), int(kernel), int(compact_every),
-                   C.c_void_p(stream) if stream else None)
+                   int(pool_depth), C.c_void_p(stream) if stream else None, int(h_begin), int(h_end))
 
 
 class Scanner:
@@ -203,6 +225,14 @@ class Scanner:
         _check(L.gpet_simulate(self._h, C.byref(source_struct(source)), C.byref(digitizer_struct(digitizer)),
                                int(n_decays), int(seed), C.byref(o), C.byref(out)))
         return Result(out)
+
+    def autotune(self, source, digitizer, pilot_decays=2_000_000, seed=1):
+        """Time the launch forms on a pilot run; returns (options dict, transport ms)."""
+        o = Options()
+        ms = C.c_float()
+        _check(load().gpet_autotune(self._h, C.byref(source_struct(source)), C.byref(digitizer_struct(digitizer)),
+                                    int(pilot_decays), int(seed), C.byref(o), C.byref(ms)))
+        return dict(kernel=o.kernel, blocks_per_sm=o.blocks_per_sm, compact_every=o.compact_every), ms.value
 
     def close(self):
         if self._h:
@@ -342,3 +372,54 @@ def simulate_batch(jobs, **opts):
     o = options_struct(**opts)
     _check(L.gpet_simulate_batch(n, scs, srcs, dgs, nd, sd, C.byref(o), outs))
     return [Result(C.c_void_p(outs[i])) for i in range(n)]
+
+
+class Server:
+    """gpet_server handle: continuous batching of simulation requests."""
+
+    def __init__(self, hbm_budget_bytes=150 * 10**9, workers=2, max_jobs_per_launch=256, **launch_opts):
+        L = load()
+        cfg = ServerConfig(int(hbm_budget_bytes), int(workers), int(max_jobs_per_launch),
+                           options_struct(**launch_opts))
+        self._h = C.c_void_p()
+        _check(L.gpet_server_create(C.byref(cfg), C.byref(self._h)))
+        self._keep = {}
+
+    def submit(self, scanner: Scanner, source, digitizer, n_decays, seed, block=True) -> int:
+        rid = C.c_uint64()
+        _check(load().gpet_server_submit(self._h, scanner._h, C.byref(source_struct(source)),
+                                         C.byref(digitizer_struct(digitizer)), int(n_decays), int(seed),
+                                         1 if block else 0, C.byref(rid)))
+        self._keep[rid.value] = scanner       # the scanner must outlive the request
+        return rid.value
+
+    def poll(self, rid):
+        out = C.c_void_p()
+        _check(load().gpet_server_poll(self._h, int(rid), C.byref(out)))
+        if not out.value:
+            return None
+        self._keep.pop(rid, None)
+        return Result(out)
+
+    def wait(self, rid):
+        out = C.c_void_p()
+        _check(load().gpet_server_wait(self._h, int(rid), C.byref(out)))
+        self._keep.pop(rid, None)
+        return Result(out)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().gpet_server_stats_get(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            load().gpet_server_destroy(self._h)
+            self._h = C.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -255,8 +255,10 @@ extern "C" int gpet_create_scanner(const gpet_scanner_desc *desc, gpet_scanner *
 void free_phantom(gpet_scanner *sc) {
     if (sc->ph_mat) cudaFree(sc->ph_mat);
     if (sc->ph_cdf) cudaFree(sc->ph_cdf);
+    if (sc->ph_guide) cudaFree(sc->ph_guide);
     sc->ph_mat = nullptr;
     sc->ph_cdf = nullptr;
+    sc->ph_guide = nullptr;
     sc->has_phantom = false;
 }
 
@@ -323,6 +325,23 @@ extern "C" int gpet_load_phantom(gpet_scanner *sc, int32_t nx, int32_t ny, int32
         if (e != cudaSuccess) { free_phantom(sc); return gpet_cuda_fail(e, "cudaMalloc(activity)"); }
         e = cudaMemcpy(sc->ph_cdf, cdf.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { free_phantom(sc); return gpet_cuda_fail(e, "cudaMemcpy(activity)"); }
+        // guide table: guide[k] = first voxel whose prefix sum lies in bucket >= k
+        if (total > 0.0) {
+            const int32_t G = (int32_t)std::min<int64_t>(65536, std::max<int64_t>(1, n));
+            const double gscale = (double)G / total;
+            std::vector<int32_t> guide((size_t)G, (int32_t)(n - 1));
+            int32_t k = 0;
+            for (int64_t i = 0; i < n && k < G; ++i) {
+                const int64_t b = std::min<int64_t>((int64_t)(cdf[(size_t)i] * gscale), G - 1);
+                while (k <= b && k < G) guide[(size_t)k++] = (int32_t)i;
+            }
+            e = cudaMalloc(&sc->ph_guide, sizeof(int32_t) * (size_t)G);
+            if (e != cudaSuccess) { free_phantom(sc); return gpet_cuda_fail(e, "cudaMalloc(guide)"); }
+            e = cudaMemcpy(sc->ph_guide, guide.data(), sizeof(int32_t) * (size_t)G, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { free_phantom(sc); return gpet_cuda_fail(e, "cudaMemcpy(guide)"); }
+            sc->ph_buckets = G;
+            sc->ph_gscale = gscale;
+        }
     }
     sc->has_phantom = true;
     sc->ph_n[0] = nx; sc->ph_n[1] = ny; sc->ph_n[2] = nz;
@@ -337,9 +356,13 @@ extern "C" int gpet_load_phantom(gpet_scanner *sc, int32_t nx, int32_t ny, int32
 // job description for the kernels
 // ---------------------------------------------------------------------------
 int gpet_make_job(const gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg, uint64_t n_decays,
-                  uint64_t seed, JobDev &J) {
+                  uint64_t seed, JobDev &J, uint64_t h_begin, uint64_t h_end) {
     if (!sc || !src || !dg) return gpet_fail(GPET_ERR_INVALID_ARG, "NULL argument");
     if (n_decays == 0) return gpet_fail(GPET_ERR_INVALID_ARG, "n_decays must be > 0");
+    if (h_end == 0) h_end = n_decays;
+    if (h_end > n_decays || h_begin >= h_end)
+        return gpet_fail(GPET_ERR_INVALID_ARG, "history range [%llu, %llu) outside the %llu-decay run",
+                         (unsigned long long)h_begin, (unsigned long long)h_end, (unsigned long long)n_decays);
     if (!(src->activity_bq > 0.0) || !std::isfinite(src->activity_bq))
         return gpet_fail(GPET_ERR_INVALID_ARG, "activity must be > 0");
     if (src->kind < 0 || src->kind > 2) return gpet_fail(GPET_ERR_INVALID_ARG, "source kind %d", src->kind);
@@ -359,6 +382,8 @@ int gpet_make_job(const gpet_scanner *sc, const gpet_source *src, const gpet_dig
     J.geom = 0;
     J.seed = seed;
     J.n_decays = n_decays;
+    J.h_base = h_begin;
+    J.n_hist = h_end - h_begin;
     J.t_span_ps = (uint64_t)std::llround(span);
     J.src_kind = src->kind;
     for (int a = 0; a < 3; ++a) {
@@ -385,6 +410,9 @@ int gpet_make_job(const gpet_scanner *sc, const gpet_source *src, const gpet_dig
         }
         J.ph_mat = sc->ph_mat;
         J.ph_cdf = sc->ph_cdf;
+        J.ph_guide = sc->ph_guide;
+        J.ph_buckets = sc->ph_buckets;
+        J.ph_gscale = sc->ph_gscale;
         J.ph_total = sc->ph_total;
         J.ph_n = (int64_t)sc->ph_n[0] * sc->ph_n[1] * sc->ph_n[2];
         J.ph_last_active = sc->ph_last_active;

@@ -23,7 +23,7 @@ int gpet_batch_build_run(Run &R, int32_t n_jobs, gpet_scanner *const *scanners, 
                          const gpet_options *opt) {
     if (n_jobs < 1 || !scanners || !sources || !digitizers || !n_decays || !seeds)
         return gpet_fail(GPET_ERR_INVALID_ARG, "batch needs n_jobs >= 1 and non-NULL arrays");
-    int st = run_default_cfg(R, opt);
+    int st = run_default_cfg(R, opt, scanners[0]);
     if (st != GPET_OK) return st;
     std::map<std::string, int> geom_index;  // deduplicated geometry table
     uint64_t total = 0;

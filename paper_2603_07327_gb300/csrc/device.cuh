@@ -63,6 +63,7 @@ struct GeomDev {
 // source and its digitizer settings
 struct JobDev {
     uint64_t seed, n_decays, t_span_ps;
+    uint64_t h_base, n_hist;          // histories [h_base, h_base + n_hist) of the run
     int32_t geom, src_kind;
     float src_pos[3], src_dir[3];
     float e_cut, e_lo, e_hi, sig_k;   // sig_k = fwhm_511 / (2 sqrt(2 ln 2))
@@ -72,8 +73,10 @@ struct JobDev {
     float ph_mu_c511[kMaxMaterials], ph_mu_pe511[kMaxMaterials];
     const uint8_t *ph_mat;
     const double *ph_cdf;             // activity prefix sums in voxel order
-    double ph_total;
+    const int32_t *ph_guide;          // guide table: first voxel of each bucket of the total
+    double ph_total, ph_gscale;       // gscale = buckets / total
     int64_t ph_n, ph_last_active;
+    int32_t ph_buckets, ph_pad;
     // per-crystal tallies of this job
     unsigned long long *tally_count, *tally_efx;
 };
@@ -81,9 +84,7 @@ struct JobDev {
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
 // ---------------------------------------------------------------------------
-// one out-of-line copy: the block is called from every event, and inlining it
-// at each call site multiplies the kernel's instruction footprint
-static __device__ __noinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
     const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll

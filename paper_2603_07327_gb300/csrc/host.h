@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <memory>
 #include <string>
 #include <vector>
@@ -23,16 +24,21 @@ struct gpet_scanner {
     std::vector<gpet_material> ph_materials;
     uint8_t *ph_mat = nullptr;
     double *ph_cdf = nullptr;
+    int32_t *ph_guide = nullptr;
+    int32_t ph_buckets = 0;
+    double ph_gscale = 0.0;
     double ph_total = 0.0;
     int64_t ph_last_active = -1;
 };
 
 int gpet_fail(int code, const char *fmt, ...);
+// tuned launch form for this scanner's design class on a device with `sms` SMs
+bool gpet_tuned_options(const gpet_scanner *sc, int sms, gpet_options *out);
 int gpet_cuda_fail(cudaError_t e, const char *where);
 int gpet_xs_table(const float **out, float *ln_emin, float *inv_h);
 int gpet_build_geometry(const gpet_scanner_desc *d, gpet::GeomDev &g, int64_t &n_crystals);
 int gpet_make_job(const gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg, uint64_t n_decays,
-                  uint64_t seed, gpet::JobDev &J);
+                  uint64_t seed, gpet::JobDev &J, uint64_t h_begin = 0, uint64_t h_end = 0);
 
 namespace gpet {
 
@@ -84,6 +90,7 @@ struct Run {
     JobStatsDev JS{};
     std::vector<unsigned long long> s_off, c_off, job_hits;
     bool own_stream = false;
+    std::function<void()> on_release;    // called once when the run's memory is gone
     ~Run();
 };
 
@@ -91,7 +98,7 @@ int run_plan(Run &R);                  // allocate the arena, upload jobs and ge
 int run_enqueue(Run &R);               // memset + transport + sort + coincidences (capturable)
 int run_collect(Run &R);               // synchronise, read the header, map device status
 void run_release(Run &R);
-int run_default_cfg(Run &R, const gpet_options *opt);
+int run_default_cfg(Run &R, const gpet_options *opt, const gpet_scanner *sc_for_tuning = nullptr);
 
 }  // namespace gpet
 
@@ -102,6 +109,11 @@ struct gpet_result {
     gpet_counts counts{};
     int job = 0;
 };
+
+namespace gpet {
+// device bytes a run of these totals will take (the arena layout of run_plan)
+size_t run_footprint(uint64_t total_decays, int64_t total_crystals, int n_jobs, size_t n_geoms, bool keep_hits);
+}
 
 struct gpet_batch {
     std::shared_ptr<gpet::Run> run;

@@ -17,6 +17,7 @@ struct LaunchCfg {
     int kernel;          // kKernelLoop / kKernelWave
     int max_smem_geoms;  // geometry descriptors staged in shared memory
     int compact_every;   // wavefront regrouping interval (events)
+    int pool_depth;      // wavefront slots per lane (pool = 32 x depth histories per warp)
 };
 
 // radix sort working set (keys ping-pong between two buffers)

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "host.h"
 
@@ -29,11 +30,44 @@ static void rebase(T *&p, char *base) {
     p = reinterpret_cast<T *>(base + reinterpret_cast<size_t>(p));
 }
 
-int run_default_cfg(Run &R, const gpet_options *opt) {
+// Keep freed arenas in the device's stream-ordered pool instead of returning
+// them to the driver at every synchronisation (once per device).
+static void keep_pool_memory(int dev) {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    if (dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
+int run_default_cfg(Run &R, const gpet_options *opt_in, const gpet_scanner *sc) {
+    // kernel 0: the autotuner's choice for this design class when one was made
+    gpet_options tuned;
+    const gpet_options *opt = opt_in;
+    gpet_options merged;
+    int sms0 = 0, dev0 = 0;
+    if (sc && (!opt_in || opt_in->kernel == 0) && cudaGetDevice(&dev0) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0) == cudaSuccess &&
+        ::gpet_tuned_options(sc, sms0, &tuned)) {
+        if (opt_in) merged = *opt_in; else std::memset(&merged, 0, sizeof(merged));
+        merged.kernel = tuned.kernel;
+        if (merged.blocks_per_sm == 0) merged.blocks_per_sm = tuned.blocks_per_sm;
+        if (merged.compact_every == 0) merged.compact_every = tuned.compact_every;
+        if (merged.pool_depth == 0) merged.pool_depth = tuned.pool_depth;
+        opt = &merged;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaGetDevice");
     R.device = dev;
+    keep_pool_memory(dev);
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaDeviceGetAttribute");
@@ -43,10 +77,12 @@ int run_default_cfg(Run &R, const gpet_options *opt) {
         return gpet_fail(GPET_ERR_INVALID_ARG, "block_size %d must be a multiple of 32 and <= 256", R.cfg.block_size);
     const int bps = (opt && opt->blocks_per_sm > 0) ? opt->blocks_per_sm : 4;
     R.cfg.grid = sms * bps;
-    R.cfg.kernel = (opt && opt->kernel > 0) ? opt->kernel : kKernelLoop;
+    R.cfg.kernel = (opt && opt->kernel > 0) ? opt->kernel : kKernelWave;
     if (R.cfg.kernel != kKernelLoop && R.cfg.kernel != kKernelWave)
         return gpet_fail(GPET_ERR_INVALID_ARG, "kernel %d not in {1, 2}", R.cfg.kernel);
     R.cfg.compact_every = (opt && opt->compact_every > 0) ? opt->compact_every : 1;
+    R.cfg.pool_depth = (opt && opt->pool_depth > 0) ? opt->pool_depth : 2;
+    if (R.cfg.pool_depth > 4) return gpet_fail(GPET_ERR_INVALID_ARG, "pool_depth must be in [1, 4]");
     if (R.cfg.compact_every > 64) return gpet_fail(GPET_ERR_INVALID_ARG, "compact_every must be <= 64");
     R.cfg.max_smem_geoms = 16;
     R.keep_hits = opt && opt->keep_hits;
@@ -65,14 +101,14 @@ int run_plan(Run &R) {
     R.total_crystals = tc;
     // chunks: small enough that every warp of the grid gets work
     uint64_t total = 0;
-    for (auto &J : R.jobs) total += J.n_decays;
+    for (auto &J : R.jobs) total += J.n_hist;
     const uint64_t warps = (uint64_t)R.cfg.grid * (R.cfg.block_size / 32);
     uint64_t cs = total / std::max<uint64_t>(warps * 8, 1);
     cs = std::max<uint64_t>(32, std::min<uint64_t>(4096, cs / 32 * 32));
     R.chunk_size = (unsigned)cs;
     R.chunk_start.assign(nj + 1, 0);
     for (int j = 0; j < nj; ++j)
-        R.chunk_start[j + 1] = R.chunk_start[j] + (R.jobs[j].n_decays + cs - 1) / cs;
+        R.chunk_start[j + 1] = R.chunk_start[j] + (R.jobs[j].n_hist + cs - 1) / cs;
 
     const uint64_t cap = std::max<uint64_t>(R.caps.singles, 1);
     const uint64_t hcap = R.keep_hits ? std::max<uint64_t>(R.caps.hits, 1) : 0;
@@ -223,15 +259,20 @@ int run_enqueue(Run &R) {
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaEventCreate");
     e = cudaMemsetAsync(R.arena, 0, R.zero_bytes, R.stream);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaMemsetAsync");
-    // external records: under stream capture they become event-record nodes
-    // that the replayed graph really records (plain records would only order)
-    e = cudaEventRecordWithFlags(R.ev[0], R.stream, cudaEventRecordExternal);
+    // under stream capture the stage events must be external records, which
+    // the replayed graph really records (a plain record there only orders
+    // work); outside capture the external flag is refused, so record plainly
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(R.stream, &cap);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaStreamIsCapturing");
+    const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    e = cudaEventRecordWithFlags(R.ev[0], R.stream, rec_flags);
     if (e == cudaSuccess) e = launch_transport(R.W, R.O, R.cfg, R.stream);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "transport launch");
-    e = cudaEventRecordWithFlags(R.ev[1], R.stream, cudaEventRecordExternal);
+    e = cudaEventRecordWithFlags(R.ev[1], R.stream, rec_flags);
     if (e == cudaSuccess) e = launch_sort_coinc(R.S, R.SD, R.C, R.cfg.sm_count, R.stream);
     if (e == cudaSuccess) e = launch_job_stats(R.SD, R.C, R.JS, R.stream);
-    if (e == cudaSuccess) e = cudaEventRecordWithFlags(R.ev[2], R.stream, cudaEventRecordExternal);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(R.ev[2], R.stream, rec_flags);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "sort / coincidence launch");
     return GPET_OK;
 }
@@ -269,7 +310,10 @@ int run_collect(Run &R) {
 }
 
 void run_release(Run &R) {
-    if (R.arena) cudaFreeAsync(R.arena, R.stream);
+    // Every run's work has been synchronised before its memory is released,
+    // and a run may outlive the stream it ran on (a server worker's, a
+    // caller's): free in the order of the legacy stream, never the run's own.
+    if (R.arena) cudaFreeAsync(R.arena, cudaStreamLegacy);
     R.arena = nullptr;
     for (auto &e : R.ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -281,6 +325,25 @@ Run::~Run() {
         cudaStreamSynchronize(stream);
         cudaStreamDestroy(stream);
     }
+    if (on_release) on_release();
+}
+
+size_t run_footprint(uint64_t total_decays, int64_t total_crystals, int n_jobs, size_t n_geoms, bool keep_hits) {
+    const uint64_t cap = std::max<uint64_t>(65536, total_decays * 6 / 10);
+    const uint64_t hcap = keep_hits ? std::max<uint64_t>(65536, total_decays * 5 / 2) : 0;
+    const uint64_t ocap = std::max<uint64_t>(4096, total_decays / 256);
+    const uint64_t tiles = (cap + 4095) / 4096;
+    size_t b = 0;
+    b += sizeof(RunHeader) + 8 * 256 * 4 + 16 * (size_t)total_crystals;
+    b += sizeof(JobDev) * n_jobs + sizeof(GeomDev) * n_geoms + 8 * (n_jobs + 1) + 8 * n_jobs;
+    b += cap * (8 + 8 + 4 * 5);                  // raw singles
+    b += hcap * (8 + 8 + 4 * 4 + 12 + 4);        // hits
+    b += ocap * 12;                              // overflow list
+    b += cap * (2 * 8 + 2 * 4) + 256 * 4 * tiles + 128;  // sort
+    b += cap * (8 + 8 + 4 * 5);                  // sorted singles
+    b += cap + 4 * tiles + 2 * 4 * (cap / 2 + 1); // coincidences
+    b += 8 * (n_jobs + 1) * 2 + 8 * n_jobs * 3;  // per-job statistics
+    return b + 64 * 256;                         // alignment slack
 }
 
 int run_with_retry(Run &R) {
@@ -320,6 +383,8 @@ void fill_counts(const Run &R, int job, uint64_t n_decays, int64_t n_crystals, g
     c->transport_ms = R.transport_ms;
     c->digitizer_ms = R.digitizer_ms;
     c->h2d_bytes = R.h2d_bytes;
+    c->wave_iterations = H.counters[6];
+    c->wave_lanes = H.counters[7];
 }
 
 }  // namespace gpet
@@ -330,21 +395,21 @@ extern "C" int gpet_simulate(gpet_scanner *sc, const gpet_source *src, const gpe
                              uint64_t seed, const gpet_options *opt, gpet_result **out) {
     if (!out) return gpet_fail(GPET_ERR_INVALID_ARG, "out is NULL");
     JobDev J;
-    int st = gpet_make_job(sc, src, dg, n_decays, seed, J);
+    int st = gpet_make_job(sc, src, dg, n_decays, seed, J, opt ? opt->h_begin : 0, opt ? opt->h_end : 0);
     if (st != GPET_OK) return st;
     gpet_result *res = new (std::nothrow) gpet_result();
     if (!res) return gpet_fail(GPET_ERR_OOM, "host allocation of the result failed");
     res->run = std::make_shared<Run>();
     Run &R = *res->run;
-    st = run_default_cfg(R, opt);
+    st = run_default_cfg(R, opt, sc);
     if (st != GPET_OK) { delete res; return st; }
     R.jobs = {J};
     R.geoms = {sc->g};
     R.job_crystals = {sc->n_crystals};
     R.windows = {(uint64_t)std::llround(dg->coinc_window_ns * 1000.0)};
-    R.caps.singles = std::max<uint64_t>(65536, n_decays * 6 / 10);
-    R.caps.hits = R.keep_hits ? std::max<uint64_t>(65536, n_decays * 5 / 2) : 0;
-    R.caps.ovf = std::max<uint64_t>(4096, n_decays / 256);
+    R.caps.singles = std::max<uint64_t>(65536, J.n_hist * 6 / 10);
+    R.caps.hits = R.keep_hits ? std::max<uint64_t>(65536, J.n_hist * 5 / 2) : 0;
+    R.caps.ovf = std::max<uint64_t>(4096, J.n_hist / 256);
     st = run_with_retry(R);
     if (st != GPET_OK) {
         delete res;

@@ -50,9 +50,9 @@ __device__ __forceinline__ void warp_refill(const WorkDev &W, uint32_t need, uin
             }
             pool_job = chunk_job(W, c);
             const uint64_t h0 = (uint64_t)(c - W.chunk_start[pool_job]) * W.chunk_size;
-            const uint64_t nd = W.jobs[pool_job].n_decays;
-            pool_next = h0;
-            pool_end = min(h0 + (uint64_t)W.chunk_size, nd);
+            const uint64_t base = W.jobs[pool_job].h_base;
+            pool_next = base + h0;
+            pool_end = base + min(h0 + (uint64_t)W.chunk_size, W.jobs[pool_job].n_hist);
             continue;
         }
         const uint32_t cnt = (uint32_t)__popc(need);
@@ -111,7 +111,6 @@ __global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int
             case kPhPhantom: st = ev_phantom(J, W, s, cnt); break;
             case kPhFlight: ev_flight(J, g, s, cnt); break;
             case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, S, cnt); break;
-            case kPhCompton: st = ev_compton<true>(J, g, O, s, SL, S, cnt); break;
             default: break;
         }
         if (st != kStatusOk) {          // iteration cap hit: abandon the history, flag the run
@@ -160,7 +159,6 @@ __global__ void __launch_bounds__(128) k_transport_redo(WorkDev W, OutDev O) {
                     case kPhPhantom: st = ev_phantom(J, W, s, cnt); break;
                     case kPhFlight: ev_flight(J, g, s, cnt); break;
                     case kPhPanel: st = ev_panel<false>(J, g, W, O, s, SL, S, cnt); break;
-                    case kPhCompton: st = ev_compton<false>(J, g, O, s, SL, S, cnt); break;
                     default: break;
                 }
                 if (st != kStatusOk) { status |= st; s.phase = kPhIdle; }

@@ -15,11 +15,8 @@
 
 namespace gpet {
 
-// history phases; a real Compton interaction is deferred to its own phase so
-// that the rejection sampling and rotation run as one wavefront
-enum : uint32_t {
-    kPhIdle = 0, kPhSource = 1, kPhPhantom = 2, kPhFlight = 3, kPhPanel = 4, kPhCompton = 5, kPhFinish = 6
-};
+// history phases
+enum : uint32_t { kPhIdle = 0, kPhSource = 1, kPhPhantom = 2, kPhFlight = 3, kPhPanel = 4, kPhFinish = 5 };
 
 // per-history singles list: unit ids, energy sums, earliest time offset
 // (t - t0 in ps); `stride` separates consecutive entries of one history
@@ -88,10 +85,6 @@ struct PState {
     float E, path, trem;
     int32_t job, panel, last;
     uint32_t sph, sdet, gamma, phase, nsing, ovf;
-    // pending Compton interaction: azimuth draw, crystal id (-1: none), module << 8 | layer
-    uint32_t cu;
-    int32_t icrys;
-    uint32_t imod;
 };
 
 struct Counters {
@@ -132,10 +125,18 @@ __device__ __forceinline__ void photon_done(const JobDev &J, PState &s) {
     }
 }
 
-// smallest voxel with cdf > target (binary search on the FP64 prefix sums)
+// Smallest voxel with cdf > target.  A guide table (Chen & Asau) narrows the
+// search: guide[k] is the first voxel whose prefix sum falls in bucket k or
+// later, the bucket of a value x being floor(x * gscale) computed exactly as
+// when the table was built, so the answer lies in [guide[b], guide[b + 1]].
 __device__ __forceinline__ int64_t pick_voxel(const JobDev &J, double target) {
     if (target >= J.ph_total) return J.ph_last_active;
     int64_t lo = 0, hi = J.ph_n - 1;
+    if (J.ph_guide) {
+        const int b = min((int)(target * J.ph_gscale), J.ph_buckets - 1);
+        lo = __ldg(J.ph_guide + b);
+        if (b + 1 < J.ph_buckets) hi = min(hi, (int64_t)__ldg(J.ph_guide + b + 1));
+    }
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
         if (__ldg(J.ph_cdf + mid) > target) hi = mid; else lo = mid + 1;
@@ -209,10 +210,15 @@ __device__ __forceinline__ int ev_phantom(const JobDev &J, const WorkDev &W, PSt
     const float mu_m = fmaf(J.ph_mu_c511[m], xs.g, pe);
     if (u01(r.y) * mu_maj >= mu_m) return kStatusOk;          // virtual
     if (u01(r.z) * mu_m < pe) { photon_done(J, s); return kStatusOk; }   // photoelectric
-    (void)step_id;
-    s.cu = r.w;                                                 // Compton: next phase
-    s.icrys = -1;
-    s.phase = kPhCompton;
+    float xm1;                                                   // Compton (Klein-Nishina)
+    const int nt = kahn_sample(J.seed, s.h, kTagPhantom, s.gamma, step_id, s.E, xm1);
+    if (nt < 0) return kStatusTimeout;
+    cnt.trials += (uint32_t)nt;
+    const float omc = xm1 / (s.E * kInvMec2);
+    rotate_dir(s.dx, s.dy, s.dz, omc, u01(r.w));
+    const float Ep = s.E / (1.0f + xm1);
+    if (Ep < J.e_cut) { photon_done(J, s); return kStatusOk; }
+    s.E = Ep;
     return kStatusOk;
 }
 
@@ -318,54 +324,34 @@ __device__ __forceinline__ int ev_panel(const JobDev &J, const GeomDev &g, const
     const float pe = g.mu_pe511[L.mat] * xs.r3;
     const float mu_m = fmaf(g.mu_c511[L.mat], xs.g, pe);
     if (u01(r.y) * mu_maj >= mu_m) return kStatusOk;   // virtual
-    if (u01(r.z) * mu_m < pe) {                        // photoelectric: deposit everything
-        if (L.crystal >= 0)
-            record_hit<kTallies>(J, g, O, s, SL, max_entries, cnt, L.crystal, L.module, L.layer, step_id, s.E);
-        photon_done(J, s);
-        return kStatusOk;
+    float dep;
+    bool dead = false;
+    if (u01(r.z) * mu_m < pe) {                        // photoelectric
+        dep = s.E;
+        dead = true;
+    } else {                                           // Compton (Klein-Nishina)
+        float xm1;
+        const int nt = kahn_sample(J.seed, s.h, kTagDetector, s.gamma, step_id, s.E, xm1);
+        if (nt < 0) return kStatusTimeout;
+        cnt.trials += (uint32_t)nt;
+        const float omc = xm1 / (s.E * kInvMec2);
+        // the panel frame (w, u, v) is a rotation of (x, y, z) about the axis
+        rotate_dir(s.dx, s.dy, s.dz, omc, u01(r.w));
+        const float Ep = s.E / (1.0f + xm1);
+        if (Ep < J.e_cut) {
+            dep = s.E;
+            dead = true;
+        } else {
+            dep = s.E * xm1 / (1.0f + xm1);
+            s.E = Ep;
+        }
     }
-    s.cu = r.w;                                        // Compton (Klein-Nishina): next phase
-    s.icrys = L.crystal;
-    s.imod = ((uint32_t)L.module << 8) | ((uint32_t)L.layer & 0xFFu);
-    s.phase = kPhCompton;
+    if (L.crystal >= 0)
+        record_hit<kTallies>(J, g, O, s, SL, max_entries, cnt, L.crystal, L.module, L.layer, step_id, dep);
+    if (dead) { photon_done(J, s); return kStatusOk; }
+    s.trem = panel_exit(g, s.x, s.y, s.z, s.dx, s.dy, s.dz);
     return kStatusOk;
 }
-
-// a deferred Compton interaction, in the phantom (panel < 0) or in a panel:
-// Kahn sampling of Klein-Nishina, rotation about the old direction, deposit,
-// hit record, cutoff
-template <bool kTallies>
-__device__ __forceinline__ int ev_compton(const JobDev &J, const GeomDev &g, const OutDev &O, PState &s,
-                                          const SinglesList &SL, int max_entries, Counters &cnt) {
-    const bool in_panel = s.panel >= 0;
-    const uint32_t step_id = (in_panel ? s.sdet : s.sph) - 1u;
-    float xm1;
-    const int nt = kahn_sample(J.seed, s.h, in_panel ? kTagDetector : kTagPhantom, s.gamma, step_id, s.E, xm1);
-    if (nt < 0) return kStatusTimeout;
-    cnt.trials += (uint32_t)nt;
-    const float omc = xm1 / (s.E * kInvMec2);
-    // the panel frame (w, u, v) is a rotation of (x, y, z) about the axis
-    rotate_dir(s.dx, s.dy, s.dz, omc, u01(s.cu));
-    const float Ep = s.E / (1.0f + xm1);
-    const bool dead = Ep < J.e_cut;
-    const float dep = dead ? s.E : s.E * xm1 / (1.0f + xm1);
-    if (!dead) s.E = Ep;
-    if (!in_panel) {
-        if (dead) photon_done(J, s); else s.phase = kPhPhantom;
-        return kStatusOk;
-    }
-    if (s.icrys >= 0)
-        record_hit<kTallies>(J, g, O, s, SL, max_entries, cnt, s.icrys, (int)(s.imod >> 8), (int)(s.imod & 0xFFu),
-                             step_id, dep);
-    if (dead) {
-        photon_done(J, s);
-    } else {
-        s.trem = panel_exit(g, s.x, s.y, s.z, s.dx, s.dy, s.dz);
-        s.phase = kPhPanel;
-    }
-    return kStatusOk;
-}
-
 
 // digitizer for one finished history: blur, window, warp-aggregated append
 // (call with the lanes of `mask` converged; `active` lanes own a history)

@@ -1,14 +1,15 @@
 // transport_wave.cu -- wavefront transport kernel with warp-ballot regrouping.
 //
-// Each warp keeps a pool of 64 history slots in shared memory (structure of
+// Each warp keeps a pool of 32 x depth history slots in shared memory (structure of
 // arrays, one 32-bit word per field and slot).  Every iteration the warp
 //   1. refills idle slots with new history ids from the chunked work queue,
-//   2. ballots the phase of all 64 slots (decay, phantom step, flight, panel
-//      step, Compton interaction) and picks the most populated phase,
+//   2. ballots the phase of all slots (decay, phantom step, flight, panel
+//      step, finish) and picks the most populated phase,
 //   3. maps its 32 lanes onto the slots in that phase (__fns over the ballot
 //      masks), so every lane runs the same event code,
-//   4. runs up to `compact_every` events of that phase per lane, stores the
-//      state back, and emits the singles of histories that finished.
+//   4. runs up to `compact_every` events of that phase per lane and stores
+//      the state back; finished histories wait in their slot until the
+//      finish phase (blur, window, append of their singles) is chosen.
 // The events are the ones of the per-lane kernel (transport.cuh), so the two
 // kernels produce the same histories bit for bit.
 #include "internal.h"
@@ -17,12 +18,13 @@
 namespace gpet {
 
 constexpr int kWaveWarps = 4;           // warps per CTA
-constexpr int kPool = 64;               // slots per warp
 constexpr int kWaveS = 6;               // singles-list entries per history (overflow -> redo kernel)
-constexpr int kWords = 26;              // 32-bit words of state per slot
+constexpr int kWords = 23;              // 32-bit words of state per slot
 
-// shared-memory footprint of one warp's pool
+// shared-memory footprint of one warp's pool of 32 * SPL slots
+template <int SPL>
 struct WarpPool {
+    static constexpr int kPool = 32 * SPL;
     uint32_t st[kWords][kPool];
     uint32_t sl_unit[kWaveS * kPool];
     float sl_e[kWaveS * kPool];
@@ -31,17 +33,15 @@ struct WarpPool {
 
 enum : int {
     kWh0 = 0, kWh1, kWt0, kWt1, kWx, kWy, kWz, kWdx, kWdy, kWdz, kWx0, kWy0, kWz0, kWox, kWoy, kWoz, kWE, kWpath,
-    kWtrem, kWjob, kWpack, kWsteps, kWcu, kWicrys, kWimod
+    kWtrem, kWjob, kWpack, kWsteps
 };
 
-__device__ __forceinline__ uint32_t pool_phase(const WarpPool &P, int q) { return (P.st[kWpack][q] >> 16) & 7u; }
-
-__device__ __forceinline__ void pool_set_phase(WarpPool &P, int q, uint32_t ph) {
-    P.st[kWpack][q] = (P.st[kWpack][q] & ~(7u << 16)) | (ph << 16);
-}
+template <class Pool>
+__device__ __forceinline__ uint32_t pool_phase(const Pool &P, int q) { return (P.st[kWpack][q] >> 16) & 7u; }
 
 // packed word: [0:7) panel+1, [7:14) last+1, [14] gamma, [16:19) phase, [19:24) nsing, [24] ovf
-__device__ __forceinline__ void pool_load(const WarpPool &P, int q, PState &s) {
+template <class Pool>
+__device__ __forceinline__ void pool_load(const Pool &P, int q, PState &s) {
     s.h = ((uint64_t)P.st[kWh1][q] << 32) | P.st[kWh0][q];
     s.t0 = ((uint64_t)P.st[kWt1][q] << 32) | P.st[kWt0][q];
     s.x = __uint_as_float(P.st[kWx][q]);
@@ -70,12 +70,10 @@ __device__ __forceinline__ void pool_load(const WarpPool &P, int q, PState &s) {
     const uint32_t sw = P.st[kWsteps][q];
     s.sph = sw & 0xFFFFu;
     s.sdet = sw >> 16;
-    s.cu = P.st[kWcu][q];
-    s.icrys = (int32_t)P.st[kWicrys][q];
-    s.imod = P.st[kWimod][q];
 }
 
-__device__ __forceinline__ void pool_store(WarpPool &P, int q, const PState &s) {
+template <class Pool>
+__device__ __forceinline__ void pool_store(Pool &P, int q, const PState &s) {
     P.st[kWh0][q] = (uint32_t)s.h;
     P.st[kWh1][q] = (uint32_t)(s.h >> 32);
     P.st[kWt0][q] = (uint32_t)s.t0;
@@ -99,9 +97,6 @@ __device__ __forceinline__ void pool_store(WarpPool &P, int q, const PState &s) 
     P.st[kWpack][q] = (uint32_t)(s.panel + 1) | ((uint32_t)(s.last + 1) << 7) | (s.gamma << 14) | (s.phase << 16) |
                       (s.nsing << 19) | (s.ovf << 24);
     P.st[kWsteps][q] = (s.sph & 0xFFFFu) | (s.sdet << 16);
-    P.st[kWcu][q] = s.cu;
-    P.st[kWicrys][q] = (uint32_t)s.icrys;
-    P.st[kWimod][q] = s.imod;
 }
 
 // warp-wide refill of the idle slots of one half of the pool (see transport.cu)
@@ -126,8 +121,9 @@ __device__ void warp_refill_wave(const WorkDev &W, uint32_t need, uint64_t &pool
             }
             pool_job = lo;
             const uint64_t h0 = (uint64_t)(c - W.chunk_start[lo]) * W.chunk_size;
-            pool_next = h0;
-            pool_end = min(h0 + (uint64_t)W.chunk_size, W.jobs[lo].n_decays);
+            const uint64_t base = W.jobs[lo].h_base;
+            pool_next = base + h0;
+            pool_end = base + min(h0 + (uint64_t)W.chunk_size, W.jobs[lo].n_hist);
             continue;
         }
         const uint32_t cnt = (uint32_t)__popc(need);
@@ -143,15 +139,18 @@ __device__ void warp_refill_wave(const WorkDev &W, uint32_t need, uint64_t &pool
     }
 }
 
+template <int SPL>
 __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, OutDev O, int ng_smem, int repeat) {
+    using Pool = WarpPool<SPL>;
+    constexpr int kPool = Pool::kPool;
     extern __shared__ __align__(16) uint8_t smem[];
     GeomDev *sgeom = reinterpret_cast<GeomDev *>(smem);
-    WarpPool *pools = reinterpret_cast<WarpPool *>(sgeom + ng_smem);
+    Pool *pools = reinterpret_cast<Pool *>(sgeom + ng_smem);
     stage_geometry(W, sgeom, ng_smem);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpPool &P = pools[wid];
-    P.st[kWpack][lane] = 0;        // phase idle
-    P.st[kWpack][lane + 32] = 0;
+    Pool &P = pools[wid];
+#pragma unroll
+    for (int g = 0; g < SPL; ++g) P.st[kWpack][g * 32 + lane] = 0;  // every slot idle
     __syncthreads();
 
     Counters cnt = {0, 0, 0, 0, 0, 0};
@@ -159,12 +158,13 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
     int pool_job = 0;
     bool exhausted = false;
     int status = kStatusOk;
+    unsigned long long iters = 0, lanes_used = 0;   // wavefront fill diagnostics
 
     for (;;) {
-        // 1. refill idle slots (two halves of 32)
+        // 1. refill idle slots, 32 at a time
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int q = half * 32 + lane;
+        for (int g = 0; g < SPL; ++g) {
+            const int q = g * 32 + lane;
             const uint32_t need = __ballot_sync(kFullMask, pool_phase(P, q) == kPhIdle);
             if (need && !exhausted) {
                 bool got;
@@ -180,28 +180,57 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
             }
         }
         __syncwarp();
-        // 2. phase census over the 64 slots
-        const uint32_t ph0 = pool_phase(P, lane), ph1 = pool_phase(P, lane + 32);
-        uint32_t best_b0 = 0, best_b1 = 0;
+        // 2. phase census over the pool
+        uint32_t ph[SPL];
+#pragma unroll
+        for (int g = 0; g < SPL; ++g) ph[g] = pool_phase(P, g * 32 + lane);
+        uint32_t best_b[SPL];
+#pragma unroll
+        for (int g = 0; g < SPL; ++g) best_b[g] = 0;
         int best_n = 0;
         uint32_t best_p = kPhIdle;
 #pragma unroll
-        for (uint32_t p = kPhSource; p <= kPhCompton; ++p) {
-            const uint32_t b0 = __ballot_sync(kFullMask, ph0 == p), b1 = __ballot_sync(kFullMask, ph1 == p);
-            const int n = __popc(b0) + __popc(b1);
-            if (n > best_n) { best_n = n; best_b0 = b0; best_b1 = b1; best_p = p; }
+        for (uint32_t p = kPhSource; p <= kPhFinish; ++p) {
+            uint32_t b[SPL];
+            int n = 0;
+#pragma unroll
+            for (int g = 0; g < SPL; ++g) { b[g] = __ballot_sync(kFullMask, ph[g] == p); n += __popc(b[g]); }
+            if (n > best_n) {
+                best_n = n;
+                best_p = p;
+#pragma unroll
+                for (int g = 0; g < SPL; ++g) best_b[g] = b[g];
+            }
         }
         if (best_n == 0) break;  // every slot idle after a refill: the queue is exhausted
-        // 3. lanes onto the slots of that phase
-        const int n0 = __popc(best_b0);
+        // 3. lane i takes the i-th slot of that phase
         const bool active = lane < best_n;
         int q = 0;
-        if (active) q = lane < n0 ? (int)__fns(best_b0, 0, lane + 1) : 32 + (int)__fns(best_b1, 0, lane - n0 + 1);
+        if (active) {
+            int rank = lane;
+#pragma unroll
+            for (int g = 0; g < SPL; ++g) {
+                const int c = __popc(best_b[g]);
+                if (rank >= 0 && rank < c) q = g * 32 + (int)__fns(best_b[g], 0, rank + 1);
+                rank -= c;
+            }
+        }
+        ++iters;
+        lanes_used += (unsigned long long)min(best_n, 32);
         // 4. events
         PState s;
         s.phase = kPhIdle;
         s.job = 0;
         const SinglesList SL{P.sl_unit + q, P.sl_e + q, P.sl_dt + q, kPool};
+        if (best_p == kPhFinish) {
+            // finished histories as one wavefront: blur, window, append
+            if (active) pool_load(P, q, s);
+            __syncwarp();
+            ev_finish(W.jobs, W.geoms, O, s, active, SL, kFullMask);
+            if (active) P.st[kWpack][q] = 0;   // slot idle
+            __syncwarp();
+            continue;
+        }
         if (active) {
             pool_load(P, q, s);
             const JobDev &J = W.jobs[s.job];
@@ -213,7 +242,6 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
                     case kPhPhantom: st = ev_phantom(J, W, s, cnt); break;
                     case kPhFlight: ev_flight(J, g, s, cnt); break;
                     case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, kWaveS, cnt); break;
-                    case kPhCompton: st = ev_compton<true>(J, g, O, s, SL, kWaveS, cnt); break;
                     default: break;
                 }
                 if (st != kStatusOk) {
@@ -221,14 +249,8 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
                     s.phase = kPhIdle;
                 }
             }
+            pool_store(P, q, s);
         }
-        __syncwarp();
-        const bool fin = active && s.phase == kPhFinish;
-        if (__any_sync(kFullMask, fin)) {
-            ev_finish(W.jobs, W.geoms, O, s, fin, SL, kFullMask);
-            if (fin) s.phase = kPhIdle;
-        }
-        if (active) pool_store(P, q, s);
         __syncwarp();
     }
     // flush counters (all lanes converged here)
@@ -238,20 +260,34 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
         const uint32_t x = __reduce_add_sync(kFullMask, v[i]);
         if (lane == 0 && x) atomicAdd(O.counters + i, (unsigned long long)x);
     }
+    if (lane == 0) {
+        atomicAdd(O.counters + 6, iters);
+        atomicAdd(O.counters + 7, lanes_used);
+    }
     if (status) atomicOr(O.status, status);
 }
 
-cudaError_t launch_transport_wave(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
+template <int SPL>
+static cudaError_t launch_wave_spl(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
     const int ng = min(W.n_geoms, cfg.max_smem_geoms);
-    const size_t smem = (size_t)ng * sizeof(GeomDev) + sizeof(WarpPool) * kWaveWarps;
-    cudaError_t e = cudaFuncSetAttribute(k_transport_wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)ng * sizeof(GeomDev) + sizeof(WarpPool<SPL>) * kWaveWarps;
+    cudaError_t e = cudaFuncSetAttribute(k_transport_wave<SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_wave, kWaveWarps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_wave<SPL>, kWaveWarps * 32, smem);
     if (e != cudaSuccess) return e;
-    const int per_sm = max(1, occ);
-    k_transport_wave<<<cfg.sm_count * per_sm, kWaveWarps * 32, smem, st>>>(W, O, ng, max(1, cfg.compact_every));
+    const int per_sm = max(1, cfg.grid >= cfg.sm_count && cfg.grid / cfg.sm_count < occ ? cfg.grid / cfg.sm_count : occ);
+    k_transport_wave<SPL><<<cfg.sm_count * per_sm, kWaveWarps * 32, smem, st>>>(W, O, ng, max(1, cfg.compact_every));
     return cudaGetLastError();
+}
+
+cudaError_t launch_transport_wave(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
+    switch (cfg.pool_depth) {
+        case 3: return launch_wave_spl<3>(W, O, cfg, st);
+        case 4: return launch_wave_spl<4>(W, O, cfg, st);
+        default: return launch_wave_spl<2>(W, O, cfg, st);
+    }
 }
 
 }  // namespace gpet

@@ -1,0 +1,76 @@
+// tune.cu -- autotuner of the transport launch.  It times the candidate
+// launch forms on a pilot run of the caller's own workload (same scanner,
+// source and digitizer): the per-lane event loop at 1 or 2 CTAs per SM, and
+// the wavefront kernel at several regrouping intervals.  The fastest form is
+// returned and remembered per design class (panels, layers, phantom) and SM
+// count; launches that leave gpet_options.kernel at 0 use it.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "host.h"
+
+using namespace gpet;
+
+namespace {
+using Key = std::tuple<int, int, int, int>;  // panels, layers, phantom, SMs
+std::mutex g_tune_mutex;
+std::map<Key, gpet_options> g_tuned;
+
+Key key_of(const gpet_scanner *sc, int sms) {
+    return Key(sc->desc.n_panels, sc->desc.n_layers, sc->has_phantom ? 1 : 0, sms);
+}
+}  // namespace
+
+// tuned launch form for this scanner on this device (false: none recorded)
+bool gpet_tuned_options(const gpet_scanner *sc, int sms, gpet_options *out) {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    auto it = g_tuned.find(key_of(sc, sms));
+    if (it == g_tuned.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+extern "C" int gpet_autotune(gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg,
+                             uint64_t pilot_decays, uint64_t seed, gpet_options *best, float *best_ms) {
+    if (!sc || !src || !dg || !best) return gpet_fail(GPET_ERR_INVALID_ARG, "NULL argument");
+    if (pilot_decays < 1000) return gpet_fail(GPET_ERR_INVALID_ARG, "pilot run needs >= 1000 decays");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "device query");
+    struct Cand { int kernel, bps, compact, depth; };
+    const Cand cands[] = {{kKernelLoop, 2, 1, 0}, {kKernelLoop, 1, 1, 0}, {kKernelWave, 0, 1, 2},
+                          {kKernelWave, 0, 2, 2}, {kKernelWave, 0, 4, 2}, {kKernelWave, 0, 1, 3},
+                          {kKernelWave, 0, 2, 3}, {kKernelWave, 0, 1, 4}};
+    float best_t = 1e30f;
+    gpet_options bo;
+    std::memset(&bo, 0, sizeof(bo));
+    for (const Cand &c : cands) {
+        gpet_options o;
+        std::memset(&o, 0, sizeof(o));
+        o.kernel = c.kernel;
+        o.blocks_per_sm = c.bps;
+        o.compact_every = c.compact;
+        o.pool_depth = c.depth;
+        float t = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {  // first repetition warms caches and pools
+            gpet_result *r = nullptr;
+            int st = gpet_simulate(sc, src, dg, pilot_decays, seed, &o, &r);
+            if (st != GPET_OK) return st;
+            if (rep > 0 && r->counts.transport_ms > 0.f) t = std::min(t, r->counts.transport_ms);
+            gpet_result_free(r);
+        }
+        if (t < best_t) { best_t = t; bo = o; }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tuned[key_of(sc, sms)] = bo;
+    }
+    *best = bo;
+    if (best_ms) *best_ms = best_t;
+    return GPET_OK;
+}

@@ -88,3 +88,16 @@ def test_null_arguments_are_errors(G):
     assert L.gpet_simulate(None, None, None, 1, 1, None, None) == -1
     L.gpet_result_free(None)
     L.gpet_destroy_scanner(None)
+
+
+def test_server_config_validation(G):
+    L = G.load()
+    h = C.c_void_p()
+    cfg = G.ServerConfig(0, 2, 16, G.options_struct())
+    assert L.gpet_server_create(C.byref(cfg), C.byref(h)) == -1
+    cfg = G.ServerConfig(10**9, 99, 16, G.options_struct())
+    assert L.gpet_server_create(C.byref(cfg), C.byref(h)) == -1
+    cfg = G.ServerConfig(10**9, 2, 5000, G.options_struct())
+    assert L.gpet_server_create(C.byref(cfg), C.byref(h)) == -1
+    assert L.gpet_server_poll(None, 1, None) == -1
+    L.gpet_server_destroy(None)

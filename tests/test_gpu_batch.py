@@ -81,3 +81,27 @@ def test_batch_of_sweep_positions(G, oracle):
         # allow the rare FP32/FP64 history flip: singles of at most a few histories differ
         assert abs(sc_["n_gpu"] - sc_["n_orc"]) <= 4 and sc_["n_common"] >= sc_["n_orc"] - 4, sc_
         assert np.all(np.diff(s["t_ps"].astype(np.int64)) >= 0)
+
+
+def test_history_shards_merge_to_the_whole_run(G):
+    """Two history ranges of one run (as two ranks would run them) merge to the
+    unsharded run: tallies add up, singles concatenate."""
+    from paper_2603_07327_gb300 import shard
+    sc = G.Scanner(W.config2_scanner("A"))
+    src, dg, n = W.point_source((0.0, 0.0, -9.0)), W.digitizer(), 1_000_003
+    full = sc.simulate(src, dg, n, 5, kernel=2)
+    parts, tallies = [], []
+    for rank in range(2):
+        h0, h1 = shard.history_range(n, rank, 2)
+        r = sc.simulate(src, dg, n, 5, kernel=2, h_begin=h0, h_end=h1)
+        parts.append(r.singles())
+        tallies.append(r.tallies())
+        assert np.all((r.singles()["h"] >= h0) & (r.singles()["h"] < h1))
+    c, e = shard.merge_tallies(tallies)
+    fc, fe = full.tallies()
+    assert np.array_equal(c, fc) and np.array_equal(e, fe)
+    m = shard.merge_singles(parts)
+    fs = full.singles()
+    order = np.lexsort((fs["h"], fs["unit"], fs["t_ps"]))
+    for f in shard.SINGLE_FIELDS:
+        assert np.array_equal(m[f], fs[f][order]), f
