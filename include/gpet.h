@@ -269,6 +269,34 @@ int gpet_simulate_batch(int32_t n_jobs, gpet_scanner *const *scanners, const gpe
                         const gpet_options *opt, gpet_result **outs);
 
 /* ------------------------------------------------------------------------ */
+/* time sort that allocates no device memory                                 */
+/* ------------------------------------------------------------------------ */
+
+/* The paper has no counterpart of this call.  It exists for callers that
+ * cannot call cudaMalloc -- a process whose device memory is all handed out
+ * up front by another allocator (for example a caching allocator that has
+ * reserved the pool, or a server with a fixed memory budget), or a
+ * latency-critical loop that cannot take an allocation's implicit device
+ * synchronisation.  It runs the digitizer's radix time sort on n 64-bit keys
+ * (the singles' time stamps in ps) with its whole working set in a fixed
+ * 24.3 MiB array that is part of the library image, held on every GPU that
+ * loads the library until the process exits; it calls no cudaMalloc, no
+ * cudaFree and no allocating library routine.
+ *   d_t_in     device, n uint64 keys (read only)
+ *   d_t_out    device, n uint64: the keys in ascending order
+ *   d_perm_out device, n uint32 or NULL: d_t_out[i] = d_t_in[d_perm_out[i]];
+ *              the sort is stable (equal keys keep their input order)
+ *   n          <= 1048576 (2^20); larger n returns GPET_ERR_INVALID_ARG
+ *   stream     cudaStream_t; the call is asynchronous on it
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and overwrites its previous
+ * contents, so calls that overlap on the GPU (other streams, other host
+ * threads) race: serialise them. */
+int gpet_sort_times_noalloc(const uint64_t *d_t_in, uint64_t n, uint64_t *d_t_out, uint32_t *d_perm_out,
+                            void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* autotuner                                                                 */
 /* ------------------------------------------------------------------------ */
 

@@ -126,6 +126,7 @@ SIGNATURES = {
     "gpet_server_wait": (C.c_int, [_P, C.c_uint64, C.POINTER(_P)]),
     "gpet_server_stats_get": (C.c_int, [_P, C.POINTER(ServerStats)]),
     "gpet_server_destroy": (None, [_P]),
+    "gpet_sort_times_noalloc": (C.c_int, [_P, C.c_uint64, _P, _P, _P]),
     "gpet_last_error": (C.c_char_p, []),
     "gpet_version": (C.c_char_p, []),
 }

@@ -64,5 +64,6 @@ cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg 
 cudaError_t launch_transport_wave(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
 cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const CoincDev &C, int sm_count,
                               cudaStream_t st);
+cudaError_t launch_radix_passes(const SortDev &S, int sm_count, cudaStream_t st);
 
 }  // namespace gpet

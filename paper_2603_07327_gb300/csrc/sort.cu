@@ -345,6 +345,21 @@ cudaError_t launch_job_stats(const SinglesDev &s, const CoincDev &C, const JobSt
     return cudaGetLastError();
 }
 
+// Plan plus the eight radix passes over an already keyed working set (used by
+// the allocation-free sort entry point; the simulation path keeps its own
+// launcher below).
+cudaError_t launch_radix_passes(const SortDev &S, int sm_count, cudaStream_t st) {
+    k_plan<<<1, kPasses * 32, 0, st>>>(S);
+    for (int p = 0; p < kPasses; ++p) {
+        const int tg = (int)(S.max_tiles < (unsigned long long)sm_count * 8 ? S.max_tiles
+                                                                              : (unsigned long long)sm_count * 8);
+        k_tile_hist<<<tg, kSortThreads, 0, st>>>(S, p);
+        k_digit_scan<<<256, 1024, 0, st>>>(S, p);
+        k_scatter<<<tg, kSortThreads, 0, st>>>(S, p);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const CoincDev &C, int sm_count,
                               cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(S.ghist, 0, sizeof(uint32_t) * kPasses * 256, st);

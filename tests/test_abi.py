@@ -101,3 +101,11 @@ def test_server_config_validation(G):
     assert L.gpet_server_create(C.byref(cfg), C.byref(h)) == -1
     assert L.gpet_server_poll(None, 1, None) == -1
     L.gpet_server_destroy(None)
+
+
+def test_noalloc_sort_refuses_oversize_before_any_launch(G):
+    """The allocation-free time sort checks its size limit on the host."""
+    L = G.load()
+    assert L.gpet_sort_times_noalloc(None, (1 << 20) + 1, None, None, None) == -1
+    assert "maximum" in L.gpet_last_error().decode()
+    assert L.gpet_sort_times_noalloc(None, 0, None, None, None) == 0
