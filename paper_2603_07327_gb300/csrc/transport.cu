@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int
         const GeomDev &g = J.geom < ng_smem ? sgeom[J.geom] : W.geoms[J.geom];
         int st = kStatusOk;
         switch (s.phase) {
-            case kPhSource: ev_source(J, s); break;
-            case kPhPhantom: st = ev_phantom(J, W, s, cnt); break;
+            case kPhSource: ev_source(J, g, s, cnt); break;
+            case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
             case kPhFlight: ev_flight(J, g, s, cnt); break;
             case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, S, cnt); break;
             default: break;
@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(128) k_transport_redo(WorkDev W, OutDev O) {
             while (s.phase != kPhFinish && s.phase != kPhIdle) {
                 int st = kStatusOk;
                 switch (s.phase) {
-                    case kPhSource: ev_source(J, s); break;
-                    case kPhPhantom: st = ev_phantom(J, W, s, cnt); break;
+                    case kPhSource: ev_source(J, g, s, cnt); break;
+                    case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
                     case kPhFlight: ev_flight(J, g, s, cnt); break;
                     case kPhPanel: st = ev_panel<false>(J, g, W, O, s, SL, S, cnt); break;
                     default: break;

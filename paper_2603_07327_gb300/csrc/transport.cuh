@@ -105,23 +105,44 @@ __device__ __forceinline__ bool in_phantom(const JobDev &J, float x, float y, fl
            z < J.ph_hi[2];
 }
 
-__device__ __forceinline__ void start_photon(const JobDev &J, PState &s) {
-    const float sg = s.gamma == 0 ? 1.0f : -1.0f;
-    s.x = s.x0; s.y = s.y0; s.z = s.z0;
-    s.dx = sg * s.ox; s.dy = sg * s.oy; s.dz = sg * s.oz;
-    s.E = kE0;
-    s.path = 0.0f;
-    s.sph = 0; s.sdet = 0;
-    s.panel = -1; s.last = -1;
-    s.phase = (J.has_phantom && in_phantom(J, s.x, s.y, s.z)) ? kPhPhantom : kPhFlight;
+// Start photon s.gamma of the history (and, when it is screened out at once,
+// the next one): into the phantom, into a flight, or straight to the end
+// when the axial screen shows it can meet no panel (that decision is its
+// flight, counted as one).
+__device__ __forceinline__ void start_photon(const JobDev &J, const GeomDev &g, PState &s, Counters &cnt) {
+    for (;;) {
+        const float sg = s.gamma == 0 ? 1.0f : -1.0f;
+        s.x = s.x0; s.y = s.y0; s.z = s.z0;
+        s.dx = sg * s.ox; s.dy = sg * s.oy; s.dz = sg * s.oz;
+        s.E = kE0;
+        s.path = 0.0f;
+        s.sph = 0; s.sdet = 0;
+        s.panel = -1; s.last = -1;
+        if (J.has_phantom && in_phantom(J, s.x, s.y, s.z)) { s.phase = kPhPhantom; return; }
+        if (!axial_miss(g, s.x, s.y, s.z, s.dx, s.dy, s.dz)) { s.phase = kPhFlight; return; }
+        cnt.flights++;
+        if (s.gamma == 0) { s.gamma = 1; continue; }
+        s.phase = kPhFinish;
+        return;
+    }
 }
 
-__device__ __forceinline__ void photon_done(const JobDev &J, PState &s) {
+__device__ __forceinline__ void photon_done(const JobDev &J, const GeomDev &g, PState &s, Counters &cnt) {
     if (s.gamma == 0) {
         s.gamma = 1;
-        start_photon(J, s);
+        start_photon(J, g, s, cnt);
     } else {
         s.phase = kPhFinish;
+    }
+}
+
+// a photon about to fly: screened out at once, or on to the flight event
+__device__ __forceinline__ void to_flight(const JobDev &J, const GeomDev &g, PState &s, Counters &cnt) {
+    if (axial_miss(g, s.x, s.y, s.z, s.dx, s.dy, s.dz)) {
+        cnt.flights++;
+        photon_done(J, g, s, cnt);
+    } else {
+        s.phase = kPhFlight;
     }
 }
 
@@ -145,7 +166,7 @@ __device__ __forceinline__ int64_t pick_voxel(const JobDev &J, double target) {
 }
 
 // decay of history h (Sec. 2.3): time, annihilation point, photon-0 direction
-__device__ __forceinline__ void ev_source(const JobDev &J, PState &s) {
+__device__ __forceinline__ void ev_source(const JobDev &J, const GeomDev &g, PState &s, Counters &cnt) {
     const uint4 r = draw(J.seed, s.h, kTagSource, 0u, 0u, 0u);
     const uint64_t r64 = ((uint64_t)r.x << 32) | r.y;
     s.t0 = __umul64hi(J.t_span_ps, r64);
@@ -174,11 +195,12 @@ __device__ __forceinline__ void ev_source(const JobDev &J, PState &s) {
     s.gamma = 0;
     s.nsing = 0;
     s.ovf = 0;
-    start_photon(J, s);
+    start_photon(J, g, s, cnt);
 }
 
 // one Woodcock step in the voxel phantom
-__device__ __forceinline__ int ev_phantom(const JobDev &J, const WorkDev &W, PState &s, Counters &cnt) {
+__device__ __forceinline__ int ev_phantom(const JobDev &J, const GeomDev &g, const WorkDev &W, PState &s,
+                                          Counters &cnt) {
     if (s.sph >= (uint32_t)kMaxSteps) return kStatusTimeout;
     const uint4 r = draw(J.seed, s.h, kTagPhantom, s.gamma, s.sph, 0u);
     const uint32_t step_id = s.sph++;
@@ -196,7 +218,7 @@ __device__ __forceinline__ int ev_phantom(const JobDev &J, const WorkDev &W, PSt
     if (step >= t_out) {
         s.x = fmaf(t_out, s.dx, s.x); s.y = fmaf(t_out, s.dy, s.y); s.z = fmaf(t_out, s.dz, s.z);
         s.path += t_out;
-        s.phase = kPhFlight;
+        to_flight(J, g, s, cnt);
         return kStatusOk;
     }
     s.x = fmaf(step, s.dx, s.x); s.y = fmaf(step, s.dy, s.y); s.z = fmaf(step, s.dz, s.z);
@@ -209,7 +231,7 @@ __device__ __forceinline__ int ev_phantom(const JobDev &J, const WorkDev &W, PSt
     const float pe = J.ph_mu_pe511[m] * xs.r3;
     const float mu_m = fmaf(J.ph_mu_c511[m], xs.g, pe);
     if (u01(r.y) * mu_maj >= mu_m) return kStatusOk;          // virtual
-    if (u01(r.z) * mu_m < pe) { photon_done(J, s); return kStatusOk; }   // photoelectric
+    if (u01(r.z) * mu_m < pe) { photon_done(J, g, s, cnt); return kStatusOk; }   // photoelectric
     float xm1;                                                   // Compton (Klein-Nishina)
     const int nt = kahn_sample(J.seed, s.h, kTagPhantom, s.gamma, step_id, s.E, xm1);
     if (nt < 0) return kStatusTimeout;
@@ -217,7 +239,7 @@ __device__ __forceinline__ int ev_phantom(const JobDev &J, const WorkDev &W, PSt
     const float omc = xm1 / (s.E * kInvMec2);
     rotate_dir(s.dx, s.dy, s.dz, omc, u01(r.w));
     const float Ep = s.E / (1.0f + xm1);
-    if (Ep < J.e_cut) { photon_done(J, s); return kStatusOk; }
+    if (Ep < J.e_cut) { photon_done(J, g, s, cnt); return kStatusOk; }
     s.E = Ep;
     return kStatusOk;
 }
@@ -227,7 +249,7 @@ __device__ __forceinline__ void ev_flight(const JobDev &J, const GeomDev &g, PSt
     cnt.flights++;
     float t_in, t_out;
     const int k = flight(g, s.x, s.y, s.z, s.dx, s.dy, s.dz, s.last, t_in, t_out);
-    if (k < 0) { photon_done(J, s); return; }
+    if (k < 0) { photon_done(J, g, s, cnt); return; }
     cnt.entered++;
     // entry point, then the panel-local frame (w, u, v)
     const float ex = fmaf(t_in, s.dx, s.x), ey = fmaf(t_in, s.dy, s.y), ez = fmaf(t_in, s.dz, s.z);
@@ -314,7 +336,7 @@ __device__ __forceinline__ int ev_panel(const JobDev &J, const GeomDev &g, const
         to_global(g, s);
         s.last = s.panel;
         s.panel = -1;
-        s.phase = kPhFlight;
+        to_flight(J, g, s, cnt);
         return kStatusOk;
     }
     s.x = fmaf(step, s.dx, s.x); s.y = fmaf(step, s.dy, s.y); s.z = fmaf(step, s.dz, s.z);
@@ -348,7 +370,7 @@ __device__ __forceinline__ int ev_panel(const JobDev &J, const GeomDev &g, const
     }
     if (L.crystal >= 0)
         record_hit<kTallies>(J, g, O, s, SL, max_entries, cnt, L.crystal, L.module, L.layer, step_id, dep);
-    if (dead) { photon_done(J, s); return kStatusOk; }
+    if (dead) { photon_done(J, g, s, cnt); return kStatusOk; }
     s.trem = panel_exit(g, s.x, s.y, s.z, s.dx, s.dy, s.dz);
     return kStatusOk;
 }

@@ -238,8 +238,8 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
             for (int r = 0; r < repeat && s.phase == best_p; ++r) {
                 int st = kStatusOk;
                 switch (best_p) {
-                    case kPhSource: ev_source(J, s); break;
-                    case kPhPhantom: st = ev_phantom(J, W, s, cnt); break;
+                    case kPhSource: ev_source(J, g, s, cnt); break;
+                    case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
                     case kPhFlight: ev_flight(J, g, s, cnt); break;
                     case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, kWaveS, cnt); break;
                     default: break;
