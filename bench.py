@@ -39,29 +39,33 @@ METRIC = "pairs tracked/s/GB300 batched vs plain; p50/p99 served-request latency
 N_POSITIONS = 61
 PAIRS_PER_POSITION = 10_000_000
 
-# Algorithmic lane-operations per event of the method, counted from the
-# arithmetic each step must do (not from compiled code):
-#   Philox4x32-10 block: 10 rounds x (2 wide multiplies = 4 ops, 4 xors, 2 key adds) = 100
-#   decay: 1 block + 64-bit time product + isotropic direction (sincospi, sqrt) = 160
-#   flight: per panel a slab test (4 projections, 3 reciprocals, 6 min/max, compares) = 25,
-#           plus 12 for the best-panel bookkeeping; entering a panel adds the frame change (20)
-#   detector step: 1 block, 4 uniforms, log, cross sections, position update, exit test,
-#           layer selection + module + crystal location, accept tests = 175
-#   phantom step: 1 block, log, exit distance, voxel index and gather, accept = 150
-#   Compton trial: 1 block, 3 uniforms, one Kahn branch and its test = 124
-#   crystal hit: kinematics, direction rotation, tallies, singles-list update = 60
-#   single: 1 block, Box-Muller (log, sqrt, cospi), blur, window, append = 150
-ALG = dict(source=160, flight_panel=25, flight_base=12, enter=20, det_step=175, ph_step=150, trial=124,
-           hit=60, single=150)
+# Algorithmic lane-operations per event of the method: the arithmetic each step
+# needs at its leanest (not counted from compiled code).  One Philox4x32-10
+# block is 10 rounds x (2 wide multiplies = 4 ops, 2 three-way xors, 2 key adds)
+# = 80.
+#   decay: 1 block, 4 uniforms, 64-bit time product, isotropic direction   130
+#   flight screen (every flight): distance to the ring, axial test            20
+#   flight test (flights the screen leaves): candidate azimuths, ~2 slab tests 140
+#   panel entry: frame change                                                 12
+#   detector step: 1 block, log, cross sections, move, exit test, layer
+#     selection + module + crystal location, accept tests                    165
+#   phantom step: 1 block, log, exit distance, voxel index + gather, accept   150
+#   Compton trial: 1 block, 3 uniforms, one Kahn branch and its test          100
+#   crystal hit: kinematics/rotation share, tallies, singles-list update       60
+#   single: 1 block, Box-Muller, blur, window, append                         140
+ALG = dict(source=130, screen=20, flight_test=140, enter=12, det_step=165, ph_step=150, trial=100, hit=60,
+           single=140)
 SM_COUNT_GB300 = 152
 LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 
 
-def alg_ops(c, n_panels):
-    return (c["n_decays"] * ALG["source"] + c["flights"] * (ALG["flight_panel"] * n_panels + ALG["flight_base"])
+def alg_ops(c, n_panels=None):
+    tested = c["flights"] - c.get("screened_flights", 0)
+    singles = c.get("singles_formed", 0) or c["hits"]
+    return (c["n_decays"] * ALG["source"] + c["flights"] * ALG["screen"] + tested * ALG["flight_test"]
             + c["entered"] * ALG["enter"] + c["det_steps"] * ALG["det_step"] + c["phantom_steps"] * ALG["ph_step"]
-            + c["compton_trials"] * ALG["trial"] + c["hits"] * (ALG["hit"] + ALG["single"]))
+            + c["compton_trials"] * ALG["trial"] + c["hits"] * ALG["hit"] + singles * ALG["single"])
 
 
 def sweep_jobs(rank=0, pairs=PAIRS_PER_POSITION, positions=N_POSITIONS):
@@ -116,6 +120,16 @@ class Clocks:
         os.unlink(self.f.name)
         return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
                     reasons=sorted(reasons), samples=len(sm))
+
+
+def _measured_hbm_gbs():
+    """Measured copy bandwidth of the GB300s (driver-written), else the
+    recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 def cpu_baseline(budget_s=12.0, threads=None):
@@ -315,10 +329,22 @@ def run_ours(args):
     ops = sum(alg_ops(c, n_panels) for c in counts)
     achieved = ops / (tr_ms / 1000.0)
     peak = SM_COUNT_GB300 * LANES_PER_SM * SM_MAX_MHZ * 1e6
+    kname = "k_transport_loop" if args.kernel == 1 else "k_transport_wave"
     roof = dict(bound="alu", achieved=achieved, peak=peak, unit="lane-ops/s", frac=achieved / peak,
-                traffic=args.traffic, kernel="k_transport_loop",
+                traffic=args.traffic, kernel=kname,
                 peak_note="152 SMs x 128 FP32/INT lanes x 2070 MHz (recipe unit counts and max clock)",
                 transport_share=tr_ms / (tr_ms + dg_ms))
+
+    # digitizer back end (time sort + coincidences), HBM-bound: algorithmic bytes
+    # per single = key build 24 + 8 radix passes x 32 (histogram read 8, scatter
+    # read 12 + write 12) + gather 76 + coincidence pass 34 = 390
+    singles_step = sum(c["singles"] for c in counts) / args.steps
+    dig_bytes = 390.0 * singles_step
+    dig_gbs = dig_bytes / (dg_ms / args.steps / 1000.0) / 1e9 if dg_ms > 0 else None
+    hbm_peak = _measured_hbm_gbs()
+    roof_dig = dict(bound="hbm", achieved=dig_gbs, peak=hbm_peak, unit="GB/s",
+                    frac=(dig_gbs / hbm_peak) if dig_gbs else None, traffic=None,
+                    bytes_per_single=390, note="time sort + coincidence sorting; peak = measured copy GB/s")
 
     # end to end through the C ABI: host descriptors in (one batch call over the
     # sweep), coincidences, singles and tallies of every job copied to host memory
@@ -355,7 +381,7 @@ def run_ours(args):
                             pairs_per_step=pairs_per_step,
                             l2="flushed between steps (256 MB write)", kernel=args.kernel or "default",
                             parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
-                wall_s=wall, gpu_launches=None, roofline=roof, clocks=clk,
+                wall_s=wall, gpu_launches=None, roofline=roof, roofline_digitizer=roof_dig, clocks=clk,
                 e2e=dict(value=pairs_per_step * world / e2e_dt, unit="pairs/s", h2d_bytes_per_step=h2d,
                          d2h_bytes_per_step=d2h),
                 stages=dict(transport_ms_per_step=tr_ms / args.steps, digitizer_ms_per_step=dg_ms / args.steps),

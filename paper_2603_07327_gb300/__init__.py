@@ -80,7 +80,8 @@ class Counts(C.Structure):
                 ("flights", C.c_uint64), ("compton_trials", C.c_uint64), ("entered", C.c_uint64),
                 ("phantom_steps", C.c_uint64), ("status", C.c_int32), ("transport_ms", C.c_float),
                 ("digitizer_ms", C.c_float), ("h2d_bytes", C.c_uint64), ("wave_iterations", C.c_uint64),
-                ("wave_lanes", C.c_uint64), ("latency_ms", C.c_double)]
+                ("wave_lanes", C.c_uint64), ("screened_flights", C.c_uint64), ("singles_formed", C.c_uint64),
+                ("latency_ms", C.c_double)]
 
 
 class ServerConfig(C.Structure):

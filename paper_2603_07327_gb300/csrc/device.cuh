@@ -288,29 +288,6 @@ __device__ __forceinline__ void panel_slab(const GeomDev &g, int k, float x, flo
     }
 }
 
-// True when the ray (x, d) cannot enter any panel.  Every panel box lies at
-// distance >= R from the axis and within |v| <= half_v; a ray that starts
-// inside the circle R reaches that annulus at t1 and from then on moves
-// monotonically in z, so if it is already beyond the axial extent there and
-// moving away (or runs parallel to the axis) it misses every panel.  A ray
-// starting outside the circle is screened only when z is already beyond the
-// extent and moving away.  1e-3 mm of margin covers FP32 rounding.
-__device__ __forceinline__ bool axial_miss(const GeomDev &g, float x, float y, float z, float dx, float dy,
-                                           float dz) {
-    const float c0 = fmaf(x, x, y * y);
-    float z1 = z;
-    if (c0 < g.R2 * 0.9999f) {
-        const float a = fmaf(dx, dx, dy * dy);
-        if (a <= 0.0f) return true;
-        const float b = fmaf(x, dx, y * dy);
-        const float d1 = g.R2 - c0;
-        const float s1 = sqrtf(fmaf(b, b, a * d1));
-        const float t1 = b > 0.0f ? __fdividef(d1, b + s1) : __fdividef(s1 - b, a);
-        z1 = fmaf(t1, dz, z);
-    }
-    return (z1 > g.half_v + 1e-3f && dz >= 0.0f) || (z1 < -g.half_v - 1e-3f && dz <= 0.0f);
-}
-
 // atan2 from the odd polynomial of Abramowitz & Stegun 4.4.47 (|error| <= 1e-5
 // rad on [-1, 1]) with octant reduction; used only to pick candidate panels,
 // where a 1e-3 rad margin absorbs its error
@@ -329,6 +306,8 @@ __device__ __forceinline__ float atan2_as(float y, float x) {
     return y < 0.0f ? -r : r;
 }
 
+constexpr int kFlightScreened = -2;  // flight() result: no panel, decided without slab tests
+
 // Line-plane flight (Sec. 2.1): nearest panel entered along (x, d), skipping
 // `skip`.  A ray that starts inside the circle of radius R (every inner face
 // is tangent to it) crosses the annulus holding all panel boxes exactly once,
@@ -345,7 +324,7 @@ __device__ __forceinline__ int flight(const GeomDev &g, float x, float y, float 
         if (a <= 0.0f) {
             t_in = bi;
             t_out = bo;
-            return -1;  // parallel to the axis inside the ring: never reaches a panel
+            return kFlightScreened;  // parallel to the axis inside the ring: never reaches a panel
         }
         const float b = fmaf(x, dx, y * dy);
         // exit distances of the circles R and R_out (stable roots, c0 < R^2)
@@ -358,7 +337,7 @@ __device__ __forceinline__ int flight(const GeomDev &g, float x, float y, float 
         if ((z1 > g.half_v + 1e-3f && dz >= 0.0f) || (z1 < -g.half_v - 1e-3f && dz <= 0.0f)) {
             t_in = bi;
             t_out = bo;
-            return -1;
+            return kFlightScreened;
         }
         const float t2 = b > 0.0f ? __fdividef(d2, b + s2) : __fdividef(s2 - b, a);
         const float p1 = atan2_as(fmaf(t1, dy, y), fmaf(t1, dx, x)) - g.phi0;

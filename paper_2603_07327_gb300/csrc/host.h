@@ -49,7 +49,9 @@ struct RunCaps {
 
 // device header read back after a run (all zeroed before launch)
 struct RunHeader {
-    unsigned long long counters[8];   // det_steps, flights, trials, entered, phantom_steps, hits
+    // det_steps, flights, trials, entered, phantom_steps, hits, wavefront iterations,
+    // wavefront lanes, screened flights, singles formed
+    unsigned long long counters[12];
     unsigned long long n_singles, n_hits, n_ovf, n_sorted, n_coinc, next_chunk;
     int status;
     int pad[3];

@@ -8,7 +8,7 @@
 
 namespace gpet {
 
-enum { kKernelDefault = 0, kKernelLoop = 1, kKernelWave = 2 };
+enum { kKernelDefault = 0, kKernelLoop = 1, kKernelWave = 2, kKernelCta = 3 };
 
 struct LaunchCfg {
     int grid;            // CTAs of the transport kernel
@@ -62,6 +62,7 @@ struct JobStatsDev {
 cudaError_t launch_job_stats(const SinglesDev &s, const CoincDev &C, const JobStatsDev &J, cudaStream_t st);
 cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
 cudaError_t launch_transport_wave(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
+cudaError_t launch_transport_cta(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
 cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const CoincDev &C, int sm_count,
                               cudaStream_t st);
 cudaError_t launch_radix_passes(const SortDev &S, int sm_count, cudaStream_t st);

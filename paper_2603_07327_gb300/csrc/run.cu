@@ -61,6 +61,7 @@ int run_default_cfg(Run &R, const gpet_options *opt_in, const gpet_scanner *sc) 
         if (merged.blocks_per_sm == 0) merged.blocks_per_sm = tuned.blocks_per_sm;
         if (merged.compact_every == 0) merged.compact_every = tuned.compact_every;
         if (merged.pool_depth == 0) merged.pool_depth = tuned.pool_depth;
+        if (merged.block_size == 0) merged.block_size = tuned.block_size;
         opt = &merged;
     }
     int dev = 0;
@@ -72,14 +73,18 @@ int run_default_cfg(Run &R, const gpet_options *opt_in, const gpet_scanner *sc) 
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaDeviceGetAttribute");
     R.cfg.sm_count = sms;
-    R.cfg.block_size = (opt && opt->block_size > 0) ? opt->block_size : 256;
-    if (R.cfg.block_size % 32 || R.cfg.block_size > 256)
-        return gpet_fail(GPET_ERR_INVALID_ARG, "block_size %d must be a multiple of 32 and <= 256", R.cfg.block_size);
+    R.cfg.kernel = (opt && opt->kernel > 0) ? opt->kernel : kKernelWave;
+    if (R.cfg.kernel != kKernelLoop && R.cfg.kernel != kKernelWave && R.cfg.kernel != kKernelCta)
+        return gpet_fail(GPET_ERR_INVALID_ARG, "kernel %d not in {1, 2, 3}", R.cfg.kernel);
+    // CTA-synchronous kernel: one CTA per SM of 256 or 512 threads; others <= 256
+    const int bs_default = R.cfg.kernel == kKernelCta ? 512 : 256;
+    R.cfg.block_size = (opt && opt->block_size > 0) ? opt->block_size : bs_default;
+    if (R.cfg.kernel == kKernelCta ? (R.cfg.block_size != 256 && R.cfg.block_size != 512)
+                                   : (R.cfg.block_size % 32 || R.cfg.block_size > 256))
+        return gpet_fail(GPET_ERR_INVALID_ARG, "block_size %d not valid for kernel %d", R.cfg.block_size,
+                         R.cfg.kernel);
     const int bps = (opt && opt->blocks_per_sm > 0) ? opt->blocks_per_sm : 4;
     R.cfg.grid = sms * bps;
-    R.cfg.kernel = (opt && opt->kernel > 0) ? opt->kernel : kKernelWave;
-    if (R.cfg.kernel != kKernelLoop && R.cfg.kernel != kKernelWave)
-        return gpet_fail(GPET_ERR_INVALID_ARG, "kernel %d not in {1, 2}", R.cfg.kernel);
     R.cfg.compact_every = (opt && opt->compact_every > 0) ? opt->compact_every : 1;
     R.cfg.pool_depth = (opt && opt->pool_depth > 0) ? opt->pool_depth : 2;
     if (R.cfg.pool_depth > 4) return gpet_fail(GPET_ERR_INVALID_ARG, "pool_depth must be in [1, 4]");
@@ -385,6 +390,8 @@ void fill_counts(const Run &R, int job, uint64_t n_decays, int64_t n_crystals, g
     c->h2d_bytes = R.h2d_bytes;
     c->wave_iterations = H.counters[6];
     c->wave_lanes = H.counters[7];
+    c->screened_flights = H.counters[8];
+    c->singles_formed = H.counters[9];
 }
 
 }  // namespace gpet

@@ -14,11 +14,12 @@
 namespace gpet {
 
 __device__ __forceinline__ void flush_counters(const OutDev &O, const Counters &c) {
-    const uint32_t v[6] = {c.det_steps, c.flights, c.trials, c.entered, c.ph_steps, c.hits};
+    const uint32_t v[8] = {c.det_steps, c.flights, c.trials, c.entered, c.ph_steps, c.hits, c.screened, c.singles};
+    const int slot[8] = {0, 1, 2, 3, 4, 5, 8, 9};
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 8; ++i) {
         const uint32_t x = __reduce_add_sync(kFullMask, v[i]);
-        if ((threadIdx.x & 31) == 0 && x) atomicAdd(O.counters + i, (unsigned long long)x);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(O.counters + slot[i], (unsigned long long)x);
     }
 }
 
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int
     PState s;
     s.phase = kPhIdle;
     s.job = 0;
-    Counters cnt = {0, 0, 0, 0, 0, 0};
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
     uint64_t pool_next = 0, pool_end = 0;
     int pool_job = 0;
     bool exhausted = false;
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int
         }
         const bool fin = s.phase == kPhFinish;
         if (__any_sync(kFullMask, fin)) {
-            ev_finish(W.jobs, W.geoms, O, s, fin, SL, kFullMask);
+            ev_finish(W.jobs, W.geoms, O, s, fin, SL, kFullMask, cnt);
             if (fin) s.phase = kPhIdle;
         }
     }
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(128) k_transport_redo(WorkDev W, OutDev O) {
     uint32_t l_dt[S];
     const SinglesList SL{l_unit, l_e, l_dt, 1};
     const unsigned long long n = min(*O.n_ovf, O.ovf_cap);
-    Counters cnt = {0, 0, 0, 0, 0, 0};
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
     int status = kStatusOk;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned long long base0 = (unsigned long long)blockIdx.x * blockDim.x;
@@ -167,8 +168,11 @@ __global__ void __launch_bounds__(128) k_transport_redo(WorkDev W, OutDev O) {
         }
         __syncwarp();
         const bool fin = s.phase == kPhFinish;
-        ev_finish(W.jobs, W.geoms, O, s, fin, SL, kFullMask);
+        ev_finish(W.jobs, W.geoms, O, s, fin, SL, kFullMask, cnt);
     }
+    // the singles of re-simulated histories are formed here (the rest was counted before)
+    const uint32_t ns = __reduce_add_sync(kFullMask, cnt.singles);
+    if ((threadIdx.x & 31) == 0 && ns) atomicAdd(O.counters + 9, (unsigned long long)ns);
     if (status) atomicOr(O.status, status);
 }
 
@@ -186,6 +190,9 @@ cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg 
     const size_t smem = loop_smem(ng, block, S);
     if (cfg.kernel == kKernelWave) {
         cudaError_t e = launch_transport_wave(W, O, cfg, st);
+        if (e != cudaSuccess) return e;
+    } else if (cfg.kernel == kKernelCta) {
+        cudaError_t e = launch_transport_cta(W, O, cfg, st);
         if (e != cudaSuccess) return e;
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_transport_loop<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -88,7 +88,7 @@ struct PState {
 };
 
 struct Counters {
-    uint32_t det_steps, flights, trials, entered, ph_steps, hits;
+    uint32_t det_steps, flights, trials, entered, ph_steps, hits, screened, singles;
 };
 
 __device__ __forceinline__ void to_global(const GeomDev &g, PState &s) {
@@ -105,26 +105,17 @@ __device__ __forceinline__ bool in_phantom(const JobDev &J, float x, float y, fl
            z < J.ph_hi[2];
 }
 
-// Start photon s.gamma of the history (and, when it is screened out at once,
-// the next one): into the phantom, into a flight, or straight to the end
-// when the axial screen shows it can meet no panel (that decision is its
-// flight, counted as one).
 __device__ __forceinline__ void start_photon(const JobDev &J, const GeomDev &g, PState &s, Counters &cnt) {
-    for (;;) {
-        const float sg = s.gamma == 0 ? 1.0f : -1.0f;
-        s.x = s.x0; s.y = s.y0; s.z = s.z0;
-        s.dx = sg * s.ox; s.dy = sg * s.oy; s.dz = sg * s.oz;
-        s.E = kE0;
-        s.path = 0.0f;
-        s.sph = 0; s.sdet = 0;
-        s.panel = -1; s.last = -1;
-        if (J.has_phantom && in_phantom(J, s.x, s.y, s.z)) { s.phase = kPhPhantom; return; }
-        if (!axial_miss(g, s.x, s.y, s.z, s.dx, s.dy, s.dz)) { s.phase = kPhFlight; return; }
-        cnt.flights++;
-        if (s.gamma == 0) { s.gamma = 1; continue; }
-        s.phase = kPhFinish;
-        return;
-    }
+    const float sg = s.gamma == 0 ? 1.0f : -1.0f;
+    s.x = s.x0; s.y = s.y0; s.z = s.z0;
+    s.dx = sg * s.ox; s.dy = sg * s.oy; s.dz = sg * s.oz;
+    s.E = kE0;
+    s.path = 0.0f;
+    s.sph = 0; s.sdet = 0;
+    s.panel = -1; s.last = -1;
+    s.phase = (J.has_phantom && in_phantom(J, s.x, s.y, s.z)) ? kPhPhantom : kPhFlight;
+    (void)g;
+    (void)cnt;
 }
 
 __device__ __forceinline__ void photon_done(const JobDev &J, const GeomDev &g, PState &s, Counters &cnt) {
@@ -133,16 +124,6 @@ __device__ __forceinline__ void photon_done(const JobDev &J, const GeomDev &g, P
         start_photon(J, g, s, cnt);
     } else {
         s.phase = kPhFinish;
-    }
-}
-
-// a photon about to fly: screened out at once, or on to the flight event
-__device__ __forceinline__ void to_flight(const JobDev &J, const GeomDev &g, PState &s, Counters &cnt) {
-    if (axial_miss(g, s.x, s.y, s.z, s.dx, s.dy, s.dz)) {
-        cnt.flights++;
-        photon_done(J, g, s, cnt);
-    } else {
-        s.phase = kPhFlight;
     }
 }
 
@@ -218,7 +199,7 @@ __device__ __forceinline__ int ev_phantom(const JobDev &J, const GeomDev &g, con
     if (step >= t_out) {
         s.x = fmaf(t_out, s.dx, s.x); s.y = fmaf(t_out, s.dy, s.y); s.z = fmaf(t_out, s.dz, s.z);
         s.path += t_out;
-        to_flight(J, g, s, cnt);
+        s.phase = kPhFlight;
         return kStatusOk;
     }
     s.x = fmaf(step, s.dx, s.x); s.y = fmaf(step, s.dy, s.y); s.z = fmaf(step, s.dz, s.z);
@@ -249,7 +230,11 @@ __device__ __forceinline__ void ev_flight(const JobDev &J, const GeomDev &g, PSt
     cnt.flights++;
     float t_in, t_out;
     const int k = flight(g, s.x, s.y, s.z, s.dx, s.dy, s.dz, s.last, t_in, t_out);
-    if (k < 0) { photon_done(J, g, s, cnt); return; }
+    if (k < 0) {
+        if (k == kFlightScreened) cnt.screened++;
+        photon_done(J, g, s, cnt);
+        return;
+    }
     cnt.entered++;
     // entry point, then the panel-local frame (w, u, v)
     const float ex = fmaf(t_in, s.dx, s.x), ey = fmaf(t_in, s.dy, s.y), ez = fmaf(t_in, s.dz, s.z);
@@ -336,7 +321,7 @@ __device__ __forceinline__ int ev_panel(const JobDev &J, const GeomDev &g, const
         to_global(g, s);
         s.last = s.panel;
         s.panel = -1;
-        to_flight(J, g, s, cnt);
+        s.phase = kPhFlight;
         return kStatusOk;
     }
     s.x = fmaf(step, s.dx, s.x); s.y = fmaf(step, s.dy, s.y); s.z = fmaf(step, s.dz, s.z);
@@ -379,11 +364,12 @@ __device__ __forceinline__ int ev_panel(const JobDev &J, const GeomDev &g, const
 // (call with the lanes of `mask` converged; `active` lanes own a history)
 __device__ __forceinline__ void ev_finish(const JobDev *__restrict__ jobs, const GeomDev *__restrict__ geoms,
                                           const OutDev &O, const PState &s, bool active, const SinglesList &SL,
-                                          uint32_t mask) {
+                                          uint32_t mask, Counters &cnt) {
     const int lane = threadIdx.x & 31;
     const JobDev *J = active ? &jobs[s.job] : nullptr;
     const bool ovf = active && s.ovf;
     const uint32_t n = (active && !ovf) ? s.nsing : 0u;
+    cnt.singles += n;
     // histories whose list overflowed go to the fallback list instead
     {
         const uint32_t b = __ballot_sync(mask, ovf);

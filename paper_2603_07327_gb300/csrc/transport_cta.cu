@@ -1,0 +1,300 @@
+// transport_cta.cu -- CTA-synchronous wavefront transport kernel.
+//
+// Same per-warp pools of history slots as the wavefront kernel, but the phase
+// is chosen for the whole CTA: every iteration each warp posts the phase
+// census of its pool to shared memory, one barrier later all warps read the
+// CTA totals and agree on the most populated phase, and every warp of the CTA
+// (one CTA per SM) runs that same event.  The whole SM then executes one
+// event's code at a time, which keeps the instruction cache warm; warps with
+// no slot in the chosen phase wait for the next iteration.  The events are
+// those of transport.cuh, so the results equal the other kernels' bit for bit.
+#include "internal.h"
+#include "transport.cuh"
+
+namespace gpet {
+
+namespace {
+
+constexpr int kCtaS = 6;     // singles-list entries per history (overflow -> redo kernel)
+constexpr int kCtaWords = 23;
+constexpr int kNumPh = 6;    // phases 0..5
+
+enum : int {
+    kCh0 = 0, kCh1, kCt0, kCt1, kCx, kCy, kCz, kCdx, kCdy, kCdz, kCx0, kCy0, kCz0, kCox, kCoy, kCoz, kCE, kCpath,
+    kCtrem, kCjob, kCpack, kCsteps
+};
+
+template <int SPL>
+struct CtaPool {
+    static constexpr int kPool = 32 * SPL;
+    uint32_t st[kCtaWords][kPool];
+    uint32_t sl_unit[kCtaS * kPool];
+    float sl_e[kCtaS * kPool];
+    uint32_t sl_dt[kCtaS * kPool];
+};
+
+template <class Pool>
+__device__ __forceinline__ uint32_t cphase(const Pool &P, int q) { return (P.st[kCpack][q] >> 16) & 7u; }
+
+template <class Pool>
+__device__ __forceinline__ void cload(const Pool &P, int q, PState &s) {
+    s.h = ((uint64_t)P.st[kCh1][q] << 32) | P.st[kCh0][q];
+    s.t0 = ((uint64_t)P.st[kCt1][q] << 32) | P.st[kCt0][q];
+    s.x = __uint_as_float(P.st[kCx][q]);
+    s.y = __uint_as_float(P.st[kCy][q]);
+    s.z = __uint_as_float(P.st[kCz][q]);
+    s.dx = __uint_as_float(P.st[kCdx][q]);
+    s.dy = __uint_as_float(P.st[kCdy][q]);
+    s.dz = __uint_as_float(P.st[kCdz][q]);
+    s.x0 = __uint_as_float(P.st[kCx0][q]);
+    s.y0 = __uint_as_float(P.st[kCy0][q]);
+    s.z0 = __uint_as_float(P.st[kCz0][q]);
+    s.ox = __uint_as_float(P.st[kCox][q]);
+    s.oy = __uint_as_float(P.st[kCoy][q]);
+    s.oz = __uint_as_float(P.st[kCoz][q]);
+    s.E = __uint_as_float(P.st[kCE][q]);
+    s.path = __uint_as_float(P.st[kCpath][q]);
+    s.trem = __uint_as_float(P.st[kCtrem][q]);
+    s.job = (int32_t)P.st[kCjob][q];
+    const uint32_t pk = P.st[kCpack][q];
+    s.panel = (int32_t)(pk & 0x7Fu) - 1;
+    s.last = (int32_t)((pk >> 7) & 0x7Fu) - 1;
+    s.gamma = (pk >> 14) & 1u;
+    s.phase = (pk >> 16) & 7u;
+    s.nsing = (pk >> 19) & 31u;
+    s.ovf = (pk >> 24) & 1u;
+    const uint32_t sw = P.st[kCsteps][q];
+    s.sph = sw & 0xFFFFu;
+    s.sdet = sw >> 16;
+}
+
+template <class Pool>
+__device__ __forceinline__ void cstore(Pool &P, int q, const PState &s, bool all) {
+    if (all) {
+        P.st[kCh0][q] = (uint32_t)s.h;
+        P.st[kCh1][q] = (uint32_t)(s.h >> 32);
+        P.st[kCt0][q] = (uint32_t)s.t0;
+        P.st[kCt1][q] = (uint32_t)(s.t0 >> 32);
+        P.st[kCx0][q] = __float_as_uint(s.x0);
+        P.st[kCy0][q] = __float_as_uint(s.y0);
+        P.st[kCz0][q] = __float_as_uint(s.z0);
+        P.st[kCox][q] = __float_as_uint(s.ox);
+        P.st[kCoy][q] = __float_as_uint(s.oy);
+        P.st[kCoz][q] = __float_as_uint(s.oz);
+        P.st[kCjob][q] = (uint32_t)s.job;
+    }
+    P.st[kCx][q] = __float_as_uint(s.x);
+    P.st[kCy][q] = __float_as_uint(s.y);
+    P.st[kCz][q] = __float_as_uint(s.z);
+    P.st[kCdx][q] = __float_as_uint(s.dx);
+    P.st[kCdy][q] = __float_as_uint(s.dy);
+    P.st[kCdz][q] = __float_as_uint(s.dz);
+    P.st[kCE][q] = __float_as_uint(s.E);
+    P.st[kCpath][q] = __float_as_uint(s.path);
+    P.st[kCtrem][q] = __float_as_uint(s.trem);
+    P.st[kCpack][q] = (uint32_t)(s.panel + 1) | ((uint32_t)(s.last + 1) << 7) | (s.gamma << 14) | (s.phase << 16) |
+                      (s.nsing << 19) | (s.ovf << 24);
+    P.st[kCsteps][q] = (s.sph & 0xFFFFu) | (s.sdet << 16);
+}
+
+// warp-wide refill of the idle slots of one group of 32 (see transport.cu)
+__device__ void cta_refill(const WorkDev &W, uint32_t need, uint64_t &pool_next, uint64_t &pool_end, int &pool_job,
+                           bool &exhausted, bool &got, uint64_t &h, int &job) {
+    const int lane = threadIdx.x & 31;
+    got = false;
+    while (need && !exhausted) {
+        const uint64_t avail = pool_end - pool_next;
+        if (avail == 0) {
+            unsigned long long c = 0;
+            if (lane == 0) c = atomicAdd(W.next_chunk, 1ull);
+            c = __shfl_sync(kFullMask, c, 0);
+            if (c >= W.total_chunks) {
+                exhausted = true;
+                break;
+            }
+            int lo = 0, hi = W.n_jobs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (W.chunk_start[mid] <= c) lo = mid; else hi = mid - 1;
+            }
+            pool_job = lo;
+            const uint64_t h0 = (uint64_t)(c - W.chunk_start[lo]) * W.chunk_size;
+            const uint64_t base = W.jobs[lo].h_base;
+            pool_next = base + h0;
+            pool_end = base + min(h0 + (uint64_t)W.chunk_size, W.jobs[lo].n_hist);
+            continue;
+        }
+        const uint32_t cnt = (uint32_t)__popc(need);
+        const uint32_t take = avail < cnt ? (uint32_t)avail : cnt;
+        const uint32_t rank = (uint32_t)__popc(need & lanemask_lt());
+        if (((need >> lane) & 1u) && rank < take) {
+            got = true;
+            h = pool_next + rank;
+            job = pool_job;
+        }
+        pool_next += take;
+        for (uint32_t i = 0; i < take; ++i) need &= need - 1u;
+    }
+}
+
+}  // namespace
+
+template <int SPL, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) k_transport_cta(WorkDev W, OutDev O, int ng_smem) {
+    using Pool = CtaPool<SPL>;
+    constexpr int kPool = Pool::kPool;
+    extern __shared__ __align__(16) uint8_t smem[];
+    GeomDev *sgeom = reinterpret_cast<GeomDev *>(smem);
+    Pool *pools = reinterpret_cast<Pool *>(sgeom + ng_smem);
+    // census of every warp, double-buffered by iteration parity
+    __shared__ int census[2][WARPS][kNumPh];
+    stage_geometry(W, sgeom, ng_smem);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    Pool &P = pools[wid];
+#pragma unroll
+    for (int g = 0; g < SPL; ++g) P.st[kCpack][g * 32 + lane] = 0;
+    __syncthreads();
+
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint64_t pool_next = 0, pool_end = 0;
+    int pool_job = 0;
+    bool exhausted = false;
+    int status = kStatusOk;
+    unsigned long long iters = 0, lanes_used = 0;
+    int parity = 0;
+
+    for (;;) {
+        // 1. refill the warp's idle slots
+#pragma unroll
+        for (int g = 0; g < SPL; ++g) {
+            const int q = g * 32 + lane;
+            const uint32_t need = __ballot_sync(kFullMask, cphase(P, q) == kPhIdle);
+            if (need && !exhausted) {
+                bool got;
+                uint64_t h = 0;
+                int job = 0;
+                cta_refill(W, need, pool_next, pool_end, pool_job, exhausted, got, h, job);
+                if (got) {
+                    P.st[kCh0][q] = (uint32_t)h;
+                    P.st[kCh1][q] = (uint32_t)(h >> 32);
+                    P.st[kCjob][q] = (uint32_t)job;
+                    P.st[kCpack][q] = (uint32_t)kPhSource << 16;
+                }
+            }
+        }
+        __syncwarp();
+        // 2. the warp's census, posted for the CTA
+        uint32_t ph[SPL];
+#pragma unroll
+        for (int g = 0; g < SPL; ++g) ph[g] = cphase(P, g * 32 + lane);
+        uint32_t mask_p[kNumPh][SPL];
+#pragma unroll
+        for (int p = 1; p < kNumPh; ++p) {
+            int n = 0;
+#pragma unroll
+            for (int g = 0; g < SPL; ++g) {
+                mask_p[p][g] = __ballot_sync(kFullMask, ph[g] == (uint32_t)p);
+                n += __popc(mask_p[p][g]);
+            }
+            if (lane == 0) census[parity][wid][p] = n;
+        }
+        __syncthreads();
+        // 3. every warp computes the same CTA-wide choice
+        int best_p = 0, best_n = 0;
+#pragma unroll
+        for (int p = 1; p < kNumPh; ++p) {
+            int tot = 0;
+            for (int w = 0; w < WARPS; ++w) tot += census[parity][w][p];
+            if (tot > best_n) { best_n = tot; best_p = p; }
+        }
+        parity ^= 1;
+        if (best_n == 0) break;  // every slot of every warp idle after refills: done
+        // 4. lanes onto this warp's slots of the chosen phase
+        int mine = 0;
+#pragma unroll
+        for (int g = 0; g < SPL; ++g) mine += __popc(mask_p[best_p][g]);
+        const bool active = lane < mine;
+        int q = 0;
+        if (active) {
+            int rank = lane;
+#pragma unroll
+            for (int g = 0; g < SPL; ++g) {
+                const int c = __popc(mask_p[best_p][g]);
+                if (rank >= 0 && rank < c) q = g * 32 + (int)__fns(mask_p[best_p][g], 0, rank + 1);
+                rank -= c;
+            }
+        }
+        if (mine == 0) continue;  // nothing of this phase here: wait for the next choice
+        ++iters;
+        lanes_used += (unsigned long long)min(mine, 32);
+        PState s;
+        s.phase = kPhIdle;
+        s.job = 0;
+        const SinglesList SL{P.sl_unit + q, P.sl_e + q, P.sl_dt + q, kPool};
+        if (best_p == kPhFinish) {
+            if (active) cload(P, q, s);
+            __syncwarp();
+            ev_finish(W.jobs, W.geoms, O, s, active, SL, kFullMask, cnt);
+            if (active) P.st[kCpack][q] = 0;
+            __syncwarp();
+            continue;
+        }
+        if (active) {
+            cload(P, q, s);
+            const JobDev &J = W.jobs[s.job];
+            const GeomDev &g = J.geom < ng_smem ? sgeom[J.geom] : W.geoms[J.geom];
+            int st = kStatusOk;
+            switch (best_p) {
+                case kPhSource: ev_source(J, g, s, cnt); break;
+                case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
+                case kPhFlight: ev_flight(J, g, s, cnt); break;
+                case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, kCtaS, cnt); break;
+                default: break;
+            }
+            if (st != kStatusOk) {
+                status |= st;
+                s.phase = kPhIdle;
+            }
+            cstore(P, q, s, best_p == kPhSource);
+        }
+        __syncwarp();
+    }
+    const uint32_t v[8] = {cnt.det_steps, cnt.flights, cnt.trials, cnt.entered, cnt.ph_steps, cnt.hits,
+                           cnt.screened, cnt.singles};
+    const int slot[8] = {0, 1, 2, 3, 4, 5, 8, 9};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t x = __reduce_add_sync(kFullMask, v[i]);
+        if (lane == 0 && x) atomicAdd(O.counters + slot[i], (unsigned long long)x);
+    }
+    if (lane == 0) {
+        atomicAdd(O.counters + 6, iters);
+        atomicAdd(O.counters + 7, lanes_used);
+    }
+    if (status) atomicOr(O.status, status);
+}
+
+template <int SPL, int WARPS>
+static cudaError_t launch_cta(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
+    const int ng = min(W.n_geoms, cfg.max_smem_geoms);
+    const size_t smem = (size_t)ng * sizeof(GeomDev) + sizeof(CtaPool<SPL>) * WARPS;
+    cudaError_t e = cudaFuncSetAttribute(k_transport_cta<SPL, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_cta<SPL, WARPS>, WARPS * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    k_transport_cta<SPL, WARPS><<<cfg.sm_count * occ, WARPS * 32, smem, st>>>(W, O, ng);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transport_cta(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
+    // block_size selects the CTA width (warps per CTA, one CTA per SM)
+    switch (cfg.block_size) {
+        case 256: return launch_cta<2, 8>(W, O, cfg, st);
+        default: return launch_cta<2, 16>(W, O, cfg, st);
+    }
+}
+
+}  // namespace gpet

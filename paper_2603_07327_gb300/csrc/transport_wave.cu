@@ -72,28 +72,32 @@ __device__ __forceinline__ void pool_load(const Pool &P, int q, PState &s) {
     s.sdet = sw >> 16;
 }
 
+// `all`: also the words only the decay event changes (history, decay time,
+// job, decay point and direction); the other events leave them as loaded
 template <class Pool>
-__device__ __forceinline__ void pool_store(Pool &P, int q, const PState &s) {
-    P.st[kWh0][q] = (uint32_t)s.h;
-    P.st[kWh1][q] = (uint32_t)(s.h >> 32);
-    P.st[kWt0][q] = (uint32_t)s.t0;
-    P.st[kWt1][q] = (uint32_t)(s.t0 >> 32);
+__device__ __forceinline__ void pool_store(Pool &P, int q, const PState &s, bool all) {
+    if (all) {
+        P.st[kWh0][q] = (uint32_t)s.h;
+        P.st[kWh1][q] = (uint32_t)(s.h >> 32);
+        P.st[kWt0][q] = (uint32_t)s.t0;
+        P.st[kWt1][q] = (uint32_t)(s.t0 >> 32);
+        P.st[kWx0][q] = __float_as_uint(s.x0);
+        P.st[kWy0][q] = __float_as_uint(s.y0);
+        P.st[kWz0][q] = __float_as_uint(s.z0);
+        P.st[kWox][q] = __float_as_uint(s.ox);
+        P.st[kWoy][q] = __float_as_uint(s.oy);
+        P.st[kWoz][q] = __float_as_uint(s.oz);
+        P.st[kWjob][q] = (uint32_t)s.job;
+    }
     P.st[kWx][q] = __float_as_uint(s.x);
     P.st[kWy][q] = __float_as_uint(s.y);
     P.st[kWz][q] = __float_as_uint(s.z);
     P.st[kWdx][q] = __float_as_uint(s.dx);
     P.st[kWdy][q] = __float_as_uint(s.dy);
     P.st[kWdz][q] = __float_as_uint(s.dz);
-    P.st[kWx0][q] = __float_as_uint(s.x0);
-    P.st[kWy0][q] = __float_as_uint(s.y0);
-    P.st[kWz0][q] = __float_as_uint(s.z0);
-    P.st[kWox][q] = __float_as_uint(s.ox);
-    P.st[kWoy][q] = __float_as_uint(s.oy);
-    P.st[kWoz][q] = __float_as_uint(s.oz);
     P.st[kWE][q] = __float_as_uint(s.E);
     P.st[kWpath][q] = __float_as_uint(s.path);
     P.st[kWtrem][q] = __float_as_uint(s.trem);
-    P.st[kWjob][q] = (uint32_t)s.job;
     P.st[kWpack][q] = (uint32_t)(s.panel + 1) | ((uint32_t)(s.last + 1) << 7) | (s.gamma << 14) | (s.phase << 16) |
                       (s.nsing << 19) | (s.ovf << 24);
     P.st[kWsteps][q] = (s.sph & 0xFFFFu) | (s.sdet << 16);
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
     for (int g = 0; g < SPL; ++g) P.st[kWpack][g * 32 + lane] = 0;  // every slot idle
     __syncthreads();
 
-    Counters cnt = {0, 0, 0, 0, 0, 0};
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
     uint64_t pool_next = 0, pool_end = 0;
     int pool_job = 0;
     bool exhausted = false;
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
             // finished histories as one wavefront: blur, window, append
             if (active) pool_load(P, q, s);
             __syncwarp();
-            ev_finish(W.jobs, W.geoms, O, s, active, SL, kFullMask);
+            ev_finish(W.jobs, W.geoms, O, s, active, SL, kFullMask, cnt);
             if (active) P.st[kWpack][q] = 0;   // slot idle
             __syncwarp();
             continue;
@@ -249,16 +253,18 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
                     s.phase = kPhIdle;
                 }
             }
-            pool_store(P, q, s);
+            pool_store(P, q, s, best_p == kPhSource);
         }
         __syncwarp();
     }
     // flush counters (all lanes converged here)
-    const uint32_t v[6] = {cnt.det_steps, cnt.flights, cnt.trials, cnt.entered, cnt.ph_steps, cnt.hits};
+    const uint32_t v[8] = {cnt.det_steps, cnt.flights, cnt.trials, cnt.entered, cnt.ph_steps, cnt.hits,
+                           cnt.screened, cnt.singles};
+    const int slot[8] = {0, 1, 2, 3, 4, 5, 8, 9};
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 8; ++i) {
         const uint32_t x = __reduce_add_sync(kFullMask, v[i]);
-        if (lane == 0 && x) atomicAdd(O.counters + i, (unsigned long long)x);
+        if (lane == 0 && x) atomicAdd(O.counters + slot[i], (unsigned long long)x);
     }
     if (lane == 0) {
         atomicAdd(O.counters + 6, iters);

@@ -42,10 +42,9 @@ extern "C" int gpet_autotune(gpet_scanner *sc, const gpet_source *src, const gpe
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "device query");
-    struct Cand { int kernel, bps, compact, depth; };
-    const Cand cands[] = {{kKernelLoop, 2, 1, 0}, {kKernelLoop, 1, 1, 0}, {kKernelWave, 0, 1, 2},
-                          {kKernelWave, 0, 2, 2}, {kKernelWave, 0, 4, 2}, {kKernelWave, 0, 1, 3},
-                          {kKernelWave, 0, 2, 3}, {kKernelWave, 0, 1, 4}};
+    struct Cand { int kernel, bps, compact, depth, block; };
+    const Cand cands[] = {{kKernelLoop, 2, 1, 0, 0}, {kKernelWave, 0, 1, 2, 0}, {kKernelWave, 0, 2, 2, 0},
+                          {kKernelWave, 0, 1, 3, 0}, {kKernelCta, 0, 1, 2, 512}, {kKernelCta, 0, 1, 2, 256}};
     float best_t = 1e30f;
     gpet_options bo;
     std::memset(&bo, 0, sizeof(bo));
@@ -56,6 +55,7 @@ extern "C" int gpet_autotune(gpet_scanner *sc, const gpet_source *src, const gpe
         o.blocks_per_sm = c.bps;
         o.compact_every = c.compact;
         o.pool_depth = c.depth;
+        o.block_size = c.block;
         float t = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {  // first repetition warms caches and pools
             gpet_result *r = nullptr;

@@ -87,7 +87,7 @@ CASES = {
 CASES["near_ring_offcentre"] = (lambda: W.config2_scanner("B"), lambda: W.point_source((45.0, 10.0, -12.0)), None,
                                 100_000, 21)
 
-KERNELS = {"loop": 1, "wave": 2}
+KERNELS = {"loop": 1, "wave": 2, "cta": 3}
 
 
 @pytest.mark.parametrize("kernel", sorted(KERNELS))
@@ -109,7 +109,7 @@ def test_kernels_agree_bit_for_bit(G, compact_every):
     for sc, src, n in ((W.config2_scanner("B"), W.point_source((3.0, -2.0, 11.0)), 300_000),
                        (W.config3_scanner(), W.phantom_source(), 60_000)):
         out = []
-        for k in (1, 2):
+        for k in (1, 2, 3):
             r = G.simulate(sc, src, W.digitizer(), n, 77, phantom=ph if src["kind"] == 1 else None, keep_hits=True,
                            kernel=k, compact_every=compact_every)
             h = PU.gpu_hits_table(r.hits())
@@ -118,12 +118,13 @@ def test_kernels_agree_bit_for_bit(G, compact_every):
             a, b = r.coincidences()
             coinc = PU.coincidence_set(s["h"], s["unit"], a, b)
             out.append((h, {k2: v[order] for k2, v in s.items()}, coinc, r.tallies()))
-        (h1, s1, c1, t1), (h2, s2, c2, t2) = out
-        assert np.array_equal(h1, h2)
-        for key in s1:
-            assert np.array_equal(s1[key], s2[key]), key
-        assert c1 == c2
-        assert np.array_equal(t1[0], t2[0]) and np.array_equal(t1[1], t2[1])
+        (h1, s1, c1, t1) = out[0]
+        for (h2, s2, c2, t2) in out[1:]:
+            assert np.array_equal(h1, h2)
+            for key in s1:
+                assert np.array_equal(s1[key], s2[key]), key
+            assert c1 == c2
+            assert np.array_equal(t1[0], t2[0]) and np.array_equal(t1[1], t2[1])
 
 
 def test_module_and_panel_readout(G, oracle):

@@ -23,7 +23,9 @@ def test_billion_history_tallies_are_exact(G):
     from paper_2603_07327_gb300 import shard
     n = 1_000_000_000
     sc = G.Scanner(W.config2_scanner("B"))
-    src, dg = W.point_source((0.0, 0.0, 11.0)), W.digitizer(e_lo=0.0, e_hi=0.0)  # window closed: tallies only
+    # 1e6 Bq keeps the acquisition (1000 s) inside the time-key range
+    src = W.point_source((0.0, 0.0, 11.0), activity_bq=1.0e6)
+    dg = W.digitizer(e_lo=0.0, e_hi=0.0)  # an empty window: tallies only
     dg["window_ns"] = 0.0
     full = sc.simulate(src, dg, n, 31, kernel=2)
     fc, fe = full.tallies()
