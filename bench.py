@@ -329,7 +329,7 @@ def run_ours(args):
     ops = sum(alg_ops(c, n_panels) for c in counts)
     achieved = ops / (tr_ms / 1000.0)
     peak = SM_COUNT_GB300 * LANES_PER_SM * SM_MAX_MHZ * 1e6
-    kname = "k_transport_loop" if args.kernel == 1 else "k_transport_wave"
+    kname = {1: "k_transport_loop", 2: "k_transport_wave"}.get(args.kernel, "k_transport_cta")
     roof = dict(bound="alu", achieved=achieved, peak=peak, unit="lane-ops/s", frac=achieved / peak,
                 traffic=args.traffic, kernel=kname,
                 peak_note="152 SMs x 128 FP32/INT lanes x 2070 MHz (recipe unit counts and max clock)",

@@ -133,10 +133,10 @@ typedef struct {
 /* Launch options; pass NULL for defaults. */
 typedef struct {
     int32_t keep_hits;       /* 1: also store every crystal interaction (tests, DOI studies) */
-    int32_t block_size;      /* threads per CTA of the transport kernel (0 = default; kernel 3: 256 or 512) */
+    int32_t block_size;      /* threads per CTA of the transport kernel (0 = 256; kernel 3: 128, 256 or 512) */
     int32_t blocks_per_sm;   /* resident CTAs per SM (0 = tuned default)                   */
-    int32_t kernel;          /* 0 = tuned default, 1 = per-lane event loop, 2 = wavefront,
-                                3 = wavefront with one phase per CTA (one CTA per SM)       */
+    int32_t kernel;          /* 0 = tuned, else 3; 1 = per-lane event loop, 2 = per-warp
+                                wavefront, 3 = wavefront with one phase per CTA            */
     int32_t compact_every;   /* wavefront regrouping interval in events (0 = default)      */
     int32_t pool_depth;      /* wavefront histories per lane in shared memory, 2..4 (0 = 2)  */
     void *stream;            /* cudaStream_t */
@@ -304,9 +304,9 @@ int gpet_sort_times_noalloc(const uint64_t *d_t_in, uint64_t n, uint64_t *d_t_ou
 /* ------------------------------------------------------------------------ */
 
 /* Time the candidate launch forms of the transport kernel -- the per-lane
- * event loop, the wavefront kernel at pool depth 2 or 3 and regrouping every
- * 1 or 2 events, the CTA-synchronous wavefront at 256 or 512 threads -- on
- * a pilot run (pilot_decays >= 1000, seed)
+ * event loop, the per-warp wavefront, the CTA-synchronous wavefront at 128,
+ * 256 or 512 threads and pool depth 2 or 3 -- on a pilot run
+ * (pilot_decays >= 1000, seed)
  * of the caller's workload, and return the fastest in *best (its transport
  * time in *best_ms, may be NULL).  The choice is remembered for the scanner's
  * design class (panels, layers, phantom) on this device's SM count; later

@@ -73,14 +73,14 @@ int run_default_cfg(Run &R, const gpet_options *opt_in, const gpet_scanner *sc) 
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaDeviceGetAttribute");
     R.cfg.sm_count = sms;
-    R.cfg.kernel = (opt && opt->kernel > 0) ? opt->kernel : kKernelWave;
+    R.cfg.kernel = (opt && opt->kernel > 0) ? opt->kernel : kKernelCta;
     if (R.cfg.kernel != kKernelLoop && R.cfg.kernel != kKernelWave && R.cfg.kernel != kKernelCta)
         return gpet_fail(GPET_ERR_INVALID_ARG, "kernel %d not in {1, 2, 3}", R.cfg.kernel);
-    // CTA-synchronous kernel: one CTA per SM of 256 or 512 threads; others <= 256
-    const int bs_default = R.cfg.kernel == kKernelCta ? 512 : 256;
-    R.cfg.block_size = (opt && opt->block_size > 0) ? opt->block_size : bs_default;
-    if (R.cfg.kernel == kKernelCta ? (R.cfg.block_size != 256 && R.cfg.block_size != 512)
-                                   : (R.cfg.block_size % 32 || R.cfg.block_size > 256))
+    // CTA-synchronous kernel: CTAs of 128, 256 or 512 threads; others <= 256
+    R.cfg.block_size = (opt && opt->block_size > 0) ? opt->block_size : 256;
+    if (R.cfg.kernel == kKernelCta
+            ? (R.cfg.block_size != 128 && R.cfg.block_size != 256 && R.cfg.block_size != 512)
+            : (R.cfg.block_size % 32 || R.cfg.block_size > 256))
         return gpet_fail(GPET_ERR_INVALID_ARG, "block_size %d not valid for kernel %d", R.cfg.block_size,
                          R.cfg.kernel);
     const int bps = (opt && opt->blocks_per_sm > 0) ? opt->blocks_per_sm : 4;

@@ -4,10 +4,11 @@
 // is chosen for the whole CTA: every iteration each warp posts the phase
 // census of its pool to shared memory, one barrier later all warps read the
 // CTA totals and agree on the most populated phase, and every warp of the CTA
-// (one CTA per SM) runs that same event.  The whole SM then executes one
-// event's code at a time, which keeps the instruction cache warm; warps with
-// no slot in the chosen phase wait for the next iteration.  The events are
-// those of transport.cuh, so the results equal the other kernels' bit for bit.
+// runs that same event.  All of a CTA's warps then execute one event's code
+// at a time, which keeps the instruction cache warm (an SM holds one or two
+// such CTAs); warps with no slot in the chosen phase wait for the next
+// iteration.  The events are those of transport.cuh, so the results equal the
+// other kernels' bit for bit.
 #include "internal.h"
 #include "transport.cuh"
 
@@ -290,10 +291,18 @@ static cudaError_t launch_cta(const WorkDev &W, const OutDev &O, const LaunchCfg
 }
 
 cudaError_t launch_transport_cta(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
-    // block_size selects the CTA width (warps per CTA, one CTA per SM)
+    // block_size selects the CTA width; pool_depth 3 deepens the per-warp pools
+    if (cfg.pool_depth == 3) {
+        switch (cfg.block_size) {
+            case 128: return launch_cta<3, 4>(W, O, cfg, st);
+            case 512: return launch_cta<3, 16>(W, O, cfg, st);
+            default: return launch_cta<3, 8>(W, O, cfg, st);
+        }
+    }
     switch (cfg.block_size) {
-        case 256: return launch_cta<2, 8>(W, O, cfg, st);
-        default: return launch_cta<2, 16>(W, O, cfg, st);
+        case 128: return launch_cta<2, 4>(W, O, cfg, st);
+        case 512: return launch_cta<2, 16>(W, O, cfg, st);
+        default: return launch_cta<2, 8>(W, O, cfg, st);
     }
 }
 

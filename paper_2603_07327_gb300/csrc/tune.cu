@@ -43,8 +43,8 @@ extern "C" int gpet_autotune(gpet_scanner *sc, const gpet_source *src, const gpe
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "device query");
     struct Cand { int kernel, bps, compact, depth, block; };
-    const Cand cands[] = {{kKernelLoop, 2, 1, 0, 0}, {kKernelWave, 0, 1, 2, 0}, {kKernelWave, 0, 2, 2, 0},
-                          {kKernelWave, 0, 1, 3, 0}, {kKernelCta, 0, 1, 2, 512}, {kKernelCta, 0, 1, 2, 256}};
+    const Cand cands[] = {{kKernelLoop, 2, 1, 0, 0}, {kKernelWave, 0, 1, 2, 0}, {kKernelCta, 0, 1, 2, 128},
+                          {kKernelCta, 0, 1, 2, 256}, {kKernelCta, 0, 1, 2, 512}, {kKernelCta, 0, 1, 3, 256}};
     float best_t = 1e30f;
     gpet_options bo;
     std::memset(&bo, 0, sizeof(bo));
