@@ -52,9 +52,9 @@ PAIRS_PER_POSITION = 10_000_000
 #   phantom step: 1 block, log, exit distance, voxel index + gather, accept   150
 #   Compton trial: 1 block, 3 uniforms, one Kahn branch and its test          100
 #   crystal hit: kinematics/rotation share, tallies, singles-list update       60
-#   single: 1 block, Box-Muller, blur, window, append                         140
+#   single: 1 block, Box-Muller, energy and depth blur, window, append        150
 ALG = dict(source=130, screen=20, flight_test=140, enter=12, det_step=165, ph_step=150, trial=100, hit=60,
-           single=140)
+           single=150)
 SM_COUNT_GB300 = 152
 LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -120,6 +120,31 @@ class Clocks:
         os.unlink(self.f.name)
         return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
                     reasons=sorted(reasons), samples=len(sm))
+
+
+# DRAM bytes (read + write) per simulated pair of the transport kernel, from an
+# ncu capture of the full batched sweep launch (dram__bytes_read.sum +
+# dram__bytes_write.sum; one pass).  The counters hold only for the sources they
+# were taken on: the entry carries their SHA-1, and `traffic` is reported as null
+# once any transport source differs.
+TRANSPORT_SOURCES = ("device.cuh", "transport.cuh", "transport.cu", "transport_cta.cu")
+TRANSPORT_TRAFFIC = None   # dict(sha1=..., bytes_per_pair=..., capture=...)
+
+
+def _transport_sources_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for name in TRANSPORT_SOURCES:
+        with open(os.path.join(ROOT, "paper_2603_07327_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _transport_traffic(pairs_per_launch):
+    t = TRANSPORT_TRAFFIC
+    if not t or t["sha1"] != _transport_sources_sha1():
+        return None
+    return t["bytes_per_pair"] * pairs_per_launch
 
 
 def _measured_hbm_gbs():
@@ -330,21 +355,25 @@ def run_ours(args):
     achieved = ops / (tr_ms / 1000.0)
     peak = SM_COUNT_GB300 * LANES_PER_SM * SM_MAX_MHZ * 1e6
     kname = {1: "k_transport_loop", 2: "k_transport_wave"}.get(args.kernel, "k_transport_cta")
+    pairs_per_launch = pairs_per_step if args.form == "batched" else pairs_per_step / max(len(jobs), 1)
+    traffic = args.traffic if args.traffic is not None else (
+        _transport_traffic(pairs_per_launch) if args.kernel in (0, 3) else None)
     roof = dict(bound="alu", achieved=achieved, peak=peak, unit="lane-ops/s", frac=achieved / peak,
-                traffic=args.traffic, kernel=kname,
+                traffic=traffic, kernel=kname,
                 peak_note="152 SMs x 128 FP32/INT lanes x 2070 MHz (recipe unit counts and max clock)",
                 transport_share=tr_ms / (tr_ms + dg_ms))
 
     # digitizer back end (time sort + coincidences), HBM-bound: algorithmic bytes
     # per single = key build 24 + 8 radix passes x 32 (histogram read 8, scatter
-    # read 12 + write 12) + gather 76 + coincidence pass 34 = 390
+    # read 12 + write 12) + gather 84 (index 4, 8 fields read 40 + written 40)
+    # + coincidence pass 34 = 398
     singles_step = sum(c["singles"] for c in counts) / args.steps
-    dig_bytes = 390.0 * singles_step
+    dig_bytes = 398.0 * singles_step
     dig_gbs = dig_bytes / (dg_ms / args.steps / 1000.0) / 1e9 if dg_ms > 0 else None
     hbm_peak = _measured_hbm_gbs()
     roof_dig = dict(bound="hbm", achieved=dig_gbs, peak=hbm_peak, unit="GB/s",
                     frac=(dig_gbs / hbm_peak) if dig_gbs else None, traffic=None,
-                    bytes_per_single=390, note="time sort + coincidence sorting; peak = measured copy GB/s")
+                    bytes_per_single=398, note="time sort + coincidence sorting; peak = measured copy GB/s")
 
     # end to end through the C ABI: host descriptors in (one batch call over the
     # sweep), coincidences, singles and tallies of every job copied to host memory

@@ -128,6 +128,9 @@ typedef struct {
     double e_lo_kev, e_hi_kev;
     double coinc_window_ns;
     double e_cut_kev;
+    double doi_fwhm_mm;   /* analytic depth-of-interaction blur of each single (0 = none); the
+                             single's depth is the energy-weighted depth of its hits (Sec. 4
+                             favours analytic light-sharing / DOI blurring over optical transport) */
 } gpet_digitizer;
 
 /* Launch options; pass NULL for defaults. */
@@ -226,7 +229,8 @@ enum {
     GPET_HITS_WUV = 14,         /* float  [hits][3] panel-local position (mm)  */
     GPET_HITS_E = 15,           /* float  [hits] deposit (keV)                 */
     GPET_HITS_T_PS = 16,        /* uint64 [hits]                               */
-    GPET_RESULT_ARRAYS = 17
+    GPET_SINGLES_DOI = 17,      /* float  [singles]   blurred depth of interaction (mm from the inner face) */
+    GPET_RESULT_ARRAYS = 18
 };
 
 /* Copy one result array to host memory dst (cap_bytes long).  Returns

@@ -123,6 +123,7 @@ typedef struct {
 
 typedef struct {
     double fwhm_at_511, e_lo, e_hi, window_ns, e_cut;
+    double doi_fwhm_mm;  /* depth blur of a single's interaction depth (0 = none) */
 } om_digitizer;
 
 /* one interaction that deposits energy in a crystal */
@@ -138,6 +139,7 @@ typedef struct {
     int32_t unit, panel;
     double e_raw, e_blur;
     int32_t kept;
+    double doi, doi_blur;  /* energy-weighted depth of the single's hits (mm) and its blurred value */
 } om_single;
 
 typedef struct {
@@ -747,20 +749,27 @@ static int or_history(const or_ctx *C, uint64_t h, or_sink *S, uint64_t *tc, uin
         om_single s;
         s.h = h; s.unit = unit; s.panel = hh[i].panel;
         s.e_raw = 0.0; s.t_ps = hh[i].t_ps;
+        double ew = 0.0;
         for (int j = i; j < nh; ++j) {
             if (used[j] || or_unit(C->g, &hh[j]) != unit) continue;
             used[j] = 1;
             s.e_raw += hh[j].edep;
+            ew += hh[j].edep * hh[j].w;
             if (hh[j].t_ps < s.t_ps) s.t_ps = hh[j].t_ps;
         }
+        s.doi = ew / s.e_raw;
         /* energy blur: FWHM(E) = fwhm_511 * sqrt(511 * E), Box-Muller normal */
         uint32_t q[4];
         uint32_t ctr[4] = {(uint32_t)h, (uint32_t)(h >> 32), OR_TAG_DIGI << 28, (uint32_t)unit};
         uint32_t key[2] = {(uint32_t)C->seed, (uint32_t)(C->seed >> 32)};
         or_philox4x32_10(ctr, key, q);
-        double n01 = sqrt(-2.0 * log(or_uniform(q[0]))) * cos(2.0 * OR_PI * or_uniform(q[1]));
+        /* Box-Muller pair: the cosine normal blurs the energy, the sine normal the depth */
+        double rad = sqrt(-2.0 * log(or_uniform(q[0])));
+        double n01 = rad * cos(2.0 * OR_PI * or_uniform(q[1]));
+        double n02 = rad * sin(2.0 * OR_PI * or_uniform(q[1]));
         double sigma = sig_k * sqrt(OR_E0_KEV * s.e_raw);
         s.e_blur = s.e_raw + sigma * n01;
+        s.doi_blur = s.doi + C->dg->doi_fwhm_mm / (2.0 * sqrt(2.0 * log(2.0))) * n02;
         s.kept = (s.e_blur >= C->dg->e_lo && s.e_blur <= C->dg->e_hi) ? 1 : 0;
         int st = or_push_single(S, &s);
         if (st != OR_OK) return st;

@@ -69,7 +69,7 @@ class Source(C.Structure):
 
 class Digitizer(C.Structure):
     _fields_ = [("fwhm_at_511", C.c_double), ("e_lo", C.c_double), ("e_hi", C.c_double),
-                ("window_ns", C.c_double), ("e_cut", C.c_double)]
+                ("window_ns", C.c_double), ("e_cut", C.c_double), ("doi_fwhm_mm", C.c_double)]
 
 
 class Hit(C.Structure):
@@ -80,7 +80,8 @@ class Hit(C.Structure):
 
 class Single(C.Structure):
     _fields_ = [("t_ps", C.c_uint64), ("h", C.c_uint64), ("unit", C.c_int32), ("panel", C.c_int32),
-                ("e_raw", C.c_double), ("e_blur", C.c_double), ("kept", C.c_int32)]
+                ("e_raw", C.c_double), ("e_blur", C.c_double), ("kept", C.c_int32), ("doi", C.c_double),
+                ("doi_blur", C.c_double)]
 
 
 class Output(C.Structure):
@@ -97,7 +98,7 @@ HIT_DTYPE = np.dtype([("h", "<u8"), ("gamma", "<i4"), ("step", "<i4"), ("panel",
                       ("layer", "<i4"), ("crystal", "<i4"), ("w", "<f8"), ("u", "<f8"), ("v", "<f8"),
                       ("edep", "<f8"), ("t_ps", "<u8")], align=True)
 SINGLE_DTYPE = np.dtype([("t_ps", "<u8"), ("h", "<u8"), ("unit", "<i4"), ("panel", "<i4"), ("e_raw", "<f8"),
-                         ("e_blur", "<f8"), ("kept", "<i4")], align=True)
+                         ("e_blur", "<f8"), ("kept", "<i4"), ("doi", "<f8"), ("doi_blur", "<f8")], align=True)
 assert HIT_DTYPE.itemsize == C.sizeof(Hit)
 assert SINGLE_DTYPE.itemsize == C.sizeof(Single)
 
@@ -188,7 +189,8 @@ def pack_source(src):
 
 
 def pack_digitizer(dg):
-    return Digitizer(dg["fwhm_at_511"], dg["e_lo"], dg["e_hi"], dg["window_ns"], dg["e_cut"])
+    return Digitizer(dg["fwhm_at_511"], dg["e_lo"], dg["e_hi"], dg["window_ns"], dg["e_cut"],
+                     dg.get("doi_fwhm_mm", 0.0))
 
 
 def n_crystals(sc) -> int:

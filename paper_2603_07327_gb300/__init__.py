@@ -23,11 +23,12 @@ ERRORS = {-1: "GPET_ERR_INVALID_ARG", -2: "GPET_ERR_GEOMETRY", -3: "GPET_ERR_OOM
 SINGLES_T_PS, SINGLES_H, SINGLES_UNIT, SINGLES_PANEL, SINGLES_E, SINGLES_E_RAW = range(6)
 COINC_A, COINC_B, TALLY_COUNT, TALLY_EFX = 6, 7, 8, 9
 HITS_H, HITS_GSTEP, HITS_CRYSTAL, HITS_LAYER, HITS_WUV, HITS_E, HITS_T_PS = range(10, 17)
+SINGLES_DOI = 17
 _ARRAY_DTYPE = {SINGLES_T_PS: np.uint64, SINGLES_H: np.uint64, SINGLES_UNIT: np.int32, SINGLES_PANEL: np.int32,
                 SINGLES_E: np.float32, SINGLES_E_RAW: np.float32, COINC_A: np.int32, COINC_B: np.int32,
                 TALLY_COUNT: np.uint64, TALLY_EFX: np.uint64, HITS_H: np.uint64, HITS_GSTEP: np.int32,
                 HITS_CRYSTAL: np.int32, HITS_LAYER: np.int32, HITS_WUV: np.float32, HITS_E: np.float32,
-                HITS_T_PS: np.uint64}
+                HITS_T_PS: np.uint64, SINGLES_DOI: np.float32}
 
 KERNEL_DEFAULT, KERNEL_LOOP, KERNEL_WAVE = 0, 1, 2
 
@@ -65,7 +66,7 @@ class Source(C.Structure):
 
 class Digitizer(C.Structure):
     _fields_ = [("fwhm_at_511", C.c_double), ("e_lo_kev", C.c_double), ("e_hi_kev", C.c_double),
-                ("coinc_window_ns", C.c_double), ("e_cut_kev", C.c_double)]
+                ("coinc_window_ns", C.c_double), ("e_cut_kev", C.c_double), ("doi_fwhm_mm", C.c_double)]
 
 
 class Options(C.Structure):
@@ -183,7 +184,8 @@ def source_struct(src):
 
 
 def digitizer_struct(dg):
-    return Digitizer(dg["fwhm_at_511"], dg["e_lo"], dg["e_hi"], dg["window_ns"], dg["e_cut"])
+    return Digitizer(dg["fwhm_at_511"], dg["e_lo"], dg["e_hi"], dg["window_ns"], dg["e_cut"],
+                     dg.get("doi_fwhm_mm", 0.0))
 
 
 def options_struct(keep_hits=False, block_size=0, blocks_per_sm=0, kernel=0, compact_every=0, pool_depth=0,
@@ -264,7 +266,7 @@ class Result:
         dt = np.dtype(_ARRAY_DTYPE[which])
         if n is None:
             c = self.counts()
-            if which <= SINGLES_E_RAW:
+            if which <= SINGLES_E_RAW or which == SINGLES_DOI:
                 n = c["singles"]
             elif which in (COINC_A, COINC_B):
                 n = c["coincidences"]
@@ -282,7 +284,8 @@ class Result:
 
     def singles(self) -> dict:
         return dict(t_ps=self.array(SINGLES_T_PS), h=self.array(SINGLES_H), unit=self.array(SINGLES_UNIT),
-                    panel=self.array(SINGLES_PANEL), e=self.array(SINGLES_E), e_raw=self.array(SINGLES_E_RAW))
+                    panel=self.array(SINGLES_PANEL), e=self.array(SINGLES_E), e_raw=self.array(SINGLES_E_RAW),
+                    doi=self.array(SINGLES_DOI))
 
     def coincidences(self):
         return self.array(COINC_A), self.array(COINC_B)

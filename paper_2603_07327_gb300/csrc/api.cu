@@ -370,7 +370,8 @@ int gpet_make_job(const gpet_scanner *sc, const gpet_source *src, const gpet_dig
         return gpet_fail(GPET_ERR_INVALID_ARG, "phantom source without a loaded activity map");
     if (!(dg->e_cut_kev >= kXsEmin) || !(dg->e_cut_kev < 511.0))
         return gpet_fail(GPET_ERR_INVALID_ARG, "e_cut_kev must lie in [%g, 511)", (double)kXsEmin);
-    if (!(dg->fwhm_at_511 >= 0.0) || !(dg->coinc_window_ns >= 0.0) || !(dg->e_hi_kev >= dg->e_lo_kev))
+    if (!(dg->fwhm_at_511 >= 0.0) || !(dg->coinc_window_ns >= 0.0) || !(dg->e_hi_kev >= dg->e_lo_kev) ||
+        !(dg->doi_fwhm_mm >= 0.0))
         return gpet_fail(GPET_ERR_INVALID_ARG, "digitizer settings out of range");
     const double span = (double)n_decays / src->activity_bq * 1e12;
     if (!(span < 4.0e15)) return gpet_fail(GPET_ERR_INVALID_ARG, "acquisition longer than 4000 s (time key limit)");
@@ -394,6 +395,7 @@ int gpet_make_job(const gpet_scanner *sc, const gpet_source *src, const gpet_dig
     J.e_lo = (float)dg->e_lo_kev;
     J.e_hi = (float)dg->e_hi_kev;
     J.sig_k = (float)(dg->fwhm_at_511 / (2.0 * std::sqrt(2.0 * std::log(2.0))));
+    J.sig_doi = (float)(dg->doi_fwhm_mm / (2.0 * std::sqrt(2.0 * std::log(2.0))));
     if (sc->has_phantom) {
         J.has_phantom = 1;
         J.ph_nx = sc->ph_n[0]; J.ph_ny = sc->ph_n[1]; J.ph_nz = sc->ph_n[2];

@@ -67,6 +67,7 @@ struct JobDev {
     int32_t geom, src_kind;
     float src_pos[3], src_dir[3];
     float e_cut, e_lo, e_hi, sig_k;   // sig_k = fwhm_511 / (2 sqrt(2 ln 2))
+    float sig_doi, pad_doi;           // depth blur sigma (mm)
     // phantom (has_phantom = 0 when none)
     int32_t has_phantom, ph_nx, ph_ny, ph_nz, ph_nmat;
     float ph_origin[3], ph_voxel[3], ph_inv_voxel[3], ph_hi[3];

@@ -32,14 +32,14 @@ struct SortDev {
     const unsigned long long *n_in;  // device count of unsorted singles
     const uint64_t *in_t, *in_h;
     const int32_t *in_unit, *in_panel, *in_job;
-    const float *in_e, *in_eraw;
+    const float *in_e, *in_eraw, *in_doi;
 };
 
 // time-ordered singles
 struct SinglesDev {
     uint64_t *t, *h;
     int32_t *unit, *panel, *job;
-    float *e, *eraw;
+    float *e, *eraw, *doi;
     unsigned long long *n;
 };
 

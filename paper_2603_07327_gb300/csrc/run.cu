@@ -139,7 +139,7 @@ int run_plan(Run &R) {
     OutDev &O = R.O;
     cv.take(O.s_t, cap); cv.take(O.s_h, cap);
     cv.take(O.s_unit, cap); cv.take(O.s_panel, cap); cv.take(O.s_job, cap);
-    cv.take(O.s_e, cap); cv.take(O.s_eraw, cap);
+    cv.take(O.s_e, cap); cv.take(O.s_eraw, cap); cv.take(O.s_doi, cap);
     // hits
     if (hcap) {
         cv.take(O.hit_h, hcap); cv.take(O.hit_t, hcap);
@@ -157,7 +157,7 @@ int run_plan(Run &R) {
     SinglesDev &SD = R.SD;
     cv.take(SD.t, cap); cv.take(SD.h, cap);
     cv.take(SD.unit, cap); cv.take(SD.panel, cap); cv.take(SD.job, cap);
-    cv.take(SD.e, cap); cv.take(SD.eraw, cap);
+    cv.take(SD.e, cap); cv.take(SD.eraw, cap); cv.take(SD.doi, cap);
     // coincidences
     CoincDev &C = R.C;
     cv.take(C.flag, cap);
@@ -183,7 +183,7 @@ int run_plan(Run &R) {
     rebase(R.d_tally_efx, base);
     rebase(d_jobs, base); rebase(d_geoms, base); rebase(d_cs, base); rebase(R.d_window, base);
     rebase(O.s_t, base); rebase(O.s_h, base); rebase(O.s_unit, base); rebase(O.s_panel, base);
-    rebase(O.s_job, base); rebase(O.s_e, base); rebase(O.s_eraw, base);
+    rebase(O.s_job, base); rebase(O.s_e, base); rebase(O.s_eraw, base); rebase(O.s_doi, base);
     if (hcap) {
         rebase(O.hit_h, base); rebase(O.hit_t, base); rebase(O.hit_gstep, base); rebase(O.hit_crystal, base);
         rebase(O.hit_layer, base); rebase(O.hit_job, base); rebase(O.hit_wuv, base); rebase(O.hit_e, base);
@@ -195,7 +195,7 @@ int run_plan(Run &R) {
     rebase(S.keys[0], base); rebase(S.keys[1], base); rebase(S.vals[0], base); rebase(S.vals[1], base);
     rebase(S.plan, base); rebase(S.tile_hist, base);
     rebase(SD.t, base); rebase(SD.h, base); rebase(SD.unit, base); rebase(SD.panel, base); rebase(SD.job, base);
-    rebase(SD.e, base); rebase(SD.eraw, base);
+    rebase(SD.e, base); rebase(SD.eraw, base); rebase(SD.doi, base);
     rebase(C.flag, base); rebase(C.tile_cnt, base); rebase(C.a, base); rebase(C.b, base);
     rebase(JS.s_off, base); rebase(JS.c_off, base); rebase(JS.hits, base); rebase(d_toff, base); rebase(d_tn, base);
     JS.n_jobs = nj;
@@ -232,7 +232,7 @@ int run_plan(Run &R) {
     S.cap = cap;
     S.n_in = &H->n_singles;
     S.in_t = O.s_t; S.in_h = O.s_h; S.in_unit = O.s_unit; S.in_panel = O.s_panel; S.in_job = O.s_job;
-    S.in_e = O.s_e; S.in_eraw = O.s_eraw;
+    S.in_e = O.s_e; S.in_eraw = O.s_eraw; S.in_doi = O.s_doi;
     SD.n = &H->n_sorted;
     C.n = &H->n_coinc;
     C.window_ps = R.d_window;
@@ -341,11 +341,11 @@ size_t run_footprint(uint64_t total_decays, int64_t total_crystals, int n_jobs, 
     size_t b = 0;
     b += sizeof(RunHeader) + 8 * 256 * 4 + 16 * (size_t)total_crystals;
     b += sizeof(JobDev) * n_jobs + sizeof(GeomDev) * n_geoms + 8 * (n_jobs + 1) + 8 * n_jobs;
-    b += cap * (8 + 8 + 4 * 5);                  // raw singles
+    b += cap * (8 + 8 + 4 * 6);                  // raw singles
     b += hcap * (8 + 8 + 4 * 4 + 12 + 4);        // hits
     b += ocap * 12;                              // overflow list
     b += cap * (2 * 8 + 2 * 4) + 256 * 4 * tiles + 128;  // sort
-    b += cap * (8 + 8 + 4 * 5);                  // sorted singles
+    b += cap * (8 + 8 + 4 * 6);                  // sorted singles
     b += cap + 4 * tiles + 2 * 4 * (cap / 2 + 1); // coincidences
     b += 8 * (n_jobs + 1) * 2 + 8 * n_jobs * 3;  // per-job statistics
     return b + 64 * 256;                         // alignment slack
@@ -450,6 +450,7 @@ static int result_array(const gpet_result *r, int32_t which, ArrayView &v) {
         case GPET_SINGLES_PANEL: v = {R.SD.panel + s0, ns * 4}; break;
         case GPET_SINGLES_E: v = {R.SD.e + s0, ns * 4}; break;
         case GPET_SINGLES_E_RAW: v = {R.SD.eraw + s0, ns * 4}; break;
+        case GPET_SINGLES_DOI: v = {R.SD.doi + s0, ns * 4}; break;
         case GPET_COINC_A: v = {R.C.a + c0, nc * 4}; break;
         case GPET_COINC_B: v = {R.C.b + c0, nc * 4}; break;
         case GPET_TALLY_COUNT: v = {R.d_tally_count + R.tally_off[j], (size_t)R.job_crystals[j] * 8}; break;
@@ -463,9 +464,9 @@ static int result_array(const gpet_result *r, int32_t which, ArrayView &v) {
         case GPET_HITS_T_PS: v = {R.O.hit_t, nh * 8}; break;
         default: return gpet_fail(GPET_ERR_INVALID_ARG, "unknown result array %d", which);
     }
-    if (which >= GPET_HITS_H && !R.keep_hits)
+    if (which >= GPET_HITS_H && which <= GPET_HITS_T_PS && !R.keep_hits)
         return gpet_fail(GPET_ERR_INVALID_ARG, "hits were not kept (gpet_options.keep_hits = 0)");
-    if (which >= GPET_HITS_H && R.jobs.size() > 1)
+    if (which >= GPET_HITS_H && which <= GPET_HITS_T_PS && R.jobs.size() > 1)
         return gpet_fail(GPET_ERR_INVALID_ARG, "hit lists are kept for single-job runs only");
     return GPET_OK;
 }

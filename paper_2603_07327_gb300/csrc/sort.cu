@@ -214,6 +214,7 @@ __global__ void k_gather(SortDev S, SinglesDev out) {
         out.job[i] = S.in_job[j];
         out.e[i] = S.in_e[j];
         out.eraw[i] = S.in_eraw[j];
+        out.doi[i] = S.in_doi[j];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *out.n = n;
 }

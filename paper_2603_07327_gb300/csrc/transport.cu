@@ -76,10 +76,12 @@ __global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int
     uint32_t *sl_unit = reinterpret_cast<uint32_t *>(sgeom + ng_smem);
     float *sl_e = reinterpret_cast<float *>(sl_unit + S * blockDim.x);
     uint32_t *sl_dt = reinterpret_cast<uint32_t *>(sl_e + S * blockDim.x);
+    float *sl_ew = reinterpret_cast<float *>(sl_dt + S * blockDim.x);
     stage_geometry(W, sgeom, ng_smem);
     __syncthreads();
 
-    const SinglesList SL{sl_unit + threadIdx.x, sl_e + threadIdx.x, sl_dt + threadIdx.x, (int)blockDim.x};
+    const SinglesList SL{sl_unit + threadIdx.x, sl_e + threadIdx.x, sl_dt + threadIdx.x, sl_ew + threadIdx.x,
+                         (int)blockDim.x};
     PState s;
     s.phase = kPhIdle;
     s.job = 0;
@@ -136,7 +138,8 @@ __global__ void __launch_bounds__(128) k_transport_redo(WorkDev W, OutDev O) {
     uint32_t l_unit[S];
     float l_e[S];
     uint32_t l_dt[S];
-    const SinglesList SL{l_unit, l_e, l_dt, 1};
+    float l_ew[S];
+    const SinglesList SL{l_unit, l_e, l_dt, l_ew, 1};
     const unsigned long long n = min(*O.n_ovf, O.ovf_cap);
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
     int status = kStatusOk;
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(128) k_transport_redo(WorkDev W, OutDev O) {
 // host launchers
 // ---------------------------------------------------------------------------
 static size_t loop_smem(int ng_smem, int block, int S) {
-    return (size_t)ng_smem * sizeof(GeomDev) + (size_t)S * block * 12;
+    return (size_t)ng_smem * sizeof(GeomDev) + (size_t)S * block * 16;
 }
 
 cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {

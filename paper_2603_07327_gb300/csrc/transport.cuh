@@ -24,6 +24,7 @@ struct SinglesList {
     uint32_t *unit;
     float *e;
     uint32_t *dt;
+    float *ew;      // sum of energy x depth (for the single's depth of interaction)
     int stride;
 };
 
@@ -32,7 +33,7 @@ struct OutDev {
     // kept singles (SoA); count in *n_singles (may exceed cap -> overflow, host re-runs)
     uint64_t *s_t, *s_h;
     int32_t *s_unit, *s_panel, *s_job;
-    float *s_e, *s_eraw;
+    float *s_e, *s_eraw, *s_doi;
     unsigned long long *n_singles;
     unsigned long long s_cap;
     // optional crystal interactions
@@ -252,7 +253,7 @@ __device__ __forceinline__ void ev_flight(const JobDev &J, const GeomDev &g, PSt
 
 // record energy `dep` deposited in crystal L.crystal into the history's singles list
 __device__ __forceinline__ void add_single(const GeomDev &g, PState &s, const SinglesList &SL, int max_entries,
-                                           int crystal, int module, float dep, uint32_t dtp) {
+                                           int crystal, int module, float dep, uint32_t dtp, float w) {
     uint32_t unit;
     if (g.readout_level == 0) unit = (uint32_t)s.panel;
     else if (g.readout_level == 1) unit = (uint32_t)(s.panel * g.modules_u * g.modules_v + module);
@@ -260,6 +261,7 @@ __device__ __forceinline__ void add_single(const GeomDev &g, PState &s, const Si
     for (uint32_t j = 0; j < s.nsing; ++j) {
         if (SL.unit[j * SL.stride] == unit) {
             SL.e[j * SL.stride] += dep;
+            SL.ew[j * SL.stride] += dep * w;
             SL.dt[j * SL.stride] = min(SL.dt[j * SL.stride], dtp);
             return;
         }
@@ -267,6 +269,7 @@ __device__ __forceinline__ void add_single(const GeomDev &g, PState &s, const Si
     if ((int)s.nsing < max_entries) {
         SL.unit[s.nsing * SL.stride] = unit;
         SL.e[s.nsing * SL.stride] = dep;
+        SL.ew[s.nsing * SL.stride] = dep * w;
         SL.dt[s.nsing * SL.stride] = dtp;
         s.nsing++;
     } else {
@@ -300,7 +303,7 @@ __device__ __forceinline__ void record_hit(const JobDev &J, const GeomDev &g, co
             }
         }
     }
-    add_single(g, s, SL, max_entries, crystal, module, dep, dtp);
+    add_single(g, s, SL, max_entries, crystal, module, dep, dtp, s.x);
 }
 
 // one Woodcock step inside the current panel (layer selection, interaction, hit)
@@ -387,7 +390,7 @@ __device__ __forceinline__ void ev_finish(const JobDev *__restrict__ jobs, const
     const uint32_t nmax = __reduce_max_sync(mask, n);
     for (uint32_t j = 0; j < nmax; ++j) {
         bool keep = false;
-        float e = 0.f, eb = 0.f;
+        float e = 0.f, eb = 0.f, db = 0.f;
         uint32_t unit = 0, dt = 0;
         if (j < n) {
             unit = SL.unit[j * SL.stride];
@@ -395,10 +398,13 @@ __device__ __forceinline__ void ev_finish(const JobDev *__restrict__ jobs, const
             dt = SL.dt[j * SL.stride];
             const uint4 q = philox4x32_10(make_uint4((uint32_t)s.h, (uint32_t)(s.h >> 32), kTagDigi << 28, unit),
                                           make_uint2((uint32_t)J->seed, (uint32_t)(J->seed >> 32)));
-            float cp = cospif(2.0f * u01(q.y));
-            const float n01 = sqrtf(-2.0f * logf(u01(q.x))) * cp;
+            // one Box-Muller pair: the cosine normal blurs the energy, the sine one the depth
+            float sp, cp;
+            sincospif(2.0f * u01(q.y), &sp, &cp);
+            const float rad = sqrtf(-2.0f * logf(u01(q.x)));
             const float sigma = J->sig_k * sqrtf(kE0 * e);
-            eb = fmaf(sigma, n01, e);
+            eb = fmaf(sigma, rad * cp, e);
+            db = fmaf(J->sig_doi, rad * sp, SL.ew[j * SL.stride] / e);
             keep = eb >= J->e_lo && eb <= J->e_hi;
         }
         const uint32_t b = __ballot_sync(mask, keep);
@@ -422,6 +428,7 @@ __device__ __forceinline__ void ev_finish(const JobDev *__restrict__ jobs, const
                 O.s_job[slot] = s.job;
                 O.s_e[slot] = eb;
                 O.s_eraw[slot] = e;
+                O.s_doi[slot] = db;
             }
         }
     }

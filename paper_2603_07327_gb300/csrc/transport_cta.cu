@@ -32,6 +32,7 @@ struct CtaPool {
     uint32_t sl_unit[kCtaS * kPool];
     float sl_e[kCtaS * kPool];
     uint32_t sl_dt[kCtaS * kPool];
+    float sl_ew[kCtaS * kPool];
 };
 
 template <class Pool>
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_transport_cta(WorkDev W, OutD
         PState s;
         s.phase = kPhIdle;
         s.job = 0;
-        const SinglesList SL{P.sl_unit + q, P.sl_e + q, P.sl_dt + q, kPool};
+        const SinglesList SL{P.sl_unit + q, P.sl_e + q, P.sl_dt + q, P.sl_ew + q, kPool};
         if (best_p == kPhFinish) {
             if (active) cload(P, q, s);
             __syncwarp();

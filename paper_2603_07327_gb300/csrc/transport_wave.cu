@@ -29,6 +29,7 @@ struct WarpPool {
     uint32_t sl_unit[kWaveS * kPool];
     float sl_e[kWaveS * kPool];
     uint32_t sl_dt[kWaveS * kPool];
+    float sl_ew[kWaveS * kPool];
 };
 
 enum : int {
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
         PState s;
         s.phase = kPhIdle;
         s.job = 0;
-        const SinglesList SL{P.sl_unit + q, P.sl_e + q, P.sl_dt + q, kPool};
+        const SinglesList SL{P.sl_unit + q, P.sl_e + q, P.sl_dt + q, P.sl_ew + q, kPool};
         if (best_p == kPhFinish) {
             // finished histories as one wavefront: blur, window, append
             if (active) pool_load(P, q, s);

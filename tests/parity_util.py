@@ -5,7 +5,9 @@ Tolerances (FP32 transport against FP64):
   * crystal / layer ids identical, history by history, in >= 99.99 % of histories;
   * deposits within 1e-5 relative; positions within 1e-3 mm; times within 1 ps;
   * blurred energies within 1e-5 relative + 1e-3 keV; window-edge flips allowed
-    only within 1e-3 keV of an edge.
+    only within 1e-3 keV of an edge;
+  * depth of interaction of a single (energy-weighted hit depth plus its blur)
+    within 2e-3 mm: the hit positions' 1e-3 mm plus FP32 rounding of the blur.
 """
 from __future__ import annotations
 
@@ -15,6 +17,7 @@ E_REL = 1e-5
 POS_ABS = 1e-3
 T_ABS = 1
 EB_ABS = 1e-3
+DOI_ABS = 2e-3
 
 
 def gpu_hits_table(h):
@@ -87,6 +90,8 @@ def compare_singles(gs, os_, bad, e_lo, e_hi):
     eo = ok_o["e_blur"][mo][io]
     rg = gs["e_raw"][mg][ig].astype(np.float64)
     ro = ok_o["e_raw"][mo][io]
+    dgi = gs["doi"][mg][ig].astype(np.float64)
+    doo = ok_o["doi_blur"][mo][io]
     tg = gs["t_ps"][mg][ig].astype(np.int64)
     to = ok_o["t_ps"][mo][io].astype(np.int64)
     # singles on one side only must sit at a window edge (blur flips)
@@ -107,7 +112,8 @@ def compare_singles(gs, os_, bad, e_lo, e_hi):
     return dict(n_gpu=int(mg.sum()), n_orc=int(mo.sum()), n_common=len(common), edge_flips=edge_flips,
                 max_rel_eraw=float((np.abs(rg - ro) / ro).max()) if len(common) else 0.0,
                 max_blur_dev=float((np.abs(eg - eo) - E_REL * eo).max()) if len(common) else 0.0,
-                max_dt=int(np.abs(tg - to).max()) if len(common) else 0)
+                max_dt=int(np.abs(tg - to).max()) if len(common) else 0,
+                max_doi_dev=float(np.abs(dgi - doo).max()) if len(common) else 0.0)
 
 
 def coincidence_set(h, unit, a, b):

@@ -50,6 +50,7 @@ def check_parity(G, oracle, res, orc, n, dg, min_hist_frac=0.9999):
     assert sc_["max_rel_eraw"] <= PU.E_REL, sc_
     assert sc_["max_blur_dev"] <= PU.EB_ABS, sc_
     assert sc_["max_dt"] <= PU.T_ABS, sc_
+    assert sc_["max_doi_dev"] <= PU.DOI_ABS, sc_
     # time order of the sorted singles
     assert np.all(np.diff(gs["t_ps"].astype(np.int64)) >= 0)
     # coincidences
@@ -96,7 +97,7 @@ def test_parity_small(G, oracle, name, kernel):
     mk_sc, mk_src, mk_ph, n, seed = CASES[name]
     sc, src = mk_sc(), mk_src()
     ph = mk_ph() if mk_ph else None
-    dg = W.digitizer()
+    dg = W.digitizer(doi_fwhm_mm=1.5)
     res, orc = run_both(G, oracle, sc, src, dg, n, seed, phantom=ph, kernel=KERNELS[kernel])
     check_parity(G, oracle, res, orc, n, dg)
 

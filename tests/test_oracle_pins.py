@@ -587,3 +587,28 @@ def test_energy_conservation_high_cutoff(oracle):
     _, inv = np.unique(key, return_inverse=True)
     tot = np.bincount(inv, weights=h["edep"])
     assert np.all((tot > 511.0 - 1e-9) | (tot < 511.0 - 300.0 + 1e-9))
+
+
+def test_doi_blur_of_singles(oracle):
+    """Depth of a single = energy-weighted depth of its hits; the depth blur is
+    Gaussian with FWHM doi_fwhm_mm and independent of the energy blur (the two
+    normals of one Box-Muller pair)."""
+    sc = W.h2rspet("2CL", modules_v=2)
+    dg = W.digitizer(e_lo=0.0, e_hi=5000.0, doi_fwhm_mm=2.0)
+    r = oracle.simulate(sc, W.point_source((2.0, -1.0, 10.0)), dg, 60000, 14, threads=8)
+    hits, s = r["hits"], r["singles"]
+    key_h = hits["h"].astype(np.int64) * 10_000_000 + hits["crystal"]
+    uk, inv = np.unique(key_h, return_inverse=True)
+    ew = np.bincount(inv, weights=hits["edep"] * hits["w"]) / np.bincount(inv, weights=hits["edep"])
+    key_s = s["h"].astype(np.int64) * 10_000_000 + s["unit"]
+    order = np.argsort(key_s)
+    np.testing.assert_allclose(s["doi"][order], ew, rtol=1e-12, atol=1e-12)
+    assert np.all((s["doi"] >= 0.0) & (s["doi"] <= 10.0))
+    sig = 2.0 / (2 * math.sqrt(2 * math.log(2)))
+    zd = (s["doi_blur"] - s["doi"]) / sig
+    ze = (s["e_blur"] - s["e_raw"]) / (0.15 / (2 * math.sqrt(2 * math.log(2))) * np.sqrt(511.0 * s["e_raw"]))
+    assert stats.kstest(zd, "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(zd, ze)[0, 1]) < 4 / math.sqrt(len(zd))
+    # no depth blur: the depth is reported as is
+    r0 = oracle.simulate(sc, W.point_source((2.0, -1.0, 10.0)), W.digitizer(e_lo=0, e_hi=5000), 5000, 14, threads=4)
+    assert np.array_equal(r0["singles"]["doi"], r0["singles"]["doi_blur"])

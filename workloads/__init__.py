@@ -70,9 +70,9 @@ def scanner(n_panels, inner_radius, layers, modules_u=1, modules_v=1, module_gap
                 layers=list(layers), materials=list(materials), readout_level=int(readout_level))
 
 
-def digitizer(fwhm_at_511=0.15, e_lo=350.0, e_hi=650.0, window_ns=2.0, e_cut=10.0):
+def digitizer(fwhm_at_511=0.15, e_lo=350.0, e_hi=650.0, window_ns=2.0, e_cut=10.0, doi_fwhm_mm=0.0):
     return dict(fwhm_at_511=float(fwhm_at_511), e_lo=float(e_lo), e_hi=float(e_hi),
-                window_ns=float(window_ns), e_cut=float(e_cut))
+                window_ns=float(window_ns), e_cut=float(e_cut), doi_fwhm_mm=float(doi_fwhm_mm))
 
 
 def point_source(pos=(0.0, 0.0, 0.0), activity_bq=DEFAULT_ACTIVITY_BQ):
