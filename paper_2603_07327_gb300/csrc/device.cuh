@@ -14,6 +14,16 @@
 
 namespace gpet {
 
+// One single as the transport kernels append it: a 48-byte record, so that the
+// time-order gather reads each single from two 32-byte sectors.
+struct __align__(16) RawSingle {
+    uint64_t t, h;        // time (ps), history
+    int32_t unit, panel, job;
+    float e, e_raw, doi;  // blurred and raw energy (keV), blurred depth (mm)
+    uint32_t pad[2];
+};
+static_assert(sizeof(RawSingle) == 48, "RawSingle layout");
+
 constexpr uint32_t kFullMask = 0xFFFFFFFFu;
 constexpr int kMaxPanels = 64;
 constexpr int kMaxLayers = 8;

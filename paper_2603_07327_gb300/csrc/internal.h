@@ -30,9 +30,7 @@ struct SortDev {
     unsigned long long max_tiles;
     unsigned long long cap;
     const unsigned long long *n_in;  // device count of unsorted singles
-    const uint64_t *in_t, *in_h;
-    const int32_t *in_unit, *in_panel, *in_job;
-    const float *in_e, *in_eraw, *in_doi;
+    const RawSingle *in_raw;         // unsorted singles
 };
 
 // time-ordered singles
@@ -63,6 +61,10 @@ cudaError_t launch_job_stats(const SinglesDev &s, const CoincDev &C, const JobSt
 cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
 cudaError_t launch_transport_wave(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
 cudaError_t launch_transport_cta(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
+// warps resident at once in the transport launch that cfg selects (sizes the work chunks)
+cudaError_t transport_resident_warps(int n_geoms, const LaunchCfg &cfg, long long *warps);
+cudaError_t wave_resident_warps(int n_geoms, const LaunchCfg &cfg, long long *warps);
+cudaError_t cta_resident_warps(int n_geoms, const LaunchCfg &cfg, long long *warps);
 cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const CoincDev &C, int sm_count,
                               cudaStream_t st);
 cudaError_t launch_radix_passes(const SortDev &S, int sm_count, cudaStream_t st);

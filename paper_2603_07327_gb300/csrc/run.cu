@@ -104,11 +104,14 @@ int run_plan(Run &R) {
     int64_t tc = 0;
     for (int j = 0; j < nj; ++j) { R.tally_off[j] = tc; tc += R.job_crystals[j]; }
     R.total_crystals = tc;
-    // chunks: small enough that every warp of the grid gets work
+    // chunks: about 48 per resident warp, so that warps run out of work within
+    // a small fraction of the launch of one another (32..4096 histories)
     uint64_t total = 0;
     for (auto &J : R.jobs) total += J.n_hist;
-    const uint64_t warps = (uint64_t)R.cfg.grid * (R.cfg.block_size / 32);
-    uint64_t cs = total / std::max<uint64_t>(warps * 8, 1);
+    long long warps = 0;
+    cudaError_t we = transport_resident_warps((int)R.geoms.size(), R.cfg, &warps);
+    if (we != cudaSuccess) return gpet_cuda_fail(we, "transport occupancy query");
+    uint64_t cs = total / std::max<uint64_t>((uint64_t)warps * 48, 1);
     cs = std::max<uint64_t>(32, std::min<uint64_t>(4096, cs / 32 * 32));
     R.chunk_size = (unsigned)cs;
     R.chunk_start.assign(nj + 1, 0);
@@ -137,9 +140,7 @@ int run_plan(Run &R) {
     cv.take(R.d_window, nj);
     // raw singles
     OutDev &O = R.O;
-    cv.take(O.s_t, cap); cv.take(O.s_h, cap);
-    cv.take(O.s_unit, cap); cv.take(O.s_panel, cap); cv.take(O.s_job, cap);
-    cv.take(O.s_e, cap); cv.take(O.s_eraw, cap); cv.take(O.s_doi, cap);
+    cv.take(O.s_raw, cap);
     // hits
     if (hcap) {
         cv.take(O.hit_h, hcap); cv.take(O.hit_t, hcap);
@@ -182,8 +183,7 @@ int run_plan(Run &R) {
     rebase(R.d_tally_count, base);
     rebase(R.d_tally_efx, base);
     rebase(d_jobs, base); rebase(d_geoms, base); rebase(d_cs, base); rebase(R.d_window, base);
-    rebase(O.s_t, base); rebase(O.s_h, base); rebase(O.s_unit, base); rebase(O.s_panel, base);
-    rebase(O.s_job, base); rebase(O.s_e, base); rebase(O.s_eraw, base); rebase(O.s_doi, base);
+    rebase(O.s_raw, base);
     if (hcap) {
         rebase(O.hit_h, base); rebase(O.hit_t, base); rebase(O.hit_gstep, base); rebase(O.hit_crystal, base);
         rebase(O.hit_layer, base); rebase(O.hit_job, base); rebase(O.hit_wuv, base); rebase(O.hit_e, base);
@@ -231,8 +231,7 @@ int run_plan(Run &R) {
     S.max_tiles = tiles;
     S.cap = cap;
     S.n_in = &H->n_singles;
-    S.in_t = O.s_t; S.in_h = O.s_h; S.in_unit = O.s_unit; S.in_panel = O.s_panel; S.in_job = O.s_job;
-    S.in_e = O.s_e; S.in_eraw = O.s_eraw; S.in_doi = O.s_doi;
+    S.in_raw = O.s_raw;
     SD.n = &H->n_sorted;
     C.n = &H->n_coinc;
     C.window_ps = R.d_window;
@@ -341,7 +340,7 @@ size_t run_footprint(uint64_t total_decays, int64_t total_crystals, int n_jobs, 
     size_t b = 0;
     b += sizeof(RunHeader) + 8 * 256 * 4 + 16 * (size_t)total_crystals;
     b += sizeof(JobDev) * n_jobs + sizeof(GeomDev) * n_geoms + 8 * (n_jobs + 1) + 8 * n_jobs;
-    b += cap * (8 + 8 + 4 * 6);                  // raw singles
+    b += cap * sizeof(RawSingle);                // raw singles
     b += hcap * (8 + 8 + 4 * 4 + 12 + 4);        // hits
     b += ocap * 12;                              // overflow list
     b += cap * (2 * 8 + 2 * 4) + 256 * 4 * tiles + 128;  // sort

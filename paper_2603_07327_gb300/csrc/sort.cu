@@ -37,7 +37,9 @@ __global__ void __launch_bounds__(kSortThreads) k_make_keys(SortDev S) {
     const unsigned long long n = sort_n(S);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint64_t key = ((uint64_t)(uint32_t)S.in_job[i] << 52) | S.in_t[i];
+        const uint4 r0 = __ldg(reinterpret_cast<const uint4 *>(S.in_raw + i));
+        const uint32_t job = __ldg(reinterpret_cast<const uint32_t *>(S.in_raw + i) + 6);
+        const uint64_t key = ((uint64_t)job << 52) | (((uint64_t)r0.y << 32) | r0.x);
         S.keys[0][i] = key;
         S.vals[0][i] = (uint32_t)i;
 #pragma unroll
@@ -139,21 +141,35 @@ __global__ void __launch_bounds__(1024) k_digit_scan(SortDev S, int p) {
     }
 }
 
-// stable scatter of one tile: ranks in (warp, round, lane) order == input order
+// Stable scatter of one tile.  Ranks come in (warp, round, lane) order, which
+// is input order.  The tile is first rebuilt in shared memory in digit order,
+// then written out from there: consecutive threads write consecutive slots of
+// one digit's run, so the global stores coalesce (a direct store from the
+// ranking registers would send each of a warp's 32 keys to its own sector).
+struct ScatterSmem {
+    uint64_t keys[kTile];
+    uint32_t vals[kTile];
+    uint32_t wh[kSortThreads / 32][256];
+    uint32_t gdelta[256];   // global run start - local run start (mod 2^32)
+    uint32_t sw[32];
+};
+constexpr size_t kScatterSmem = sizeof(ScatterSmem);
+
 __global__ void __launch_bounds__(kSortThreads) k_scatter(SortDev S, int p) {
     if (!S.plan[p]) return;
+    extern __shared__ __align__(16) unsigned char scatter_raw[];
+    ScatterSmem &sm = *reinterpret_cast<ScatterSmem *>(scatter_raw);
     const int src = S.plan[kPasses + p];
     const unsigned long long n = sort_n(S);
     const unsigned long long tiles = (n + kTile - 1) / kTile;
     constexpr int kWarps = kSortThreads / 32;
-    __shared__ uint32_t wh[kWarps][256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint64_t *kin = S.keys[src];
     const uint32_t *vin = S.vals[src];
     uint64_t *kout = S.keys[src ^ 1];
     uint32_t *vout = S.vals[src ^ 1];
     for (unsigned long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-        for (int i = threadIdx.x; i < kWarps * 256; i += blockDim.x) (&wh[0][0])[i] = 0;
+        for (int i = threadIdx.x; i < kWarps * 256; i += blockDim.x) (&sm.wh[0][0])[i] = 0;
         __syncthreads();
         const unsigned long long wb = t * kTile + (unsigned long long)w * (32 * kSortItems);
         uint64_t k[kSortItems];
@@ -167,36 +183,54 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(SortDev S, int p) {
             v[j] = ok ? vin[i] : 0u;
             const uint32_t d = ok ? (uint32_t)((k[j] >> (8 * p)) & 0xFF) : 256u;
             const uint32_t peers = __match_any_sync(kFullMask, d);
-            const uint32_t before = (d < 256u) ? wh[w][d] : 0u;
+            const uint32_t before = (d < 256u) ? sm.wh[w][d] : 0u;
             rank[j] = before + __popc(peers & lane_lt());
             __syncwarp();
-            if (d < 256u && (peers & lane_lt()) == 0) wh[w][d] = before + __popc(peers);
+            if (d < 256u && (peers & lane_lt()) == 0) sm.wh[w][d] = before + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
-        // per digit: tile offset + exclusive prefix over the warps
-        for (int d = threadIdx.x; d < 256; d += blockDim.x) {
-            uint32_t off = S.tile_hist[(size_t)d * S.max_tiles + t];
+        // thread d owns digit d: warp prefixes, local run start, global delta
+        {
+            const int d = threadIdx.x;  // kSortThreads == 256 digits
+            uint32_t c = 0;
 #pragma unroll
             for (int ww = 0; ww < kWarps; ++ww) {
-                const uint32_t c = wh[ww][d];
-                wh[ww][d] = off;
-                off += c;
+                const uint32_t x = sm.wh[ww][d];
+                sm.wh[ww][d] = c;
+                c += x;
             }
+            uint32_t tot;
+            const uint32_t lstart = block_exscan(c, tot, sm.sw);
+#pragma unroll
+            for (int ww = 0; ww < kWarps; ++ww) sm.wh[ww][d] += lstart;
+            sm.gdelta[d] = S.tile_hist[(size_t)d * S.max_tiles + t] - lstart;
         }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const unsigned long long i = wb + (unsigned long long)j * 32 + lane;
             if (i < n) {
-                const uint32_t d = (uint32_t)((k[j] >> (8 * p)) & 0xFF);
-                const uint32_t pos = wh[w][d] + rank[j];
-                kout[pos] = k[j];
-                vout[pos] = v[j];
+                const uint32_t lp = sm.wh[w][(uint32_t)((k[j] >> (8 * p)) & 0xFF)] + rank[j];
+                sm.keys[lp] = k[j];
+                sm.vals[lp] = v[j];
             }
         }
         __syncthreads();
+        const unsigned long long rem = n - t * kTile;
+        const int tn = rem < (unsigned long long)kTile ? (int)rem : kTile;
+        for (int i = threadIdx.x; i < tn; i += kSortThreads) {
+            const uint64_t key = sm.keys[i];
+            const uint32_t pos = sm.gdelta[(uint32_t)((key >> (8 * p)) & 0xFF)] + (uint32_t)i;
+            kout[pos] = key;
+            vout[pos] = sm.vals[i];
+        }
+        __syncthreads();
     }
+}
+
+static cudaError_t scatter_smem_attr() {
+    return cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
 }
 
 // singles into time order
@@ -206,15 +240,16 @@ __global__ void k_gather(SortDev S, SinglesDev out) {
     const uint32_t *perm = S.vals[fin];
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint32_t j = perm[i];
-        out.t[i] = S.in_t[j];
-        out.h[i] = S.in_h[j];
-        out.unit[i] = S.in_unit[j];
-        out.panel[i] = S.in_panel[j];
-        out.job[i] = S.in_job[j];
-        out.e[i] = S.in_e[j];
-        out.eraw[i] = S.in_eraw[j];
-        out.doi[i] = S.in_doi[j];
+        const uint4 *r = reinterpret_cast<const uint4 *>(S.in_raw + perm[i]);
+        const uint4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+        out.t[i] = ((uint64_t)a.y << 32) | a.x;
+        out.h[i] = ((uint64_t)a.w << 32) | a.z;
+        out.unit[i] = (int32_t)b.x;
+        out.panel[i] = (int32_t)b.y;
+        out.job[i] = (int32_t)b.z;
+        out.e[i] = __uint_as_float(b.w);
+        out.eraw[i] = __uint_as_float(c.x);
+        out.doi[i] = __uint_as_float(c.y);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *out.n = n;
 }
@@ -350,20 +385,24 @@ cudaError_t launch_job_stats(const SinglesDev &s, const CoincDev &C, const JobSt
 // the allocation-free sort entry point; the simulation path keeps its own
 // launcher below).
 cudaError_t launch_radix_passes(const SortDev &S, int sm_count, cudaStream_t st) {
+    cudaError_t e = scatter_smem_attr();
+    if (e != cudaSuccess) return e;
     k_plan<<<1, kPasses * 32, 0, st>>>(S);
     for (int p = 0; p < kPasses; ++p) {
         const int tg = (int)(S.max_tiles < (unsigned long long)sm_count * 8 ? S.max_tiles
                                                                               : (unsigned long long)sm_count * 8);
         k_tile_hist<<<tg, kSortThreads, 0, st>>>(S, p);
         k_digit_scan<<<256, 1024, 0, st>>>(S, p);
-        k_scatter<<<tg, kSortThreads, 0, st>>>(S, p);
+        k_scatter<<<tg, kSortThreads, kScatterSmem, st>>>(S, p);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const CoincDev &C, int sm_count,
                               cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(S.ghist, 0, sizeof(uint32_t) * kPasses * 256, st);
+    cudaError_t e = scatter_smem_attr();
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(S.ghist, 0, sizeof(uint32_t) * kPasses * 256, st);
     if (e != cudaSuccess) return e;
     const int grid = sm_count * 4;
     k_make_keys<<<grid, kSortThreads, 0, st>>>(S);
@@ -372,7 +411,7 @@ cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const Coi
         const int tg = (int)(S.max_tiles < (unsigned long long)sm_count * 8 ? S.max_tiles : (unsigned long long)sm_count * 8);
         k_tile_hist<<<tg, kSortThreads, 0, st>>>(S, p);
         k_digit_scan<<<256, 1024, 0, st>>>(S, p);
-        k_scatter<<<tg, kSortThreads, 0, st>>>(S, p);
+        k_scatter<<<tg, kSortThreads, kScatterSmem, st>>>(S, p);
     }
     k_gather<<<grid, 256, 0, st>>>(S, out);
     // a cluster's flags are written by the thread at its start, possibly past

@@ -186,11 +186,34 @@ static size_t loop_smem(int ng_smem, int block, int S) {
     return (size_t)ng_smem * sizeof(GeomDev) + (size_t)S * block * 16;
 }
 
+// dynamic shared memory and resident CTAs of the per-lane loop kernel
+static cudaError_t loop_shape(int n_geoms, const LaunchCfg &cfg, size_t *smem, int *ctas) {
+    constexpr int S = 8;
+    const int ng = min(n_geoms, cfg.max_smem_geoms);
+    *smem = loop_smem(ng, cfg.block_size, S);
+    cudaError_t e = cudaFuncSetAttribute(k_transport_loop<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)*smem);
+    if (e != cudaSuccess) return e;
+    // persistent grid: never more CTAs than can be resident at once
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_loop<S>, cfg.block_size, *smem);
+    if (e != cudaSuccess) return e;
+    *ctas = cfg.sm_count * max(1, min(occ, cfg.grid / max(cfg.sm_count, 1)));
+    return cudaSuccess;
+}
+
+cudaError_t transport_resident_warps(int n_geoms, const LaunchCfg &cfg, long long *warps) {
+    if (cfg.kernel == kKernelWave) return wave_resident_warps(n_geoms, cfg, warps);
+    if (cfg.kernel == kKernelCta) return cta_resident_warps(n_geoms, cfg, warps);
+    size_t smem = 0;
+    int ctas = 0;
+    cudaError_t e = loop_shape(n_geoms, cfg, &smem, &ctas);
+    *warps = (long long)ctas * (cfg.block_size / 32);
+    return e;
+}
+
 cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
     constexpr int S = 8;
-    const int block = cfg.block_size;
-    const int ng = min(W.n_geoms, cfg.max_smem_geoms);
-    const size_t smem = loop_smem(ng, block, S);
     if (cfg.kernel == kKernelWave) {
         cudaError_t e = launch_transport_wave(W, O, cfg, st);
         if (e != cudaSuccess) return e;
@@ -198,15 +221,11 @@ cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg 
         cudaError_t e = launch_transport_cta(W, O, cfg, st);
         if (e != cudaSuccess) return e;
     } else {
-        cudaError_t e = cudaFuncSetAttribute(k_transport_loop<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        size_t smem = 0;
+        int ctas = 0;
+        cudaError_t e = loop_shape(W.n_geoms, cfg, &smem, &ctas);
         if (e != cudaSuccess) return e;
-        // persistent grid: never more CTAs than can be resident at once
-        int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_loop<S>, block, smem);
-        if (e != cudaSuccess) return e;
-        const int per_sm = max(1, min(occ, cfg.grid / max(cfg.sm_count, 1)));
-        k_transport_loop<S><<<cfg.sm_count * per_sm, block, smem, st>>>(W, O, ng);
+        k_transport_loop<S><<<ctas, cfg.block_size, smem, st>>>(W, O, min(W.n_geoms, cfg.max_smem_geoms));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

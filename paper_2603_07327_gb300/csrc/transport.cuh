@@ -31,9 +31,7 @@ struct SinglesList {
 // outputs shared by all jobs of a launch
 struct OutDev {
     // kept singles (SoA); count in *n_singles (may exceed cap -> overflow, host re-runs)
-    uint64_t *s_t, *s_h;
-    int32_t *s_unit, *s_panel, *s_job;
-    float *s_e, *s_eraw, *s_doi;
+    RawSingle *s_raw;
     unsigned long long *n_singles;
     unsigned long long s_cap;
     // optional crystal interactions
@@ -421,14 +419,11 @@ __device__ __forceinline__ void ev_finish(const JobDev *__restrict__ jobs, const
                 if (g.readout_level == 0) panel = (int)unit;
                 else if (g.readout_level == 1) panel = (int)(unit / (uint32_t)(g.modules_u * g.modules_v));
                 else panel = (int)(unit / (uint32_t)(g.crystals_per_module * g.modules_u * g.modules_v));
-                O.s_t[slot] = s.t0 + dt;
-                O.s_h[slot] = s.h;
-                O.s_unit[slot] = (int32_t)unit;
-                O.s_panel[slot] = panel;
-                O.s_job[slot] = s.job;
-                O.s_e[slot] = eb;
-                O.s_eraw[slot] = e;
-                O.s_doi[slot] = db;
+                const uint64_t t = s.t0 + dt;
+                uint4 *r = reinterpret_cast<uint4 *>(O.s_raw + slot);
+                r[0] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)s.h, (uint32_t)(s.h >> 32));
+                r[1] = make_uint4(unit, (uint32_t)panel, (uint32_t)s.job, __float_as_uint(eb));
+                r[2] = make_uint4(__float_as_uint(e), __float_as_uint(db), 0u, 0u);
             }
         }
     }

@@ -141,8 +141,9 @@ __device__ void cta_refill(const WorkDev &W, uint32_t need, uint64_t &pool_next,
 
 }  // namespace
 
+// at most 128 registers a thread: 16 warps of the kernel stay resident per SM
 template <int SPL, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) k_transport_cta(WorkDev W, OutDev O, int ng_smem) {
+__global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1)) k_transport_cta(WorkDev W, OutDev O, int ng_smem) {
     using Pool = CtaPool<SPL>;
     constexpr int kPool = Pool::kPool;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -276,19 +277,55 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_transport_cta(WorkDev W, OutD
     if (status) atomicOr(O.status, status);
 }
 
+// dynamic shared memory and resident CTAs of one instantiation
 template <int SPL, int WARPS>
-static cudaError_t launch_cta(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
-    const int ng = min(W.n_geoms, cfg.max_smem_geoms);
-    const size_t smem = (size_t)ng * sizeof(GeomDev) + sizeof(CtaPool<SPL>) * WARPS;
+static cudaError_t cta_shape(int n_geoms, const LaunchCfg &cfg, size_t *smem, int *ctas) {
+    const int ng = min(n_geoms, cfg.max_smem_geoms);
+    *smem = (size_t)ng * sizeof(GeomDev) + sizeof(CtaPool<SPL>) * WARPS;
     cudaError_t e = cudaFuncSetAttribute(k_transport_cta<SPL, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)*smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_cta<SPL, WARPS>, WARPS * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_cta<SPL, WARPS>, WARPS * 32, *smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    k_transport_cta<SPL, WARPS><<<cfg.sm_count * occ, WARPS * 32, smem, st>>>(W, O, ng);
+    *ctas = cfg.sm_count * occ;
+    return cudaSuccess;
+}
+
+template <int SPL, int WARPS>
+static cudaError_t launch_cta(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
+    size_t smem = 0;
+    int ctas = 0;
+    cudaError_t e = cta_shape<SPL, WARPS>(W.n_geoms, cfg, &smem, &ctas);
+    if (e != cudaSuccess) return e;
+    k_transport_cta<SPL, WARPS><<<ctas, WARPS * 32, smem, st>>>(W, O, min(W.n_geoms, cfg.max_smem_geoms));
     return cudaGetLastError();
+}
+
+template <int SPL, int WARPS>
+static cudaError_t warps_cta(int n_geoms, const LaunchCfg &cfg, long long *warps) {
+    size_t smem = 0;
+    int ctas = 0;
+    cudaError_t e = cta_shape<SPL, WARPS>(n_geoms, cfg, &smem, &ctas);
+    *warps = (long long)ctas * WARPS;
+    return e;
+}
+
+// resident warps of the launch that launch_transport_cta makes
+cudaError_t cta_resident_warps(int n_geoms, const LaunchCfg &cfg, long long *warps) {
+    if (cfg.pool_depth == 3) {
+        switch (cfg.block_size) {
+            case 128: return warps_cta<3, 4>(n_geoms, cfg, warps);
+            case 512: return warps_cta<3, 16>(n_geoms, cfg, warps);
+            default: return warps_cta<3, 8>(n_geoms, cfg, warps);
+        }
+    }
+    switch (cfg.block_size) {
+        case 128: return warps_cta<2, 4>(n_geoms, cfg, warps);
+        case 512: return warps_cta<2, 16>(n_geoms, cfg, warps);
+        default: return warps_cta<2, 8>(n_geoms, cfg, warps);
+    }
 }
 
 cudaError_t launch_transport_cta(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {

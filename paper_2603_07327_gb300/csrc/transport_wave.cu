@@ -275,17 +275,28 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
 }
 
 template <int SPL>
-static cudaError_t launch_wave_spl(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
-    const int ng = min(W.n_geoms, cfg.max_smem_geoms);
-    const size_t smem = (size_t)ng * sizeof(GeomDev) + sizeof(WarpPool<SPL>) * kWaveWarps;
+static cudaError_t wave_shape(int n_geoms, const LaunchCfg &cfg, size_t *smem, int *ctas) {
+    const int ng = min(n_geoms, cfg.max_smem_geoms);
+    *smem = (size_t)ng * sizeof(GeomDev) + sizeof(WarpPool<SPL>) * kWaveWarps;
     cudaError_t e = cudaFuncSetAttribute(k_transport_wave<SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)*smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_wave<SPL>, kWaveWarps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_wave<SPL>, kWaveWarps * 32, *smem);
     if (e != cudaSuccess) return e;
     const int per_sm = max(1, cfg.grid >= cfg.sm_count && cfg.grid / cfg.sm_count < occ ? cfg.grid / cfg.sm_count : occ);
-    k_transport_wave<SPL><<<cfg.sm_count * per_sm, kWaveWarps * 32, smem, st>>>(W, O, ng, max(1, cfg.compact_every));
+    *ctas = cfg.sm_count * per_sm;
+    return cudaSuccess;
+}
+
+template <int SPL>
+static cudaError_t launch_wave_spl(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
+    size_t smem = 0;
+    int ctas = 0;
+    cudaError_t e = wave_shape<SPL>(W.n_geoms, cfg, &smem, &ctas);
+    if (e != cudaSuccess) return e;
+    k_transport_wave<SPL><<<ctas, kWaveWarps * 32, smem, st>>>(W, O, min(W.n_geoms, cfg.max_smem_geoms),
+                                                              max(1, cfg.compact_every));
     return cudaGetLastError();
 }
 
@@ -295,6 +306,20 @@ cudaError_t launch_transport_wave(const WorkDev &W, const OutDev &O, const Launc
         case 4: return launch_wave_spl<4>(W, O, cfg, st);
         default: return launch_wave_spl<2>(W, O, cfg, st);
     }
+}
+
+// resident warps of the launch that launch_transport_wave makes
+cudaError_t wave_resident_warps(int n_geoms, const LaunchCfg &cfg, long long *warps) {
+    size_t smem = 0;
+    int ctas = 0;
+    cudaError_t e;
+    switch (cfg.pool_depth) {
+        case 3: e = wave_shape<3>(n_geoms, cfg, &smem, &ctas); break;
+        case 4: e = wave_shape<4>(n_geoms, cfg, &smem, &ctas); break;
+        default: e = wave_shape<2>(n_geoms, cfg, &smem, &ctas); break;
+    }
+    *warps = (long long)ctas * kWaveWarps;
+    return e;
 }
 
 }  // namespace gpet
