@@ -149,13 +149,17 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
     extern __shared__ __align__(16) uint8_t smem[];
     GeomDev *sgeom = reinterpret_cast<GeomDev *>(smem);
     Pool *pools = reinterpret_cast<Pool *>(sgeom + ng_smem);
-    // census of every warp, double-buffered by iteration parity
-    __shared__ int census[2][WARPS][kNumPh];
+    // CTA-wide phase totals, triple-buffered: iteration i adds into buffer
+    // i % 3 before its barrier and reads it after; the buffer of iteration
+    // i - 1 is cleared after the barrier of iteration i, which every read of
+    // it precedes and every add of iteration i + 2 follows.
+    __shared__ int census[3][8];
     stage_geometry(W, sgeom, ng_smem);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     Pool &P = pools[wid];
 #pragma unroll
     for (int g = 0; g < SPL; ++g) P.st[kCpack][g * 32 + lane] = 0;
+    if (threadIdx.x < 24) (&census[0][0])[threadIdx.x] = 0;
     __syncthreads();
 
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -164,15 +168,17 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
     bool exhausted = false;
     int status = kStatusOk;
     unsigned long long iters = 0, lanes_used = 0;
-    int parity = 0;
+    int buf = 0;
+    bool may_idle = true;  // slots turn idle only in the finish event (or on an error)
 
     for (;;) {
         // 1. refill the warp's idle slots
 #pragma unroll
         for (int g = 0; g < SPL; ++g) {
+            if (!may_idle || exhausted) break;
             const int q = g * 32 + lane;
             const uint32_t need = __ballot_sync(kFullMask, cphase(P, q) == kPhIdle);
-            if (need && !exhausted) {
+            if (need) {
                 bool got;
                 uint64_t h = 0;
                 int job = 0;
@@ -185,12 +191,14 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
                 }
             }
         }
+        may_idle = false;
         __syncwarp();
-        // 2. the warp's census, posted for the CTA
+        // 2. the warp's census: lane p adds the warp's count of phase p
         uint32_t ph[SPL];
 #pragma unroll
         for (int g = 0; g < SPL; ++g) ph[g] = cphase(P, g * 32 + lane);
         uint32_t mask_p[kNumPh][SPL];
+        int my_n = 0;
 #pragma unroll
         for (int p = 1; p < kNumPh; ++p) {
             int n = 0;
@@ -199,19 +207,18 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
                 mask_p[p][g] = __ballot_sync(kFullMask, ph[g] == (uint32_t)p);
                 n += __popc(mask_p[p][g]);
             }
-            if (lane == 0) census[parity][wid][p] = n;
+            if (lane == p) my_n = n;
         }
+        if (my_n) atomicAdd(&census[buf][lane], my_n);
         __syncthreads();
-        // 3. every warp computes the same CTA-wide choice
-        int best_p = 0, best_n = 0;
-#pragma unroll
-        for (int p = 1; p < kNumPh; ++p) {
-            int tot = 0;
-            for (int w = 0; w < WARPS; ++w) tot += census[parity][w][p];
-            if (tot > best_n) { best_n = tot; best_p = p; }
-        }
-        parity ^= 1;
-        if (best_n == 0) break;  // every slot of every warp idle after refills: done
+        // 3. every warp reads the same totals: the most populated phase wins
+        //    (ties to the later phase, which finishes histories sooner)
+        const uint32_t key = (lane >= 1 && lane < kNumPh) ? ((uint32_t)census[buf][lane] << 3) | (uint32_t)lane : 0u;
+        const uint32_t best = __reduce_max_sync(kFullMask, key);
+        if (threadIdx.x < 8) census[buf == 0 ? 2 : buf - 1][threadIdx.x] = 0;
+        buf = buf == 2 ? 0 : buf + 1;
+        const int best_p = (int)(best & 7u);
+        if ((best >> 3) == 0) break;  // every slot of every warp idle after refills: done
         // 4. lanes onto this warp's slots of the chosen phase
         int mine = 0;
 #pragma unroll
@@ -239,6 +246,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
             __syncwarp();
             ev_finish(W.jobs, W.geoms, O, s, active, SL, kFullMask, cnt);
             if (active) P.st[kCpack][q] = 0;
+            may_idle = true;
             __syncwarp();
             continue;
         }
@@ -260,6 +268,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
             }
             cstore(P, q, s, best_p == kPhSource);
         }
+        may_idle = may_idle || __any_sync(kFullMask, active && s.phase == kPhIdle);
         __syncwarp();
     }
     const uint32_t v[8] = {cnt.det_steps, cnt.flights, cnt.trials, cnt.entered, cnt.ph_steps, cnt.hits,
