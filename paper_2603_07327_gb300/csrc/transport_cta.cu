@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
     // i - 1 is cleared after the barrier of iteration i, which every read of
     // it precedes and every add of iteration i + 2 follows.
     __shared__ int census[3][8];
+    __shared__ uint8_t assign[WARPS][32];  // slot of each lane in the chosen phase
     stage_geometry(W, sgeom, ng_smem);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     Pool &P = pools[wid];
@@ -219,21 +220,21 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
         buf = buf == 2 ? 0 : buf + 1;
         const int best_p = (int)(best & 7u);
         if ((best >> 3) == 0) break;  // every slot of every warp idle after refills: done
-        // 4. lanes onto this warp's slots of the chosen phase
+        // 4. lanes onto this warp's slots of the chosen phase: the slot of
+        //    rank r (in slot order) goes to lane r
         int mine = 0;
 #pragma unroll
-        for (int g = 0; g < SPL; ++g) mine += __popc(mask_p[best_p][g]);
-        const bool active = lane < mine;
-        int q = 0;
-        if (active) {
-            int rank = lane;
+        for (int g = 0; g < SPL; ++g) {
+            uint32_t m = 0;
 #pragma unroll
-            for (int g = 0; g < SPL; ++g) {
-                const int c = __popc(mask_p[best_p][g]);
-                if (rank >= 0 && rank < c) q = g * 32 + (int)__fns(mask_p[best_p][g], 0, rank + 1);
-                rank -= c;
-            }
+            for (int p = 1; p < kNumPh; ++p) m = p == best_p ? mask_p[p][g] : m;
+            const int r = mine + __popc(m & lanemask_lt());
+            if (ph[g] == (uint32_t)best_p && r < 32) assign[wid][r] = (uint8_t)(g * 32 + lane);
+            mine += __popc(m);
         }
+        __syncwarp();
+        const bool active = lane < mine;
+        const int q = active ? assign[wid][lane] : 0;
         if (mine == 0) continue;  // nothing of this phase here: wait for the next choice
         ++iters;
         lanes_used += (unsigned long long)min(mine, 32);
