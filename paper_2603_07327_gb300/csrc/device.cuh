@@ -319,25 +319,56 @@ __device__ __forceinline__ float atan2_as(float y, float x) {
 
 constexpr int kFlightScreened = -2;  // flight() result: no panel, decided without slab tests
 
+// Slab-test the panels whose angular sector can meet the azimuths the ray
+// sweeps between t = ta and t = tb (a stretch inside the annulus that holds
+// all panel boxes; along a line the azimuth is monotonic and the sweep is
+// shorter than pi).  Panel k can be entered there only if its centre angle
+// k*dphi lies within beta of the swept interval; 1e-3 rad of margin covers
+// FP32 rounding.
+__device__ __forceinline__ void flight_sector(const GeomDev &g, float x, float y, float z, float dx, float dy,
+                                              float dz, float ta, float tb, int skip, int &best, float &bi,
+                                              float &bo) {
+    const float p1 = atan2_as(fmaf(ta, dy, y), fmaf(ta, dx, x)) - g.phi0;
+    float p2 = atan2_as(fmaf(tb, dy, y), fmaf(tb, dx, x)) - g.phi0;
+    // unwrap p2 next to p1
+    if (p2 - p1 > 3.14159265f) p2 -= 6.28318531f;
+    else if (p1 - p2 > 3.14159265f) p2 += 6.28318531f;
+    const float lo = fminf(p1, p2) - g.beta - 1e-3f, hi = fmaxf(p1, p2) + g.beta + 1e-3f;
+    const int jlo = (int)ceilf(lo * g.inv_dphi), jhi = (int)floorf(hi * g.inv_dphi);
+    for (int j = jlo; j <= jhi && j < jlo + g.n_panels; ++j) {
+        int k = j % g.n_panels;
+        if (k < 0) k += g.n_panels;
+        if (k == skip) continue;
+        panel_slab(g, k, x, y, z, dx, dy, dz, best, bi, bo);
+    }
+}
+
 // Line-plane flight (Sec. 2.1): nearest panel entered along (x, d), skipping
-// `skip`.  A ray that starts inside the circle of radius R (every inner face
-// is tangent to it) crosses the annulus holding all panel boxes exactly once,
-// and its azimuth is monotonic along the way; only panels whose angular
-// sector meets that azimuth interval can be entered, so only those are
-// slab-tested (same result as testing all panels).  Other rays test all.
+// `skip`.  Every panel box lies in the annulus between the circle of radius
+// R (every inner face is tangent to it) and the circle through the outer
+// corners, so only the stretches of the ray inside that annulus matter: one
+// for a ray that starts inside R, at most two (before and after it passes
+// inside R) for one that starts in or beyond the annulus.  Only panels whose
+// sector meets the azimuths of those stretches are slab-tested, which gives
+// the same result as testing all panels.
 __device__ __forceinline__ int flight(const GeomDev &g, float x, float y, float z, float dx, float dy, float dz,
                                       int skip, float &t_in, float &t_out) {
     int best = -1;
     float bi = 3.0e38f, bo = 0.0f;
     const float c0 = fmaf(x, x, y * y);
     const float a = fmaf(dx, dx, dy * dy);
-    if (c0 < g.R2 * 0.9999f && g.n_panels > 2) {
+    const float b = fmaf(x, dx, y * dy);
+    if (g.n_panels <= 2) {
+        for (int k = 0; k < g.n_panels; ++k) {
+            if (k == skip) continue;
+            panel_slab(g, k, x, y, z, dx, dy, dz, best, bi, bo);
+        }
+    } else if (c0 < g.R2 * 0.9999f) {
         if (a <= 0.0f) {
             t_in = bi;
             t_out = bo;
             return kFlightScreened;  // parallel to the axis inside the ring: never reaches a panel
         }
-        const float b = fmaf(x, dx, y * dy);
         // exit distances of the circles R and R_out (stable roots, c0 < R^2)
         const float d1 = g.R2 - c0, d2 = g.rout2 - c0;
         const float s1 = sqrtf(fmaf(b, b, a * d1)), s2 = sqrtf(fmaf(b, b, a * d2));
@@ -351,20 +382,33 @@ __device__ __forceinline__ int flight(const GeomDev &g, float x, float y, float 
             return kFlightScreened;
         }
         const float t2 = b > 0.0f ? __fdividef(d2, b + s2) : __fdividef(s2 - b, a);
-        const float p1 = atan2_as(fmaf(t1, dy, y), fmaf(t1, dx, x)) - g.phi0;
-        float p2 = atan2_as(fmaf(t2, dy, y), fmaf(t2, dx, x)) - g.phi0;
-        // unwrap p2 next to p1 (the swept interval is shorter than pi)
-        if (p2 - p1 > 3.14159265f) p2 -= 6.28318531f;
-        else if (p1 - p2 > 3.14159265f) p2 += 6.28318531f;
-        // panel k can be entered only if its centre angle k*dphi lies within beta
-        // of the swept interval; 1e-3 rad of margin covers FP32 rounding
-        const float lo = fminf(p1, p2) - g.beta - 1e-3f, hi = fmaxf(p1, p2) + g.beta + 1e-3f;
-        const int jlo = (int)ceilf(lo * g.inv_dphi), jhi = (int)floorf(hi * g.inv_dphi);
-        for (int j = jlo; j <= jhi && j < jlo + g.n_panels; ++j) {
-            int k = j % g.n_panels;
-            if (k < 0) k += g.n_panels;
-            if (k == skip) continue;
-            panel_slab(g, k, x, y, z, dx, dy, dz, best, bi, bo);
+        flight_sector(g, x, y, z, dx, dy, dz, t1, t2, skip, best, bi, bo);
+    } else if (a > 0.0f) {
+        // start in or beyond the annulus; its circles are widened by 1e-4 in
+        // r^2 so that rounding can only add candidates
+        const float ro2 = g.rout2 * 1.0001f, ri2 = g.R2 * 0.9999f;
+        const float cA = c0 - ro2;
+        const float DA = fmaf(b, b, -a * cA);
+        if (cA > 0.0f && (b >= 0.0f || DA <= 0.0f)) {
+            t_in = bi;
+            t_out = bo;
+            return kFlightScreened;  // beyond the outer circle and never coming back inside it
+        }
+        const float sA = sqrtf(fmaxf(DA, 0.0f));
+        // roots tA <= tB of the outer circle (stable forms)
+        const float tB = b > 0.0f ? __fdividef(-cA, b + sA) : __fdividef(sA - b, a);
+        const float tA = b > 0.0f ? __fdividef(-(b + sA), a) : __fdividef(cA, sA - b);
+        const float t0 = fmaxf(tA, 0.0f);
+        const float cR = c0 - ri2;
+        const float DR = fmaf(b, b, -a * cR);
+        if (b < 0.0f && DR > 0.0f) {
+            // passes inside the inner circle between tC and tD
+            const float sR = sqrtf(DR);
+            const float tC = __fdividef(cR, sR - b), tD = __fdividef(sR - b, a);
+            flight_sector(g, x, y, z, dx, dy, dz, t0, tC, skip, best, bi, bo);
+            flight_sector(g, x, y, z, dx, dy, dz, tD, tB, skip, best, bi, bo);
+        } else {
+            flight_sector(g, x, y, z, dx, dy, dz, t0, tB, skip, best, bi, bo);
         }
     } else {
         for (int k = 0; k < g.n_panels; ++k) {
