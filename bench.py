@@ -128,13 +128,18 @@ class Clocks:
 # were taken on: the entry carries their SHA-1, and `traffic` is reported as null
 # once any transport source differs.
 TRANSPORT_SOURCES = ("device.cuh", "transport.cuh", "transport.cu", "transport_cta.cu")
-TRANSPORT_TRAFFIC = None   # dict(sha1=..., bytes_per_pair=..., capture=...)
+TRANSPORT_TRAFFIC = dict(sha1="e082f2d6e76e1d65f4d82a671e1709ec0a05e751", bytes_per_pair=8.4218,
+                         capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
+# The same for the digitizer back end (make_keys .. job_stats of one step), per single.
+DIGITIZER_SOURCES = ("device.cuh", "sort.cu")
+DIGITIZER_TRAFFIC = dict(sha1="acc7df8abf6195697b232951e87d48800a455c4c", bytes_per_single=531.0,
+                         capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
 
 
-def _transport_sources_sha1():
+def _sources_sha1(names):
     import hashlib
     h = hashlib.sha1()
-    for name in TRANSPORT_SOURCES:
+    for name in names:
         with open(os.path.join(ROOT, "paper_2603_07327_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -142,9 +147,16 @@ def _transport_sources_sha1():
 
 def _transport_traffic(pairs_per_launch):
     t = TRANSPORT_TRAFFIC
-    if not t or t["sha1"] != _transport_sources_sha1():
+    if not t or t["sha1"] != _sources_sha1(TRANSPORT_SOURCES):
         return None
     return t["bytes_per_pair"] * pairs_per_launch
+
+
+def _digitizer_traffic(singles_per_step):
+    t = DIGITIZER_TRAFFIC
+    if not t or t["sha1"] != _sources_sha1(DIGITIZER_SOURCES):
+        return None
+    return t["bytes_per_single"] * singles_per_step
 
 
 def _measured_hbm_gbs():
@@ -372,8 +384,10 @@ def run_ours(args):
     dig_gbs = dig_bytes / (dg_ms / args.steps / 1000.0) / 1e9 if dg_ms > 0 else None
     hbm_peak = _measured_hbm_gbs()
     roof_dig = dict(bound="hbm", achieved=dig_gbs, peak=hbm_peak, unit="GB/s",
-                    frac=(dig_gbs / hbm_peak) if dig_gbs else None, traffic=None,
-                    bytes_per_single=398, note="time sort + coincidence sorting; peak = measured copy GB/s")
+                    frac=(dig_gbs / hbm_peak) if dig_gbs else None, traffic=_digitizer_traffic(singles_step),
+                    bytes_per_single=398,
+                    note="time sort + coincidence sorting; peak = measured copy GB/s; traffic = DRAM bytes of "
+                         "all back-end kernels of one step")
 
     # end to end through the C ABI: host descriptors in (one batch call over the
     # sweep), coincidences, singles and tallies of every job copied to host memory
