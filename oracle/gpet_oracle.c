@@ -104,6 +104,11 @@ typedef struct {
     int32_t n_materials;
     const om_material *materials;
     int32_t readout_level; /* 0 panel, 1 module, 3 crystal */
+    /* Non-repetition mode (Sec. 2.1: panels placed one by one): NULL, or 12
+     * doubles per panel -- the global unit vectors of the panel's w (depth,
+     * away from the inner face), u and v axes, then the global position of the
+     * centre of its inner face.  NULL = the repetition-mode ring above. */
+    const double *panel_poses;
 } om_scanner;
 
 typedef struct {
@@ -280,6 +285,9 @@ typedef struct {
     const om_scanner *sc;
     double U, V, W;          /* panel extents: u in [-U/2,U/2], v in [-V/2,V/2], w in [0,W] */
     double cphi[OR_MAX_PANELS], sphi[OR_MAX_PANELS];
+    int posed;                      /* 1: explicit panel poses (sc->panel_poses) */
+    double ax[OR_MAX_PANELS][3][3]; /* posed: the w, u, v axes of each panel */
+    double org[OR_MAX_PANELS][3];   /* posed: the centre of each panel's inner face */
     double layer_w0[OR_MAX_LAYERS]; /* start depth of each layer's crystals */
     int32_t layer_off[OR_MAX_LAYERS]; /* crystal-id offset of each layer inside a module */
     int32_t crystals_per_module;
@@ -315,17 +323,41 @@ static int or_geom_init(or_geom *g, const om_scanner *sc) {
         g->cphi[k] = cos(phi);
         g->sphi[k] = sin(phi);
     }
+    g->posed = sc->panel_poses != NULL;
+    if (g->posed)
+        for (int k = 0; k < sc->n_panels; ++k) {
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c) g->ax[k][a][c] = sc->panel_poses[12 * k + 3 * a + c];
+            for (int c = 0; c < 3; ++c) g->org[k][c] = sc->panel_poses[12 * k + 9 + c];
+        }
     return OR_OK;
 }
 
-/* global -> panel-local (w = depth from the inner face, u tangential, v axial) */
+static double or_dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* global -> panel-local (w = depth from the inner face, u tangential, v axial).
+ * Ring: rotation by the panel angle about z, then the radius.  Posed panel:
+ * components of x - (inner-face centre) along the panel's own axes. */
 static void or_to_local(const or_geom *g, int k, const double x[3], double *w, double *u, double *v) {
+    if (g->posed) {
+        const double p[3] = {x[0] - g->org[k][0], x[1] - g->org[k][1], x[2] - g->org[k][2]};
+        *w = or_dot3(p, g->ax[k][0]);
+        *u = or_dot3(p, g->ax[k][1]);
+        *v = or_dot3(p, g->ax[k][2]);
+        return;
+    }
     *w = x[0] * g->cphi[k] + x[1] * g->sphi[k] - g->sc->inner_radius;
     *u = -x[0] * g->sphi[k] + x[1] * g->cphi[k];
     *v = x[2];
 }
 
 static void or_dir_local(const or_geom *g, int k, const double d[3], double *dw, double *du, double *dv) {
+    if (g->posed) {
+        *dw = or_dot3(d, g->ax[k][0]);
+        *du = or_dot3(d, g->ax[k][1]);
+        *dv = or_dot3(d, g->ax[k][2]);
+        return;
+    }
     *dw = d[0] * g->cphi[k] + d[1] * g->sphi[k];
     *du = -d[0] * g->sphi[k] + d[1] * g->cphi[k];
     *dv = d[2];
@@ -641,7 +673,18 @@ static int or_transport_photon(const or_ctx *C, uint64_t h, uint32_t gamma, doub
                 double omc = xm1 / kk;
                 double c = 1.0 - omc, sn = sqrt(omc * (2.0 - omc));
                 double T = E * xm1 / (1.0 + xm1), Ep = E / (1.0 + xm1);
-                or_rotate(d, c, sn, or_uniform(r[3]));
+                if (g->posed) {
+                    /* posed panel: the polar reference of the rotation is the
+                     * panel's own v axis (for the ring, v = z and the global
+                     * rotation below is the same map) */
+                    double q[3];
+                    or_dir_local(g, k, d, &q[0], &q[1], &q[2]);
+                    or_rotate(q, c, sn, or_uniform(r[3]));
+                    for (int a = 0; a < 3; ++a)
+                        d[a] = q[0] * g->ax[k][0][a] + q[1] * g->ax[k][1][a] + q[2] * g->ax[k][2][a];
+                } else {
+                    or_rotate(d, c, sn, or_uniform(r[3]));
+                }
                 if (Ep < C->dg->e_cut) { dep = E; dead = 1; }
                 else { dep = T; E = Ep; }
             }

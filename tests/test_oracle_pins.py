@@ -359,6 +359,23 @@ def test_split_zero_gap_equals_single_layer(oracle):
     assert np.array_equal(ca, cb)
 
 
+def test_four_layer_stack_zero_gap_equals_single_layer(oracle):
+    """Four 2.5 mm layers stacked with no gaps are one 10 mm layer: same hits
+    history by history; layer l holds depths [2.5 l, 2.5 (l+1)), and each hit
+    keeps its crystal position inside its layer."""
+    one = W.scanner(8, 40.0, [W.layer(8, 8, 1.6, 0.1, 10.0)])
+    four = W.scanner(8, 40.0, [W.layer(8, 8, 1.6, 0.1, 2.5) for _ in range(4)])
+    a = oracle.simulate(one, W.point_source((-2.0, 1.0, 1.5)), W.digitizer(), 30000, seed=22, threads=4)["hits"]
+    b = oracle.simulate(four, W.point_source((-2.0, 1.0, 1.5)), W.digitizer(), 30000, seed=22, threads=4)["hits"]
+    assert len(a) == len(b) and len(a) > 1000
+    for f in ("h", "gamma", "step", "panel", "module", "w", "u", "v", "edep", "t_ps"):
+        assert np.array_equal(a[f], b[f]), f
+    assert np.array_equal(b["layer"], np.floor(b["w"] / 2.5).astype(np.int32))
+    assert set(np.unique(b["layer"])) == {0, 1, 2, 3}
+    assert np.array_equal(a["crystal"] % 64, (b["crystal"] % 256) % 64)
+    assert np.array_equal((b["crystal"] % 256) // 64, b["layer"])
+
+
 def test_blur_width_and_normals(oracle):
     """Box-Muller normals of the digitizer are N(0,1) (KS test); the photopeak
     blur has sigma = 0.15 * 511 / 2.3548."""
@@ -612,3 +629,102 @@ def test_doi_blur_of_singles(oracle):
     # no depth blur: the depth is reported as is
     r0 = oracle.simulate(sc, W.point_source((2.0, -1.0, 10.0)), W.digitizer(e_lo=0, e_hi=5000), 5000, 14, threads=4)
     assert np.array_equal(r0["singles"]["doi"], r0["singles"]["doi_blur"])
+
+
+# --------------------------------------------------------------------------
+# Non-repetition mode: panels placed one by one (Sec. 2.1)
+# --------------------------------------------------------------------------
+
+def _hits_key(h):
+    return np.lexsort((h["step"], h["gamma"], h["h"]))
+
+
+def test_ring_written_as_poses_is_the_ring(oracle):
+    """The repetition-mode ring written out as explicit poses (built from the
+    ring's definition in workloads.ring_poses) gives the same hits, crystal for
+    crystal, as the ring itself; positions and energies agree to rounding."""
+    sc = W.config3_scanner()
+    posed = W.with_poses(sc, W.ring_poses(sc))
+    src, dg = W.point_source((7.0, -4.0, 12.0)), W.digitizer()
+    a = oracle.simulate(sc, src, dg, 20_000, 31, threads=4)["hits"]
+    b = oracle.simulate(posed, src, dg, 20_000, 31, threads=4)["hits"]
+    assert len(a) == len(b) > 10_000
+    a, b = a[_hits_key(a)], b[_hits_key(b)]
+    for f in ("h", "gamma", "step", "panel", "module", "layer", "crystal", "t_ps"):
+        assert np.array_equal(a[f], b[f]), f
+    for f in ("w", "u", "v", "edep"):
+        np.testing.assert_allclose(a[f], b[f], rtol=0, atol=1e-9)
+
+
+def _triangle_solid_angle(r1, r2, r3):
+    """Solid angle of a triangle seen from the origin (Van Oosterom and
+    Strackee, IEEE Trans. Biomed. Eng. 30, 1983)."""
+    l1, l2, l3 = (np.linalg.norm(r) for r in (r1, r2, r3))
+    num = abs(np.dot(r1, np.cross(r2, r3)))
+    den = l1 * l2 * l3 + np.dot(r1, r2) * l3 + np.dot(r1, r3) * l2 + np.dot(r2, r3) * l1
+    return 2.0 * math.atan2(num, den)
+
+
+def _posed_box_solid_angle(pose_row, U, V, Wd, src):
+    """Exact solid angle of a convex panel box: the sum over the faces the
+    source sees from outside, each face split into two triangles."""
+    w, u, v, o = (np.asarray(pose_row[3 * i:3 * i + 3]) for i in range(4))
+    c = [o + a * Wd * w + b * U / 2 * u + e * V / 2 * v for a in (0, 1) for b in (-1, 1) for e in (-1, 1)]
+    c = np.array(c)  # index = 4a + 2(b>0) + (e>0)
+    faces = [((0, 2, 3, 1), -w), ((4, 5, 7, 6), w), ((0, 1, 5, 4), -u), ((2, 6, 7, 3), u),
+             ((0, 4, 6, 2), -v), ((1, 3, 7, 5), v)]
+    total = 0.0
+    for idx, nrm in faces:
+        P = c[list(idx)] - src
+        if np.dot(P[0], nrm) >= 0.0:       # the source is behind this face's plane
+            continue
+        total += _triangle_solid_angle(P[0], P[1], P[2]) + _triangle_solid_angle(P[0], P[2], P[3])
+    return total
+
+
+def test_posed_panels_acceptance_exact_solid_angle(oracle):
+    """Posed heads (tilted, turned, at different distances): the fraction of
+    isotropic rays from an off-centre point that enter each head equals that
+    box's exact solid angle / 4 pi."""
+    sc = W.box_scanner()
+    U, V, Wd = oracle.panel_extent(sc)
+    src = np.array([4.0, -3.0, 6.0])
+    rng = np.random.default_rng(17)
+    n = 2_000_000
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    pn, ti = oracle.flight(sc, np.tile(src, (n, 1)), d)
+    for k in range(sc["n_panels"]):
+        p_exp = _posed_box_solid_angle(sc["panel_poses"][k], U, V, Wd, src) / (4 * math.pi)
+        p = (pn == k).mean()
+        assert 0.01 < p_exp < 0.2
+        assert abs(p - p_exp) < 4.5 * math.sqrt(p_exp * (1 - p_exp) / n), (k, p, p_exp)
+
+
+def test_rigid_motion_of_posed_scanner_and_pencil_source(oracle):
+    """Moving every panel and a pencil source by the same rotation and
+    translation leaves each hit unchanged in its panel's own frame: crystal,
+    local position, deposit, time (transport is equivariant, and the Compton
+    rotation of a posed panel takes the panel's v axis as polar reference)."""
+    sc = W.box_scanner()
+    p0, d0 = np.array([2.0, 1.0, -3.0]), np.array([1.0, 0.08, 0.05])
+    d0 /= np.linalg.norm(d0)
+    rng = np.random.default_rng(23)
+    A = rng.normal(size=(3, 3))
+    Q, Rr = np.linalg.qr(A)
+    Q = Q * np.sign(np.diag(Rr))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] = -Q[:, 0]
+    t = np.array([13.0, -7.0, 21.0])
+    moved = W.rigid_motion(sc, Q, t)
+    dg = W.digitizer()
+    a = oracle.simulate(sc, W.pencil_source(p0, d0), dg, 20_000, 41, threads=4)["hits"]
+    b = oracle.simulate(moved, W.pencil_source(Q @ p0 + t, Q @ d0), dg, 20_000, 41, threads=4)["hits"]
+    assert len(a) == len(b) > 20_000
+    assert set(np.unique(a["panel"])) >= {0, 1}
+    a, b = a[_hits_key(a)], b[_hits_key(b)]
+    for f in ("h", "gamma", "step", "panel", "module", "layer", "crystal"):
+        assert np.array_equal(a[f], b[f]), f
+    for f in ("w", "u", "v", "edep"):
+        np.testing.assert_allclose(a[f], b[f], rtol=0, atol=1e-8)
+    assert np.abs(a["t_ps"].astype(np.int64) - b["t_ps"].astype(np.int64)).max() <= 1

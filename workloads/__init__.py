@@ -70,6 +70,90 @@ def scanner(n_panels, inner_radius, layers, modules_u=1, modules_v=1, module_gap
                 layers=list(layers), materials=list(materials), readout_level=int(readout_level))
 
 
+def ring_poses(sc):
+    """The repetition-mode ring of `sc` written out as explicit panel poses: per
+    panel the global w (normal), u (z x normal) and v (z) axes and the centre of
+    the inner face (radius R along the normal), 12 numbers."""
+    out = np.zeros((sc["n_panels"], 12))
+    for k in range(sc["n_panels"]):
+        phi = sc["first_angle"] + 2.0 * np.pi * k / sc["n_panels"]
+        w = np.array([np.cos(phi), np.sin(phi), 0.0])
+        u = np.array([-np.sin(phi), np.cos(phi), 0.0])
+        v = np.array([0.0, 0.0, 1.0])
+        out[k] = np.concatenate([w, u, v, sc["inner_radius"] * w])
+    return out
+
+
+def with_poses(sc, poses, name=None):
+    """Non-repetition mode (Sec. 2.1: panels placed one by one): the same panel
+    definition at the given poses."""
+    out = dict(sc)
+    out["panel_poses"] = np.ascontiguousarray(poses, dtype=np.float64).reshape(-1, 12)
+    out["n_panels"] = int(out["panel_poses"].shape[0])
+    if name:
+        out["name"] = name
+    return out
+
+
+def _axis_rotation(axis, ang):
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * (K @ K)
+
+
+def pose(normal, u_hint, centre):
+    """Pose of a panel whose inner face is centred at `centre` with outward
+    normal `normal`; u is `u_hint` made orthogonal to the normal, v = w x u."""
+    w = np.asarray(normal, dtype=np.float64)
+    w = w / np.linalg.norm(w)
+    u = np.asarray(u_hint, dtype=np.float64)
+    u = u - (u @ w) * w
+    u = u / np.linalg.norm(u)
+    v = np.cross(w, u)
+    return np.concatenate([w, u, v, np.asarray(centre, dtype=np.float64)])
+
+
+def four_layer_scanner(readout_level=READOUT_CRYSTAL):
+    """A four-layer stack (Sec. 2.1: the number of layers is a module parameter): 12-panel
+    ring at R = 60 mm, 1 x 2 modules; 4 mm LYSO layers of 1.0 mm pitch, the
+    second and fourth offset by half a pitch, the third at 1.25 mm pitch with
+    16 x 16 crystals, 0.05 mm reflector between layers."""
+    ls = [layer(20, 20, 1.0, 0.1, 4.0),
+          layer(20, 20, 1.0, 0.1, 4.0, gap_before=0.05, offset_u=0.5, offset_v=0.5),
+          layer(16, 16, 1.25, 0.1, 4.0, gap_before=0.05),
+          layer(20, 20, 1.0, 0.1, 4.0, gap_before=0.05, offset_u=0.5, offset_v=0.5)]
+    return scanner(12, 60.0, ls, modules_u=1, modules_v=2, readout_level=readout_level, name="ring12-4layer")
+
+
+def box_scanner(readout_level=READOUT_CRYSTAL):
+    """A non-ring design in non-repetition mode: two opposed heads at
+    different distances, a third head tilted 20 degrees out of the transaxial
+    plane, a fourth turned 15 degrees about its own normal.  Modules 1 x 2 of
+    16 x 16 LYSO crystals (1.25 mm pitch, 0.1 mm gap), two 6 mm layers, the
+    second offset by half a pitch, 0.05 mm reflector."""
+    base = scanner(4, 45.0, [layer(16, 16, 1.25, 0.1, 6.0),
+                             layer(16, 16, 1.25, 0.1, 6.0, gap_before=0.05, offset_u=0.625, offset_v=0.625)],
+                   modules_u=1, modules_v=2, readout_level=readout_level, name="box4-posed")
+    t20 = _axis_rotation((-1, 0, 0), np.radians(20.0))  # tilts the +y head out of the transaxial plane
+    r15 = _axis_rotation((-1, 0, 0), np.radians(15.0))  # turns the -x head about its normal
+    poses = [pose((1, 0, 0), (0, 1, 0), (45.0, 0.0, 0.0)),
+             pose((-1, 0, 0), r15 @ np.array([0.0, -1.0, 0.0]), (-60.0, 0.0, 0.0)),
+             pose(t20 @ np.array([0.0, 1.0, 0.0]), (1, 0, 0), (0.0, 52.0, 3.0)),
+             pose((0, -1, 0), (-1, 0, 0), (0.0, -48.0, -5.0))]
+    return with_poses(base, np.stack(poses), name="box4-posed")
+
+
+def rigid_motion(sc, Q, t):
+    """Move every panel of a posed scanner by x -> Q x + t."""
+    P = np.asarray(sc["panel_poses"], dtype=np.float64).reshape(-1, 12).copy()
+    for k in range(len(P)):
+        for a in range(3):
+            P[k, 3 * a:3 * a + 3] = Q @ P[k, 3 * a:3 * a + 3]
+        P[k, 9:12] = Q @ P[k, 9:12] + np.asarray(t, dtype=np.float64)
+    return with_poses(sc, P)
+
+
 def digitizer(fwhm_at_511=0.15, e_lo=350.0, e_hi=650.0, window_ns=2.0, e_cut=10.0, doi_fwhm_mm=0.0):
     return dict(fwhm_at_511=float(fwhm_at_511), e_lo=float(e_lo), e_hi=float(e_hi),
                 window_ns=float(window_ns), e_cut=float(e_cut), doi_fwhm_mm=float(doi_fwhm_mm))
