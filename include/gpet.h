@@ -98,7 +98,19 @@ typedef struct {
  * inner_radius_mm.  Panel-local frame: w = depth from the inner face, u =
  * tangential (z x normal), v = axial.  Modules tile the panel face
  * (modules_u x modules_v of module_size, separated by module_gap); layers
- * stack along w in order. */
+ * stack along w in order.
+ *
+ * Non-repetition mode (Sec. 2.1: panels placed one by one): panel_poses != NULL
+ * gives each of the n_panels copies of the same panel definition its own pose,
+ * 12 doubles per panel in host memory, row k at panel_poses + 12 k: the global
+ * unit vectors of the panel's w (depth, pointing away from the inner face), u
+ * and v axes, then the global position (mm) of the centre of its inner face.
+ * The axes must be orthonormal and right-handed (v = w x u) to 1e-6, and no two
+ * panel boxes may overlap (GPET_ERR_GEOMETRY otherwise).  inner_radius_mm and
+ * first_angle_rad are then ignored.  A Compton scatter inside a posed panel
+ * takes the panel's own v axis as the polar reference of its direction
+ * rotation (in the ring v = z, so both modes agree on a ring written as poses).
+ * The array is copied by gpet_create_scanner. */
 typedef struct {
     int32_t n_panels;
     double inner_radius_mm;
@@ -111,6 +123,7 @@ typedef struct {
     int32_t n_materials;
     const gpet_material *materials; /* host, n_materials entries */
     int32_t readout_level;          /* GPET_READOUT_* */
+    const double *panel_poses;      /* host, n_panels x 12, or NULL for the ring */
 } gpet_scanner_desc;
 
 typedef struct {

@@ -56,7 +56,8 @@ class ScannerDesc(C.Structure):
                 ("modules_u", C.c_int32), ("modules_v", C.c_int32), ("module_size_u", C.c_double),
                 ("module_size_v", C.c_double), ("module_gap_u", C.c_double), ("module_gap_v", C.c_double),
                 ("n_layers", C.c_int32), ("layers", C.POINTER(Layer)), ("n_materials", C.c_int32),
-                ("materials", C.POINTER(Material)), ("readout_level", C.c_int32)]
+                ("materials", C.POINTER(Material)), ("readout_level", C.c_int32),
+                ("panel_poses", C.POINTER(C.c_double))]
 
 
 class Source(C.Structure):
@@ -171,10 +172,15 @@ def scanner_desc(sc):
         layers[i] = Layer(l["n_u"], l["n_v"], l["pitch_u"], l["pitch_v"], l["gap_u"], l["gap_v"], l["depth"],
                           l["gap_before"], l["offset_u"], l["offset_v"], l["crystal_mat"], l["interval_mat"])
     mats = _materials(sc["materials"])
+    poses = sc.get("panel_poses")
+    pp = None
+    if poses is not None:
+        poses = np.ascontiguousarray(poses, dtype=np.float64).reshape(sc["n_panels"], 12)
+        pp = poses.ctypes.data_as(C.POINTER(C.c_double))
     d = ScannerDesc(sc["n_panels"], sc["inner_radius"], sc["first_angle"], sc["modules_u"], sc["modules_v"],
                     sc["module_size_u"], sc["module_size_v"], sc["module_gap_u"], sc["module_gap_v"],
-                    len(sc["layers"]), layers, len(sc["materials"]), mats, sc["readout_level"])
-    d._keep = (layers, mats)
+                    len(sc["layers"]), layers, len(sc["materials"]), mats, sc["readout_level"], pp)
+    d._keep = (layers, mats, poses)
     return d
 
 

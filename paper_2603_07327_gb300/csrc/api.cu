@@ -126,7 +126,87 @@ static bool panels_overlap(double R, double W, double half_u, double a0, double 
     return true;
 }
 
-int gpet_build_geometry(const gpet_scanner_desc *d, GeomDev &g, int64_t &n_crystals) {
+// oriented box of posed panel k: centre, axes (rows w, u, v) and half extents
+struct Obb {
+    double c[3], a[3][3], e[3];
+};
+
+static Obb posed_box(const double *P, double W, double U, double V) {
+    Obb b;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) b.a[i][j] = P[3 * i + j];
+    for (int j = 0; j < 3; ++j) b.c[j] = P[9 + j] + 0.5 * W * P[j];
+    b.e[0] = 0.5 * W; b.e[1] = 0.5 * U; b.e[2] = 0.5 * V;
+    return b;
+}
+
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// separating-axis test of two oriented boxes (face normals of both and their
+// nine cross products); touching boxes do not overlap
+static bool boxes_overlap(const Obb &A, const Obb &B) {
+    double axes[15][3];
+    int n = 0;
+    for (int i = 0; i < 3; ++i) { for (int j = 0; j < 3; ++j) axes[n][j] = A.a[i][j]; ++n; }
+    for (int i = 0; i < 3; ++i) { for (int j = 0; j < 3; ++j) axes[n][j] = B.a[i][j]; ++n; }
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) {
+            const double *p = A.a[i], *q = B.a[k];
+            double x[3] = {p[1] * q[2] - p[2] * q[1], p[2] * q[0] - p[0] * q[2], p[0] * q[1] - p[1] * q[0]};
+            const double nn = std::sqrt(dot3(x, x));
+            if (nn < 1e-9) continue;  // parallel edges: covered by the face normals
+            for (int j = 0; j < 3; ++j) axes[n][j] = x[j] / nn;
+            ++n;
+        }
+    const double scale = std::max({A.e[0], A.e[1], A.e[2], B.e[0], B.e[1], B.e[2], 1.0});
+    for (int t = 0; t < n; ++t) {
+        const double *L = axes[t];
+        double ra = 0.0, rb = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            ra += A.e[i] * std::fabs(dot3(A.a[i], L));
+            rb += B.e[i] * std::fabs(dot3(B.a[i], L));
+        }
+        const double d[3] = {B.c[0] - A.c[0], B.c[1] - A.c[1], B.c[2] - A.c[2]};
+        if (std::fabs(dot3(d, L)) >= ra + rb - 1e-9 * scale) return false;  // separated (touching allowed)
+    }
+    return true;
+}
+
+// non-repetition mode: validate the poses, reject overlapping panels and
+// build the device table (4 float4 per panel: axis + axis.origin, then origin)
+static int build_poses(const gpet_scanner_desc *d, double W, double U, double V, std::vector<float> &out) {
+    const double *P = d->panel_poses;
+    for (int k = 0; k < d->n_panels; ++k) {
+        const double *p = P + 12 * k;
+        for (int j = 0; j < 12; ++j)
+            if (!std::isfinite(p[j])) return gpet_fail(GPET_ERR_INVALID_ARG, "panel %d: pose entry %d not finite", k, j);
+        for (int i = 0; i < 3; ++i)
+            if (std::fabs(dot3(p + 3 * i, p + 3 * i) - 1.0) > 2e-6)
+                return gpet_fail(GPET_ERR_GEOMETRY, "panel %d: pose axis %d is not a unit vector", k, i);
+        if (std::fabs(dot3(p, p + 3)) > 1e-6 || std::fabs(dot3(p, p + 6)) > 1e-6 || std::fabs(dot3(p + 3, p + 6)) > 1e-6)
+            return gpet_fail(GPET_ERR_GEOMETRY, "panel %d: pose axes are not orthogonal", k);
+        const double cx[3] = {p[1] * p[5] - p[2] * p[4], p[2] * p[3] - p[0] * p[5], p[0] * p[4] - p[1] * p[3]};
+        if (dot3(cx, p + 6) < 1.0 - 1e-6)
+            return gpet_fail(GPET_ERR_GEOMETRY, "panel %d: pose axes are not right-handed (v != w x u)", k);
+    }
+    for (int a = 0; a < d->n_panels; ++a)
+        for (int b = a + 1; b < d->n_panels; ++b)
+            if (boxes_overlap(posed_box(P + 12 * a, W, U, V), posed_box(P + 12 * b, W, U, V)))
+                return gpet_fail(GPET_ERR_GEOMETRY, "posed panels %d and %d overlap", a, b);
+    out.assign((size_t)16 * d->n_panels, 0.0f);
+    for (int k = 0; k < d->n_panels; ++k) {
+        const double *p = P + 12 * k;
+        float *q = out.data() + 16 * k;
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) q[4 * i + j] = (float)p[3 * i + j];
+            q[4 * i + 3] = (float)dot3(p + 3 * i, p + 9);
+        }
+        for (int j = 0; j < 3; ++j) q[12 + j] = (float)p[9 + j];
+    }
+    return GPET_OK;
+}
+
+int gpet_build_geometry(const gpet_scanner_desc *d, GeomDev &g, int64_t &n_crystals, std::vector<float> *pose_dev) {
     if (!d) return gpet_fail(GPET_ERR_INVALID_ARG, "scanner description is NULL");
     if (d->n_panels < 1 || d->n_panels > kMaxPanels)
         return gpet_fail(GPET_ERR_INVALID_ARG, "n_panels=%d outside [1, %d]", d->n_panels, kMaxPanels);
@@ -137,7 +217,8 @@ int gpet_build_geometry(const gpet_scanner_desc *d, GeomDev &g, int64_t &n_cryst
                          kMaxMaterials);
     if (d->modules_u < 1 || d->modules_v < 1)
         return gpet_fail(GPET_ERR_INVALID_ARG, "modules %d x %d", d->modules_u, d->modules_v);
-    if (!(d->inner_radius_mm > 0.0) || !(d->module_size_u > 0.0) || !(d->module_size_v > 0.0) ||
+    const bool posed = d->panel_poses != nullptr;
+    if (!(posed || d->inner_radius_mm > 0.0) || !(d->module_size_u > 0.0) || !(d->module_size_v > 0.0) ||
         !(d->module_gap_u >= 0.0) || !(d->module_gap_v >= 0.0) || !std::isfinite(d->first_angle_rad))
         return gpet_fail(GPET_ERR_GEOMETRY, "radius, module sizes must be > 0 and module gaps >= 0");
     if (d->readout_level != 0 && d->readout_level != 1 && d->readout_level != 3)
@@ -219,6 +300,15 @@ int gpet_build_geometry(const gpet_scanner_desc *d, GeomDev &g, int64_t &n_cryst
     g.phi0 = (float)d->first_angle_rad;
     g.dphi = (float)(2.0 * M_PI / d->n_panels);
     g.inv_dphi = (float)(d->n_panels / (2.0 * M_PI));
+    if (posed) {
+        std::vector<float> tab;
+        const int st = build_poses(d, w, U, V, tab);
+        if (st != GPET_OK) return st;
+        g.posed = 1;
+        g.pose = nullptr;  // device copy placed by the run that uses it
+        if (pose_dev) *pose_dev = std::move(tab);
+        return GPET_OK;
+    }
     std::vector<double> ang(d->n_panels);
     for (int k = 0; k < d->n_panels; ++k) {
         ang[k] = d->first_angle_rad + 2.0 * M_PI * k / d->n_panels;
@@ -233,11 +323,18 @@ int gpet_build_geometry(const gpet_scanner_desc *d, GeomDev &g, int64_t &n_cryst
     return GPET_OK;
 }
 
+std::string gpet_geometry_key(const gpet_scanner *sc) {
+    std::string key(reinterpret_cast<const char *>(&sc->g), sizeof(GeomDev));
+    key.append(reinterpret_cast<const char *>(sc->pose_dev.data()), sizeof(float) * sc->pose_dev.size());
+    return key;
+}
+
 extern "C" int gpet_create_scanner(const gpet_scanner_desc *desc, gpet_scanner **out) {
     if (!out) return gpet_fail(GPET_ERR_INVALID_ARG, "out is NULL");
     GeomDev g;
     int64_t nc = 0;
-    int st = gpet_build_geometry(desc, g, nc);
+    std::vector<float> pose_dev;
+    int st = gpet_build_geometry(desc, g, nc, &pose_dev);
     if (st != GPET_OK) return st;
     gpet_scanner *sc = new (std::nothrow) gpet_scanner();
     if (!sc) return gpet_fail(GPET_ERR_OOM, "host allocation of the scanner failed");
@@ -246,6 +343,11 @@ extern "C" int gpet_create_scanner(const gpet_scanner_desc *desc, gpet_scanner *
     sc->materials.assign(desc->materials, desc->materials + desc->n_materials);
     sc->desc.layers = sc->layers.data();
     sc->desc.materials = sc->materials.data();
+    if (desc->panel_poses) {
+        sc->poses.assign(desc->panel_poses, desc->panel_poses + 12 * (size_t)desc->n_panels);
+        sc->desc.panel_poses = sc->poses.data();
+        sc->pose_dev = std::move(pose_dev);
+    }
     sc->g = g;
     sc->n_crystals = nc;
     *out = sc;
@@ -292,15 +394,29 @@ extern "C" int gpet_load_phantom(gpet_scanner *sc, int32_t nx, int32_t ny, int32
         if (material_ids[i] >= n_materials)
             return gpet_fail(GPET_ERR_INVALID_ARG, "voxel %lld has material %d >= %d", (long long)i, material_ids[i],
                              n_materials);
-    // the grid must stay inside the ring (photons never re-enter it after a panel)
+    // the grid must stay clear of the panels (photons never re-enter it after a panel)
     const double xs[2] = {origin_mm[0], origin_mm[0] + nx * voxel_mm[0]};
     const double ys[2] = {origin_mm[1], origin_mm[1] + ny * voxel_mm[1]};
-    double rmax = 0.0;
-    for (double x : xs)
-        for (double y : ys) rmax = std::max(rmax, std::sqrt(x * x + y * y));
-    if (rmax > sc->desc.inner_radius_mm)
-        return gpet_fail(GPET_ERR_GEOMETRY, "phantom reaches radius %.3f mm > ring radius %.3f mm", rmax,
-                         sc->desc.inner_radius_mm);
+    if (sc->desc.panel_poses) {
+        Obb box;
+        const double ext[3] = {nx * voxel_mm[0], ny * voxel_mm[1], nz * voxel_mm[2]};
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) box.a[i][j] = i == j ? 1.0 : 0.0;
+            box.c[i] = origin_mm[i] + 0.5 * ext[i];
+            box.e[i] = 0.5 * ext[i];
+        }
+        const double Wd = sc->g.W, U = 2.0 * sc->g.half_u, V = 2.0 * sc->g.half_v;
+        for (int k = 0; k < sc->desc.n_panels; ++k)
+            if (boxes_overlap(box, posed_box(sc->poses.data() + 12 * k, Wd, U, V)))
+                return gpet_fail(GPET_ERR_GEOMETRY, "phantom grid overlaps posed panel %d", k);
+    } else {
+        double rmax = 0.0;
+        for (double x : xs)
+            for (double y : ys) rmax = std::max(rmax, std::sqrt(x * x + y * y));
+        if (rmax > sc->desc.inner_radius_mm)
+            return gpet_fail(GPET_ERR_GEOMETRY, "phantom reaches radius %.3f mm > ring radius %.3f mm", rmax,
+                             sc->desc.inner_radius_mm);
+    }
     std::vector<double> cdf;
     double total = 0.0;
     int64_t last = -1;

@@ -32,11 +32,12 @@ int gpet_batch_build_run(Run &R, int32_t n_jobs, gpet_scanner *const *scanners, 
         JobDev J;
         st = gpet_make_job(scanners[j], &sources[j], &digitizers[j], n_decays[j], seeds[j], J);
         if (st != GPET_OK) return gpet_fail(st, "job %d: %s", j, gpet_last_error());
-        const std::string key(reinterpret_cast<const char *>(&scanners[j]->g), sizeof(GeomDev));
+        const std::string key = gpet_geometry_key(scanners[j]);
         auto it = geom_index.find(key);
         if (it == geom_index.end()) {
             it = geom_index.emplace(key, (int)R.geoms.size()).first;
             R.geoms.push_back(scanners[j]->g);
+            R.geom_pose.push_back(scanners[j]->pose_dev);
         }
         J.geom = it->second;
         R.jobs.push_back(J);

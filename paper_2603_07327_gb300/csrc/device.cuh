@@ -66,8 +66,14 @@ struct GeomDev {
     // ring culling: every panel box lies in the annulus R^2 <= r^2 <= rout2 and
     // inside its angular sector |phi - phi_k| <= beta (phi_k = phi0 + k dphi)
     float R2, rout2, beta, phi0, dphi, inv_dphi;
+    // non-repetition mode (posed = 1): per panel 4 float4 in global memory --
+    // (w axis, w.o), (u axis, u.o), (v axis, v.o), (o, 0) with o the centre of
+    // the inner face; the ring fields above are then unused
+    const float4 *pose;
+    int32_t posed, pose_pad;
     LayerDev layers[kMaxLayers];
 };
+static_assert(sizeof(GeomDev) % 16 == 0, "GeomDev is copied in words and staged in shared memory");
 
 // one simulation job: a scanner design (index into the geometry table), a
 // source and its digitizer settings
@@ -299,6 +305,46 @@ __device__ __forceinline__ void panel_slab(const GeomDev &g, int k, float x, flo
     }
 }
 
+// slab test of the ray against posed panel k (non-repetition mode): the
+// same box test in the panel's own (w, u, v) frame, read from its pose
+__device__ __forceinline__ void panel_slab_posed(const GeomDev &g, int k, float x, float y, float z, float dx,
+                                                 float dy, float dz, int &best, float &bi, float &bo) {
+    const float4 aw = __ldg(g.pose + 4 * k), au = __ldg(g.pose + 4 * k + 1), av = __ldg(g.pose + 4 * k + 2);
+    const float w0 = fmaf(x, aw.x, fmaf(y, aw.y, fmaf(z, aw.z, -aw.w)));
+    const float dw = fmaf(dx, aw.x, fmaf(dy, aw.y, dz * aw.z));
+    if (w0 < 0.0f && dw <= 0.0f) return;  // behind the inner face and moving away
+    const float u0 = fmaf(x, au.x, fmaf(y, au.y, fmaf(z, au.z, -au.w)));
+    const float du = fmaf(dx, au.x, fmaf(dy, au.y, dz * au.z));
+    const float v0 = fmaf(x, av.x, fmaf(y, av.y, fmaf(z, av.z, -av.w)));
+    const float dv = fmaf(dx, av.x, fmaf(dy, av.y, dz * av.z));
+    float tmin = -3.0e38f, tmax = 3.0e38f;
+    bool miss = false;
+    if (dw != 0.0f) {
+        const float i = 1.0f / dw;
+        const float t1 = -w0 * i, t2 = (g.W - w0) * i;
+        tmin = fmaxf(tmin, fminf(t1, t2));
+        tmax = fminf(tmax, fmaxf(t1, t2));
+    } else if (w0 < 0.0f || w0 > g.W) miss = true;
+    if (du != 0.0f) {
+        const float i = 1.0f / du;
+        const float t1 = (-g.half_u - u0) * i, t2 = (g.half_u - u0) * i;
+        tmin = fmaxf(tmin, fminf(t1, t2));
+        tmax = fminf(tmax, fmaxf(t1, t2));
+    } else if (u0 < -g.half_u || u0 > g.half_u) miss = true;
+    if (dv != 0.0f) {
+        const float i = 1.0f / dv;
+        const float t1 = (-g.half_v - v0) * i, t2 = (g.half_v - v0) * i;
+        tmin = fmaxf(tmin, fminf(t1, t2));
+        tmax = fminf(tmax, fmaxf(t1, t2));
+    } else if (v0 < -g.half_v || v0 > g.half_v) miss = true;
+    tmin = fmaxf(tmin, 0.0f);
+    if (!miss && tmin < tmax && (tmin < bi || (tmin == bi && k < best))) {
+        best = k;
+        bi = tmin;
+        bo = tmax;
+    }
+}
+
 // atan2 from the odd polynomial of Abramowitz & Stegun 4.4.47 (|error| <= 1e-5
 // rad on [-1, 1]) with octant reduction; used only to pick candidate panels,
 // where a 1e-3 rad margin absorbs its error
@@ -358,7 +404,13 @@ __device__ __forceinline__ int flight(const GeomDev &g, float x, float y, float 
     const float c0 = fmaf(x, x, y * y);
     const float a = fmaf(dx, dx, dy * dy);
     const float b = fmaf(x, dx, y * dy);
-    if (g.n_panels <= 2) {
+    if (g.posed) {
+        // panels placed one by one: no ring symmetry to cull with
+        for (int k = 0; k < g.n_panels; ++k) {
+            if (k == skip) continue;
+            panel_slab_posed(g, k, x, y, z, dx, dy, dz, best, bi, bo);
+        }
+    } else if (g.n_panels <= 2) {
         for (int k = 0; k < g.n_panels; ++k) {
             if (k == skip) continue;
             panel_slab(g, k, x, y, z, dx, dy, dz, best, bi, bo);

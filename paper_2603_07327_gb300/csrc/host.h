@@ -16,6 +16,8 @@ struct gpet_scanner {
     std::vector<gpet_layer> layers;
     std::vector<gpet_material> materials;
     gpet::GeomDev g;
+    std::vector<double> poses;   // non-repetition mode: n_panels x 12 (copy of desc.panel_poses)
+    std::vector<float> pose_dev; // its device form: n_panels x 16 (see GeomDev::pose)
     int64_t n_crystals = 0;
     // phantom
     bool has_phantom = false;
@@ -36,7 +38,10 @@ int gpet_fail(int code, const char *fmt, ...);
 bool gpet_tuned_options(const gpet_scanner *sc, int sms, gpet_options *out);
 int gpet_cuda_fail(cudaError_t e, const char *where);
 int gpet_xs_table(const float **out, float *ln_emin, float *inv_h);
-int gpet_build_geometry(const gpet_scanner_desc *d, gpet::GeomDev &g, int64_t &n_crystals);
+int gpet_build_geometry(const gpet_scanner_desc *d, gpet::GeomDev &g, int64_t &n_crystals,
+                        std::vector<float> *pose_dev = nullptr);
+// bytes that identify a scanner's geometry (descriptor and panel poses), for deduplication
+std::string gpet_geometry_key(const gpet_scanner *sc);
 int gpet_make_job(const gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg, uint64_t n_decays,
                   uint64_t seed, gpet::JobDev &J, uint64_t h_begin = 0, uint64_t h_end = 0);
 
@@ -63,6 +68,7 @@ struct Run {
     cudaStream_t stream = nullptr;
     std::vector<JobDev> jobs;            // host copies (tally pointers filled by plan)
     std::vector<GeomDev> geoms;
+    std::vector<std::vector<float>> geom_pose;  // per geometry: posed-panel table (empty for the ring)
     std::vector<int64_t> tally_off;      // per job, in crystals
     std::vector<int64_t> job_crystals;
     std::vector<uint64_t> windows;       // coincidence window per job (ps)

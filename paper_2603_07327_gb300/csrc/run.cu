@@ -136,6 +136,15 @@ int run_plan(Run &R) {
     unsigned long long *d_cs;
     cv.take(d_jobs, nj);
     cv.take(d_geoms, R.geoms.size());
+    // posed-panel tables of the geometries in non-repetition mode
+    std::vector<size_t> pose_off(R.geoms.size(), 0);
+    size_t pose_floats = 0;
+    for (size_t i = 0; i < R.geoms.size(); ++i) {
+        pose_off[i] = pose_floats;
+        if (i < R.geom_pose.size()) pose_floats += R.geom_pose[i].size();
+    }
+    float *d_pose = nullptr;
+    if (pose_floats) cv.take(d_pose, pose_floats);
     cv.take(d_cs, nj + 1);
     cv.take(R.d_window, nj);
     // raw singles
@@ -183,6 +192,10 @@ int run_plan(Run &R) {
     rebase(R.d_tally_count, base);
     rebase(R.d_tally_efx, base);
     rebase(d_jobs, base); rebase(d_geoms, base); rebase(d_cs, base); rebase(R.d_window, base);
+    if (pose_floats) rebase(d_pose, base);
+    for (size_t i = 0; i < R.geoms.size(); ++i)
+        R.geoms[i].pose = (i < R.geom_pose.size() && !R.geom_pose[i].empty())
+                              ? reinterpret_cast<const float4 *>(d_pose + pose_off[i]) : nullptr;
     rebase(O.s_raw, base);
     if (hcap) {
         rebase(O.hit_h, base); rebase(O.hit_t, base); rebase(O.hit_gstep, base); rebase(O.hit_crystal, base);
@@ -241,6 +254,10 @@ int run_plan(Run &R) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_geoms, R.geoms.data(), sizeof(GeomDev) * R.geoms.size(), cudaMemcpyHostToDevice,
                             R.stream);
+    for (size_t i = 0; i < R.geoms.size() && e == cudaSuccess; ++i)
+        if (i < R.geom_pose.size() && !R.geom_pose[i].empty())
+            e = cudaMemcpyAsync(d_pose + pose_off[i], R.geom_pose[i].data(), sizeof(float) * R.geom_pose[i].size(),
+                                cudaMemcpyHostToDevice, R.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_cs, R.chunk_start.data(), sizeof(unsigned long long) * (nj + 1),
                             cudaMemcpyHostToDevice, R.stream);
@@ -250,7 +267,8 @@ int run_plan(Run &R) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_toff, toff.data(), sizeof(long long) * nj, cudaMemcpyHostToDevice, R.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_tn, tn.data(), sizeof(long long) * nj, cudaMemcpyHostToDevice, R.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(R.stream);  // host vectors may change after return
-    R.h2d_bytes = sizeof(JobDev) * nj + sizeof(GeomDev) * R.geoms.size() + sizeof(unsigned long long) * (nj + 1) +
+    R.h2d_bytes = sizeof(JobDev) * nj + sizeof(GeomDev) * R.geoms.size() + sizeof(float) * pose_floats +
+                  sizeof(unsigned long long) * (nj + 1) +
                   sizeof(uint64_t) * nj + 2 * sizeof(long long) * nj;
     if (e != cudaSuccess) return gpet_cuda_fail(e, "upload of the job descriptors");
     return GPET_OK;
@@ -339,7 +357,7 @@ size_t run_footprint(uint64_t total_decays, int64_t total_crystals, int n_jobs, 
     const uint64_t tiles = (cap + 4095) / 4096;
     size_t b = 0;
     b += sizeof(RunHeader) + 8 * 256 * 4 + 16 * (size_t)total_crystals;
-    b += sizeof(JobDev) * n_jobs + sizeof(GeomDev) * n_geoms + 8 * (n_jobs + 1) + 8 * n_jobs;
+    b += sizeof(JobDev) * n_jobs + (sizeof(GeomDev) + 16 * 4 * kMaxPanels) * n_geoms + 8 * (n_jobs + 1) + 8 * n_jobs;
     b += cap * sizeof(RawSingle);                // raw singles
     b += hcap * (8 + 8 + 4 * 4 + 12 + 4);        // hits
     b += ocap * 12;                              // overflow list
@@ -411,6 +429,7 @@ extern "C" int gpet_simulate(gpet_scanner *sc, const gpet_source *src, const gpe
     if (st != GPET_OK) { delete res; return st; }
     R.jobs = {J};
     R.geoms = {sc->g};
+    R.geom_pose = {sc->pose_dev};
     R.job_crystals = {sc->n_crystals};
     R.windows = {(uint64_t)std::llround(dg->coinc_window_ns * 1000.0)};
     R.caps.singles = std::max<uint64_t>(65536, J.n_hist * 6 / 10);

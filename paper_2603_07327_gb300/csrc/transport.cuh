@@ -91,6 +91,18 @@ struct Counters {
 };
 
 __device__ __forceinline__ void to_global(const GeomDev &g, PState &s) {
+    if (g.posed) {
+        const float4 aw = __ldg(g.pose + 4 * s.panel), au = __ldg(g.pose + 4 * s.panel + 1);
+        const float4 av = __ldg(g.pose + 4 * s.panel + 2), o = __ldg(g.pose + 4 * s.panel + 3);
+        const float w = s.x, u = s.y, v = s.z, dw = s.dx, du = s.dy, dv = s.dz;
+        s.x = fmaf(w, aw.x, fmaf(u, au.x, fmaf(v, av.x, o.x)));
+        s.y = fmaf(w, aw.y, fmaf(u, au.y, fmaf(v, av.y, o.y)));
+        s.z = fmaf(w, aw.z, fmaf(u, au.z, fmaf(v, av.z, o.z)));
+        s.dx = fmaf(dw, aw.x, fmaf(du, au.x, dv * av.x));
+        s.dy = fmaf(dw, aw.y, fmaf(du, au.y, dv * av.y));
+        s.dz = fmaf(dw, aw.z, fmaf(du, au.z, dv * av.z));
+        return;
+    }
     const float c = g.pc[s.panel], sn = g.ps[s.panel];
     const float rw = g.R + s.x;
     const float gx = rw * c - s.y * sn, gy = rw * sn + s.y * c;
@@ -238,12 +250,23 @@ __device__ __forceinline__ void ev_flight(const JobDev &J, const GeomDev &g, PSt
     // entry point, then the panel-local frame (w, u, v)
     const float ex = fmaf(t_in, s.dx, s.x), ey = fmaf(t_in, s.dy, s.y), ez = fmaf(t_in, s.dz, s.z);
     s.path += t_in;
-    const float c = g.pc[k], sn = g.ps[k];
-    const float w = fmaf(ex, c, ey * sn) - g.R;
-    const float u = fmaf(-ex, sn, ey * c);
-    const float dw = fmaf(s.dx, c, s.dy * sn), du = fmaf(-s.dx, sn, s.dy * c);
-    s.x = w; s.y = u; s.z = ez;
-    s.dx = dw; s.dy = du;
+    if (g.posed) {
+        const float4 aw = __ldg(g.pose + 4 * k), au = __ldg(g.pose + 4 * k + 1), av = __ldg(g.pose + 4 * k + 2);
+        const float dw = fmaf(s.dx, aw.x, fmaf(s.dy, aw.y, s.dz * aw.z));
+        const float du = fmaf(s.dx, au.x, fmaf(s.dy, au.y, s.dz * au.z));
+        const float dv = fmaf(s.dx, av.x, fmaf(s.dy, av.y, s.dz * av.z));
+        s.x = fmaf(ex, aw.x, fmaf(ey, aw.y, fmaf(ez, aw.z, -aw.w)));
+        s.y = fmaf(ex, au.x, fmaf(ey, au.y, fmaf(ez, au.z, -au.w)));
+        s.z = fmaf(ex, av.x, fmaf(ey, av.y, fmaf(ez, av.z, -av.w)));
+        s.dx = dw; s.dy = du; s.dz = dv;
+    } else {
+        const float c = g.pc[k], sn = g.ps[k];
+        const float w = fmaf(ex, c, ey * sn) - g.R;
+        const float u = fmaf(-ex, sn, ey * c);
+        const float dw = fmaf(s.dx, c, s.dy * sn), du = fmaf(-s.dx, sn, s.dy * c);
+        s.x = w; s.y = u; s.z = ez;
+        s.dx = dw; s.dy = du;
+    }
     s.trem = t_out - t_in;
     s.panel = k;
     s.phase = kPhPanel;
@@ -343,7 +366,9 @@ __device__ __forceinline__ int ev_panel(const JobDev &J, const GeomDev &g, const
         if (nt < 0) return kStatusTimeout;
         cnt.trials += (uint32_t)nt;
         const float omc = xm1 / (s.E * kInvMec2);
-        // the panel frame (w, u, v) is a rotation of (x, y, z) about the axis
+        // rotation in the panel frame with v as polar reference: for the ring
+        // (w, u, v) is a rotation of (x, y, z) about the axis, so this equals the
+        // global rotation; a posed panel takes its own v axis
         rotate_dir(s.dx, s.dy, s.dz, omc, u01(r.w));
         const float Ep = s.E / (1.0f + xm1);
         if (Ep < J.e_cut) {

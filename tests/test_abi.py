@@ -71,6 +71,62 @@ def test_scanner_validation(G, oracle):
     assert "readout_level" in G.load().gpet_last_error().decode()
 
 
+def test_posed_scanner_validation(G):
+    """Non-repetition mode: valid poses are accepted; overlapping panels,
+    non-unit, non-orthogonal or left-handed axes are GPET_ERR_GEOMETRY; a
+    ring written as poses is rejected by the 3-D box test exactly where the
+    ring's own transaxial test rejects it."""
+    import numpy as np
+    assert _create(G, W.box_scanner()) == 0
+    assert _create(G, W.four_layer_scanner()) == 0
+    ring = W.config2_scanner("B")
+    assert _create(G, W.with_poses(ring, W.ring_poses(ring))) == 0
+    box = W.box_scanner()
+    P = np.array(box["panel_poses"])
+    moved = P.copy()
+    moved[0, 9:12] = [5.0, 45.0, 0.0]         # head 0 pushed into head 2
+    assert _create(G, W.with_poses(box, moved)) == -2
+    assert "overlap" in G.load().gpet_last_error().decode()
+    scaled = P.copy()
+    scaled[1, 0:3] *= 1.01                    # w axis not a unit vector
+    assert _create(G, W.with_poses(box, scaled)) == -2
+    left = P.copy()
+    left[2, 3:6] *= -1.0                      # u flipped: v != w x u
+    assert _create(G, W.with_poses(box, left)) == -2
+    skew = P.copy()
+    skew[3, 6:9] = skew[3, 3:6]               # v equal to u
+    assert _create(G, W.with_poses(box, skew)) == -2
+    nan = P.copy()
+    nan[0, 10] = float("nan")
+    assert _create(G, W.with_poses(box, nan)) == -1
+    # rings too tight for the panel width: both tests reject, looser ones accept
+    for R, want in ((18.0, -2), (19.0, -2), (40.0, 0), (55.0, 0)):
+        r = W.config2_scanner("A")
+        r["inner_radius"] = R
+        assert _create(G, r) == want, R
+        assert _create(G, W.with_poses(r, W.ring_poses(r))) == want, R
+
+
+def test_phantom_must_clear_posed_panels(G):
+    """A phantom grid that reaches into a posed panel is GPET_ERR_GEOMETRY
+    (checked before any device work, so this runs without a GPU)."""
+    import ctypes as C
+    import numpy as np
+    L = G.load()
+    h = C.c_void_p()
+    assert L.gpet_create_scanner(C.byref(G.scanner_desc(W.box_scanner())), C.byref(h)) == 0
+    try:
+        mats = G._materials([W.WATER])
+        ids = np.zeros(8, dtype=np.uint8)
+        vox = (C.c_double * 3)(30.0, 30.0, 30.0)
+        org = (C.c_double * 3)(-10.0, -10.0, -10.0)   # reaches x = 50: the +x head starts at 45
+        code = L.gpet_load_phantom(h, 2, 2, 2, vox, org, ids.ctypes.data_as(C.POINTER(C.c_uint8)), None, 1, mats)
+        assert code == -2
+        assert "posed panel 0" in L.gpet_last_error().decode()
+    finally:
+        L.gpet_destroy_scanner(h)
+
+
 def test_crystal_count_matches_oracle(G, oracle):
     for sc in (W.config1_scanner(), W.config2_scanner("B"), W.config3_scanner(), W.h2rspet("2CL")):
         h = C.c_void_p()
