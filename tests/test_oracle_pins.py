@@ -728,3 +728,85 @@ def test_rigid_motion_of_posed_scanner_and_pencil_source(oracle):
     for f in ("w", "u", "v", "edep"):
         np.testing.assert_allclose(a[f], b[f], rtol=0, atol=1e-8)
     assert np.abs(a["t_ps"].astype(np.int64) - b["t_ps"].astype(np.int64)).max() <= 1
+
+
+# ---------------------------------------------------------------------------
+# sensitivity map S(r, E) and the symmetric percent difference (Sec. 2.4)
+# ---------------------------------------------------------------------------
+def _pair_acceptance_on_axis(n_panels, R, U, V, z, n=400_000):
+    """Fraction of isotropic back-to-back pairs from (0, 0, z) whose two photons
+    both cross a panel's inner face, by midpoint quadrature over the azimuth.
+    For an even ring a transaxial direction phi meets panel k's face iff
+    |R tan(phi - phi_k)| <= U/2, and then so does phi + pi (the opposite panel),
+    at the same distance rho = R / cos(phi - phi_k).  Both photons stay inside
+    the axial extent iff |rho cot(theta)| <= V/2 - |z|, which for cos(theta)
+    uniform on [-1, 1] has probability a / sqrt(1 + a^2), a = (V/2 - |z|) / rho."""
+    phi = (np.arange(n) + 0.5) * (2 * math.pi / n)
+    dphi = 2 * math.pi / n_panels
+    rel = (phi + 0.5 * dphi) % dphi - 0.5 * dphi      # angle to the nearest panel normal
+    hit = np.abs(R * np.tan(rel)) <= 0.5 * U
+    rho = R / np.cos(rel)
+    a = max(0.5 * V - abs(z), 0.0) / rho
+    return float(np.mean(np.where(hit, a / np.sqrt(1 + a * a), 0.0)))
+
+
+def test_sensitivity_equals_pair_acceptance_of_an_opaque_ring(oracle):
+    """Opaque photoelectric crystals without gaps, no energy blur: every photon
+    that crosses an inner face deposits 511 keV in one crystal, so S in any
+    window holding 511 keV is the pair acceptance (quadrature above), a window
+    above 511 keV counts nothing, and windows holding 511 keV agree exactly."""
+    sc = W.opaque_ring()
+    sc["materials"][1] = dict(sc["materials"][1], mu_total_511_cm=1000.0)
+    dg = W.digitizer(fwhm_at_511=0.0, window_ns=2.0)
+    zs = [0.0, 25.0, 38.0]
+    n = 100_000
+    counts, S = oracle.sensitivity_map([sc], [(0.0, 0.0, z) for z in zs], dg,
+                                       [(150.0, 700.0), (450.0, 700.0), (600.0, 700.0)], n, 17, threads=8,
+                                       activity_bq=100.0)
+    for p, z in enumerate(zs):
+        expect = _pair_acceptance_on_axis(12, 55.0, 20.0, 80.0, z)
+        assert abs(S[0, p, 0] - expect) < 4.5 * math.sqrt(expect * (1 - expect) / n), (z, S[0, p, 0], expect)
+        assert counts[0, p, 1] == counts[0, p, 0]
+        assert counts[0, p, 2] == 0
+    assert _pair_acceptance_on_axis(12, 55.0, 20.0, 80.0, 0.0) == pytest.approx(0.4024, abs=5e-3)
+
+
+def test_sensitivity_window_changes_only_the_digitizer(oracle):
+    """Draws are addressed by history, photon and step, and the energy window
+    acts on singles only: the coincidences of a run with window E equal those
+    of the widest-window run with its singles cut to E afterwards."""
+    sc = W.h2rspet("2CL", modules_v=2)
+    dg = W.sensitivity_digitizer()
+    pos = (20.0, 0.0, 10.0)
+    counts, _ = oracle.sensitivity_map([sc], [pos], dg, W.SENS_WINDOWS_KEV, 30_000, 5, threads=8)
+    r = oracle.simulate(sc, W.point_source(pos), dict(dg, e_lo=150.0, e_hi=700.0), 30_000, 5, threads=8,
+                        tallies=False)
+    s = r["singles"]
+    for w, (lo, hi) in enumerate(W.SENS_WINDOWS_KEV):
+        cut = s[(s["e_blur"] >= lo) & (s["e_blur"] <= hi)]
+        cut = cut[np.argsort(cut["t_ps"], kind="stable")]
+        _, a, _ = oracle.coincidences(np.array(cut), dg["window_ns"])
+        assert counts[0, 0, w] == len(a), w
+
+
+def test_delta_sym_properties_and_the_paper_relation(oracle):
+    """Delta_sym = 200 (S_a - S_b) / (S_a + S_b): antisymmetric, zero for equal
+    sensitivities, bounded by +-200 (reached when one is zero), scale-free, and
+    to first order 100 ln(S_a / S_b); NaN where both are zero.  The paper
+    reports the single layer above the offset dual layer by about 2-5 % (Sec.
+    3.3); the oracle's H2RSPET-1CL vs -2CL at three positions and four windows
+    agrees in sign and size."""
+    a = np.array([0.1, 0.2, 0.0, 0.3, 0.05])
+    b = np.array([0.1, 0.1, 0.2, 0.0, 0.0501])
+    d = oracle.delta_sym(a, b)
+    np.testing.assert_allclose(oracle.delta_sym(b, a), -d)
+    assert d[0] == 0.0 and d[2] == -200.0 and d[3] == 200.0
+    np.testing.assert_allclose(oracle.delta_sym(7 * a, 7 * b), d)
+    assert d[4] == pytest.approx(100 * math.log(0.05 / 0.0501), rel=1e-5)
+    assert np.isnan(oracle.delta_sym(0.0, 0.0))
+    scs = [W.h2rspet("1CL", modules_v=2), W.h2rspet("2CL", modules_v=2)]
+    _, S = oracle.sensitivity_map(scs, [(0.0, 0.0, 0.0), (30.0, 0.0, 0.0), (0.0, 0.0, 40.0)],
+                                  W.sensitivity_digitizer(), W.SENS_WINDOWS_KEV, 200_000, 11, threads=8)
+    ds = oracle.delta_sym(S[0], S[1])
+    assert np.all(ds > 0.0) and np.all(ds < 8.0), ds
+    assert 1.5 < ds.mean() < 5.5, ds

@@ -367,3 +367,31 @@ def h2rspet(kind="1CL", modules_v=6):
         raise ValueError(kind)
     return scanner(10, 85.0, layers, modules_u=1, modules_v=modules_v, module_gap_v=7.0,
                    module_size_u=51 * p, module_size_v=51 * p, name=f"H2RSPET-{kind}")
+
+
+# Sec. 2.4 sensitivity study: radial offsets 0..70 mm (5 mm steps), axial offsets
+# 0..170 mm (10 mm steps), four energy windows with a 700 keV upper edge
+SENS_WINDOWS_KEV = ((150.0, 700.0), (250.0, 700.0), (350.0, 700.0), (450.0, 700.0))
+
+
+def sensitivity_positions(radial=tuple(range(0, 75, 5)), axial=tuple(range(0, 180, 10))):
+    """Source positions of the sensitivity study: every radial offset along +x in
+    the central slice, then every axial offset on the axis (the two profiles)."""
+    pos = [(float(r), 0.0, 0.0) for r in radial]
+    pos += [(0.0, 0.0, float(z)) for z in axial if z != 0]
+    return pos
+
+
+def sensitivity_digitizer():
+    """Sec. 2.4 digitizer: 16 % energy resolution, 3 ns coincidence window."""
+    return digitizer(fwhm_at_511=0.16, e_lo=150.0, e_hi=700.0, window_ns=3.0)
+
+
+def opaque_ring(n_panels=12, radius=55.0):
+    """Ring for the pair-acceptance pin: 1 x 4 modules of 20 x 20 crystals at 1.0
+    mm pitch with no crystal or module gaps, 10 mm deep, of a photoelectric-only
+    material with mu = 100 / cm (every photon entering a panel is absorbed in a
+    crystal within ~0.1 mm, depositing 511 keV)."""
+    opaque = dict(name="opaque", mu_total_511_cm=100.0, photo_frac_511=1.0, electron_density_cm3=0.0)
+    return scanner(n_panels, radius, [layer(20, 20, 1.0, 0.0, 10.0)], modules_u=1, modules_v=4,
+                   materials=[AIR, opaque], name="opaque-ring")
