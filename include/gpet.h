@@ -289,6 +289,46 @@ int gpet_simulate_batch(int32_t n_jobs, gpet_scanner *const *scanners, const gpe
                         const gpet_options *opt, gpet_result **outs);
 
 /* ------------------------------------------------------------------------ */
+/* sensitivity map (Sec. 2.4)                                                */
+/* ------------------------------------------------------------------------ */
+
+#define GPET_MAX_WINDOWS 16
+
+/* NEMA NU4-style sensitivity S(r, E) (Sec. 2.4: sensitivity as a function of
+ * source position and energy window): the coincidences a point source at r
+ * gives in energy window E, per decay.  One batched launch runs every
+ * (scanner, position) pair as a job: job j = s * n_positions + p is an
+ * isotropic point source at positions_mm[3p .. 3p + 2] (mm) with n_decays
+ * decays at activity_bq, under Philox key seed + p -- the same decays for
+ * every scanner, so designs are compared on common random numbers.  The
+ * digitizer's blur, coincidence window, cutoff and DOI blur apply; its
+ * e_lo_kev / e_hi_kev are ignored.  Transport and singles run once with the
+ * union of the energy windows, and one pass over the time-sorted singles
+ * counts, for every window, the coincidences that a run with that window alone
+ * counts (dropping singles outside a window can split a cluster of singles
+ * close in time, never join two).
+ *   scanners     host, n_scanners handles (>= 1)
+ *   positions_mm host, n_positions x 3 doubles (>= 1 position)
+ *   windows_kev  host, n_windows x (lo, hi) doubles, 0 <= lo <= hi, inclusive;
+ *                1 <= n_windows <= GPET_MAX_WINDOWS
+ *   counts       host, n_scanners x n_positions x n_windows uint64 (row-major):
+ *                coincidences
+ *   sens         host, the same shape in double: counts / n_decays, or NULL
+ *   total        host or NULL: counts of the whole launch (event counters,
+ *                stage times; singles and coincidences of the union window)
+ * n_scanners x n_positions <= 4095 jobs.  Returns GPET_ERR_INVALID_ARG for bad
+ * sizes or windows; other codes as gpet_simulate. */
+int gpet_sensitivity_map(int32_t n_scanners, gpet_scanner *const *scanners, int32_t n_positions,
+                         const double *positions_mm, double activity_bq, const gpet_digitizer *digitizer,
+                         int32_t n_windows, const double *windows_kev, uint64_t n_decays, uint64_t seed,
+                         const gpet_options *opt, uint64_t *counts, double *sens, gpet_counts *total);
+
+/* Symmetric percent difference of two sensitivities (Sec. 2.4):
+ * out[i] = 200 (s_a[i] - s_b[i]) / (s_a[i] + s_b[i]), NaN where both are zero.
+ * Host arrays of n doubles (out may alias either input). */
+int gpet_delta_sym(int64_t n, const double *s_a, const double *s_b, double *out);
+
+/* ------------------------------------------------------------------------ */
 /* time sort that allocates no device memory                                 */
 /* ------------------------------------------------------------------------ */
 

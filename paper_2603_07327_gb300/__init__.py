@@ -130,6 +130,10 @@ SIGNATURES = {
     "gpet_server_stats_get": (C.c_int, [_P, C.POINTER(ServerStats)]),
     "gpet_server_destroy": (None, [_P]),
     "gpet_sort_times_noalloc": (C.c_int, [_P, C.c_uint64, _P, _P, _P]),
+    "gpet_sensitivity_map": (C.c_int, [C.c_int32, C.POINTER(_P), C.c_int32, C.POINTER(C.c_double), C.c_double,
+                                       C.POINTER(Digitizer), C.c_int32, C.POINTER(C.c_double), C.c_uint64,
+                                       C.c_uint64, C.POINTER(Options), _P, _P, C.POINTER(Counts)]),
+    "gpet_delta_sym": (C.c_int, [C.c_int64, _P, _P, _P]),
     "gpet_last_error": (C.c_char_p, []),
     "gpet_version": (C.c_char_p, []),
 }
@@ -383,6 +387,39 @@ def simulate_batch(jobs, **opts):
     o = options_struct(**opts)
     _check(L.gpet_simulate_batch(n, scs, srcs, dgs, nd, sd, C.byref(o), outs))
     return [Result(C.c_void_p(outs[i])) for i in range(n)]
+
+
+def sensitivity_map(scanners, positions, digitizer: dict, windows, n_decays: int, seed: int,
+                    activity_bq: float = 1.7e4, **opts):
+    """gpet_sensitivity_map: `scanners` are Scanner handles, `positions` an
+    (n, 3) array in mm, `windows` (lo, hi) keV pairs.  Returns (counts, S,
+    totals): counts and S of shape [scanner][position][window], totals the
+    launch-wide gpet_counts as a dict."""
+    L = load()
+    pos = np.ascontiguousarray(positions, dtype=np.float64).reshape(-1, 3)
+    win = np.ascontiguousarray(windows, dtype=np.float64).reshape(-1, 2)
+    ns, npos, nw = len(scanners), len(pos), len(win)
+    scs = (C.c_void_p * ns)(*[sc._h.value for sc in scanners])
+    counts = np.zeros((ns, npos, nw), dtype=np.uint64)
+    sens = np.zeros((ns, npos, nw), dtype=np.float64)
+    tot = Counts()
+    o = options_struct(**opts)
+    _check(L.gpet_sensitivity_map(ns, scs, npos, pos.ctypes.data_as(C.POINTER(C.c_double)), float(activity_bq),
+                                  C.byref(digitizer_struct(digitizer)), nw,
+                                  win.ctypes.data_as(C.POINTER(C.c_double)), int(n_decays), int(seed), C.byref(o),
+                                  counts.ctypes.data, sens.ctypes.data, C.byref(tot)))
+    return counts, sens, {k: getattr(tot, k) for k, _ in Counts._fields_}
+
+
+def delta_sym(s_a, s_b):
+    """gpet_delta_sym over two arrays of the same shape."""
+    a = np.ascontiguousarray(s_a, dtype=np.float64)
+    b = np.ascontiguousarray(s_b, dtype=np.float64)
+    if a.shape != b.shape:
+        raise ValueError("delta_sym needs arrays of one shape")
+    out = np.empty_like(a)
+    _check(load().gpet_delta_sym(a.size, a.ctypes.data, b.ctypes.data, out.ctypes.data))
+    return out
 
 
 class Server:

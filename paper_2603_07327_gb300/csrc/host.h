@@ -97,6 +97,10 @@ struct Run {
     // per-job segments of the outputs (device, then host copies after collect)
     JobStatsDev JS{};
     std::vector<unsigned long long> s_off, c_off, job_hits;
+    // energy windows counted in one pass over the sorted singles (sensitivity map)
+    std::vector<float> win_lo, win_hi;
+    unsigned long long *d_win_counts = nullptr;  // [job][window], cleared before every launch
+    std::vector<unsigned long long> win_counts;
     bool own_stream = false;
     std::function<void()> on_release;    // called once when the run's memory is gone
     ~Run();
@@ -131,6 +135,10 @@ struct gpet_batch {
     std::vector<int64_t> n_crystals;
     ~gpet_batch();
 };
+
+int gpet_batch_build_run(gpet::Run &R, int32_t n_jobs, gpet_scanner *const *scanners, const gpet_source *sources,
+                         const gpet_digitizer *digitizers, const uint64_t *n_decays, const uint64_t *seeds,
+                         const gpet_options *opt);
 
 namespace gpet {
 void fill_counts(const Run &R, int job, uint64_t n_decays, int64_t n_crystals, gpet_counts *c);

@@ -69,4 +69,14 @@ cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const Coi
                               cudaStream_t st);
 cudaError_t launch_radix_passes(const SortDev &S, int sm_count, cudaStream_t st);
 
+// energy windows of one pass over the time-sorted singles
+constexpr int kMaxWindows = 16;
+struct WinDev {
+    float lo[kMaxWindows], hi[kMaxWindows];
+    int n;
+};
+// counts[job * n + w] += coincidences of window w (cap = capacity of the singles)
+cudaError_t launch_coinc_windows(const SinglesDev &s, const CoincDev &C, const WinDev &win,
+                                 unsigned long long *counts, unsigned long long cap, cudaStream_t st);
+
 }  // namespace gpet

@@ -130,6 +130,8 @@ int run_plan(Run &R) {
     cv.take(R.S.ghist, 8 * 256);
     cv.take(R.d_tally_count, (size_t)tc);
     cv.take(R.d_tally_efx, (size_t)tc);
+    const size_t nwin = R.win_lo.size();
+    if (nwin) cv.take(R.d_win_counts, (size_t)nj * nwin);
     R.zero_bytes = align_up(cv.off, 256);
     JobDev *d_jobs;
     GeomDev *d_geoms;
@@ -191,6 +193,7 @@ int run_plan(Run &R) {
     rebase(S.ghist, base);
     rebase(R.d_tally_count, base);
     rebase(R.d_tally_efx, base);
+    if (nwin) rebase(R.d_win_counts, base); else R.d_win_counts = nullptr;
     rebase(d_jobs, base); rebase(d_geoms, base); rebase(d_cs, base); rebase(R.d_window, base);
     if (pose_floats) rebase(d_pose, base);
     for (size_t i = 0; i < R.geoms.size(); ++i)
@@ -294,6 +297,12 @@ int run_enqueue(Run &R) {
     e = cudaEventRecordWithFlags(R.ev[1], R.stream, rec_flags);
     if (e == cudaSuccess) e = launch_sort_coinc(R.S, R.SD, R.C, R.cfg.sm_count, R.stream);
     if (e == cudaSuccess) e = launch_job_stats(R.SD, R.C, R.JS, R.stream);
+    if (e == cudaSuccess && R.d_win_counts) {
+        WinDev win{};
+        win.n = (int)R.win_lo.size();
+        for (int w = 0; w < win.n; ++w) { win.lo[w] = R.win_lo[w]; win.hi[w] = R.win_hi[w]; }
+        e = launch_coinc_windows(R.SD, R.C, win, R.d_win_counts, R.S.cap, R.stream);
+    }
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(R.ev[2], R.stream, rec_flags);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "sort / coincidence launch");
     return GPET_OK;
@@ -310,6 +319,11 @@ int run_collect(Run &R) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(R.c_off.data(), R.JS.c_off, 8 * (nj + 1), cudaMemcpyDeviceToHost, R.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(R.job_hits.data(), R.JS.hits, 8 * nj, cudaMemcpyDeviceToHost, R.stream);
+    if (e == cudaSuccess && R.d_win_counts) {
+        R.win_counts.resize(nj * R.win_lo.size());
+        e = cudaMemcpyAsync(R.win_counts.data(), R.d_win_counts, 8 * R.win_counts.size(), cudaMemcpyDeviceToHost,
+                            R.stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(R.stream);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "run read-back");
     if (R.ev[0] && cudaEventElapsedTime(&R.transport_ms, R.ev[0], R.ev[1]) != cudaSuccess) {

@@ -24,9 +24,6 @@
 
 using namespace gpet;
 
-int gpet_batch_build_run(Run &R, int32_t n_jobs, gpet_scanner *const *scanners, const gpet_source *sources,
-                         const gpet_digitizer *digitizers, const uint64_t *n_decays, const uint64_t *seeds,
-                         const gpet_options *opt);
 
 namespace {
 

@@ -165,3 +165,37 @@ def test_noalloc_sort_refuses_oversize_before_any_launch(G):
     assert L.gpet_sort_times_noalloc(None, (1 << 20) + 1, None, None, None) == -1
     assert "maximum" in L.gpet_last_error().decode()
     assert L.gpet_sort_times_noalloc(None, 0, None, None, None) == 0
+
+
+def test_delta_sym_host_call_matches_the_oracle(G, oracle):
+    """gpet_delta_sym is host arithmetic of the library: it agrees with the
+    oracle's own Delta_sym, NaN where both sensitivities are zero."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    a = rng.uniform(0, 0.2, 50)
+    b = rng.uniform(0, 0.2, 50)
+    a[:3] = [0.0, 0.0, 0.1]
+    b[:3] = [0.0, 0.1, 0.0]
+    got = G.delta_sym(a, b)
+    want = oracle.delta_sym(a, b)
+    assert np.isnan(got[0]) and np.isnan(want[0])
+    np.testing.assert_allclose(got[1:], want[1:], rtol=1e-15, atol=0)
+
+
+def test_sensitivity_map_refuses_bad_arguments_before_any_launch(G):
+    """Windows out of order, too many windows or jobs, and NaN positions are
+    GPET_ERR_INVALID_ARG (checked on the host, so this runs without a GPU)."""
+    import numpy as np
+    sc = G.Scanner(W.config1_scanner())
+    dg = W.digitizer()
+    try:
+        for pos, win in (([(0, 0, 0)], [(500.0, 400.0)]),
+                         ([(0, 0, 0)], [(-1.0, 400.0)]),
+                         ([(0, 0, 0)], [(100.0, 700.0)] * 17),
+                         ([(0, 0, float("nan"))], [(100.0, 700.0)]),
+                         ([(0, 0, 0)] * 4096, [(100.0, 700.0)])):
+            with pytest.raises(G.GpetError) as e:
+                G.sensitivity_map([sc], np.array(pos, dtype=float), dg, win, 100, 1)
+            assert e.value.code == -1, str(e.value)
+    finally:
+        sc.close()
