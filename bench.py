@@ -329,6 +329,7 @@ def run_sensitivity(G, args):
                 device_ms=1000 * dev_s, pairs_per_s=pairs / dev_s, e2e_ms=1000 * wall_s, e2e_pairs_per_s=pairs / wall_s,
                 plain_per_window_ms=1000 * tp, plain_per_window_pairs_per_s=pairs * len(W.SENS_WINDOWS_KEV) / tp,
                 map_over_plain_per_window=tp / wall_s, reps=args.sens_reps,
+                singles_per_pair=tot["singles"] / pairs, coincidences_union_window=tot["coincidences"],
                 delta_sym_centre=[round(float(x), 3) for x in d[0]],
                 delta_sym_mean_rich_cells=float(np.nanmean(d[rich])), rich_cells=int(rich.sum()),
                 sensitivity_centre_350_700=[float(S[0, 0, 2]), float(S[1, 0, 2])])

@@ -136,6 +136,9 @@ extern "C" int gpet_sensitivity_map(int32_t n_scanners, gpet_scanner *const *sca
     Run R;
     int st = gpet_batch_build_run(R, nj, scs.data(), srcs.data(), dgs.data(), nds.data(), seeds.data(), opt);
     if (st != GPET_OK) return st;
+    // a wide union window keeps more singles than the default guess of 0.6 per
+    // pair: size for one per pair so that the first run fits
+    R.caps.singles = std::max<uint64_t>(R.caps.singles, n_decays * (uint64_t)nj + 65536);
     for (int w = 0; w < n_windows; ++w) {
         // the same FP32 edges a run with this window alone compares against
         R.win_lo.push_back((float)windows_kev[2 * w]);

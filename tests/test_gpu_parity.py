@@ -42,6 +42,7 @@ def check_parity(G, oracle, res, orc, n, dg, min_hist_frac=0.9999):
     assert hc["frac_identical"] >= min_hist_frac, hc
     assert hc["max_rel_e"] <= PU.E_REL, hc
     assert hc["max_pos"] <= PU.POS_ABS, "worst hits: " + repr(hc["worst_pos"]) + f" p99.9={hc['p999_pos']}"
+    assert hc["max_pos_outlier"] <= PU.POS_CAP, hc["worst_pos"]
     assert hc["max_dt"] <= PU.T_ABS, hc
     bad = hc["bad"]
     gs = res.singles()
@@ -210,6 +211,7 @@ def test_full_size_sampled_histories(G, oracle):
     hc = PU.compare_hits(gsel, oh, len(sample))
     assert hc["frac_identical"] >= 1.0 - 2.0 / len(sample), hc
     assert hc["max_rel_e"] <= PU.E_REL and hc["max_pos"] <= PU.POS_ABS and hc["max_dt"] <= PU.T_ABS, hc
+    assert hc["max_pos_outlier"] <= PU.POS_CAP, hc
     tc, te = res.tallies()
     assert tc.sum() == c["hits"]
     np.testing.assert_allclose(te.sum() / 2 ** 20, gh["e"].astype(np.float64).sum(), rtol=1e-6)
