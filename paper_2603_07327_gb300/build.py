@@ -15,9 +15,11 @@ LIB = os.path.join(HERE, "libgpet.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Device division and square root to within 2 ulp instead of IEEE rounding:
 # FP32 transport against the FP64 oracle has tolerances far wider than that,
-# and the IEEE sequences cost a tenth of the transport time.
+# and the IEEE sequences cost a tenth of the transport time.  Denormals flush
+# to zero: no quantity of the path comes near 1e-38, and the special-function
+# sequences drop their denormal range handling.
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr", "-prec-div=false", "-prec-sqrt=false",
+         "--expt-relaxed-constexpr", "-prec-div=false", "-prec-sqrt=false", "-ftz=true",
          "-I", CSRC, "-I", os.path.join(ROOT, "include")]
 
 

@@ -159,33 +159,42 @@ __device__ __forceinline__ float mu_total(float c511, float pe511, const Xs &x) 
 }
 
 // ---------------------------------------------------------------------------
-// Kahn's rejection sampling of Klein-Nishina; returns trials (> 0) or -1
+// Kahn's rejection sampling of Klein-Nishina
 // ---------------------------------------------------------------------------
+// one trial from one Philox block: candidate xm1 = E/E' - 1 and its acceptance
+__device__ __forceinline__ bool kahn_try(const uint4 r, float k, float a, float b, float &xm1) {
+    const float r1 = u01(r.x), r2 = u01(r.y), r3 = u01(r.z);
+    bool accept;
+    if (r1 * b <= a) {
+        xm1 = 2.0f * k * r2;
+        const float eta = 1.0f + xm1;
+        accept = r3 * eta * eta <= 4.0f * xm1;
+    } else {
+        const float den = fmaf(2.0f * k, r2, 1.0f);
+        xm1 = 2.0f * k * (1.0f - r2) / den;
+        const float eta = 1.0f + xm1;
+        const float c = 1.0f - xm1 / k;
+        accept = 2.0f * r3 <= fmaf(c, c, 1.0f / eta);
+    }
+    return accept;
+}
+
+// Kahn's rejection sampling of Klein-Nishina; returns trials (> 0) or -1.
+// Trials are evaluated two at a time (independent Philox blocks, so the two
+// chains overlap); the first accepted one in trial order is returned.
 __device__ __forceinline__ int kahn_sample(uint64_t seed, uint64_t h, uint32_t tag, uint32_t gamma, uint32_t step,
                                            float E, float &xm1_out) {
     const float k = E * kInvMec2;
     const float a = 1.0f + 2.0f * k;
     const float b = 9.0f + 2.0f * k;
-    for (int trial = 0; trial < kMaxTrials; ++trial) {
-        const uint4 r = draw(seed, h, tag, gamma, step, 1u + (uint32_t)trial);
-        const float r1 = u01(r.x), r2 = u01(r.y), r3 = u01(r.z);
-        float xm1;
-        bool accept;
-        if (r1 * b <= a) {
-            xm1 = 2.0f * k * r2;
-            const float eta = 1.0f + xm1;
-            accept = r3 * eta * eta <= 4.0f * xm1;
-        } else {
-            const float den = fmaf(2.0f * k, r2, 1.0f);
-            xm1 = 2.0f * k * (1.0f - r2) / den;
-            const float eta = 1.0f + xm1;
-            const float c = 1.0f - xm1 / k;
-            accept = 2.0f * r3 <= fmaf(c, c, 1.0f / eta);
-        }
-        if (accept) {
-            xm1_out = xm1;
-            return trial + 1;
-        }
+    for (int trial = 0; trial < kMaxTrials; trial += 2) {
+        const uint4 ra = draw(seed, h, tag, gamma, step, 1u + (uint32_t)trial);
+        const uint4 rb = draw(seed, h, tag, gamma, step, 2u + (uint32_t)trial);
+        float xa, xb;
+        const bool acc_a = kahn_try(ra, k, a, b, xa);
+        const bool acc_b = kahn_try(rb, k, a, b, xb);
+        if (acc_a) { xm1_out = xa; return trial + 1; }
+        if (acc_b) { xm1_out = xb; return trial + 2; }
     }
     return -1;
 }
