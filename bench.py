@@ -128,11 +128,11 @@ class Clocks:
 # were taken on: the entry carries their SHA-1, and `traffic` is reported as null
 # once any transport source differs.
 TRANSPORT_SOURCES = ("device.cuh", "transport.cuh", "transport.cu", "transport_cta.cu")
-TRANSPORT_TRAFFIC = dict(sha1="e082f2d6e76e1d65f4d82a671e1709ec0a05e751", bytes_per_pair=8.4218,
+TRANSPORT_TRAFFIC = dict(sha1="3beaf4eafb368d78083e80e0f9c46891321a0d91", bytes_per_pair=8.408,
                          capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
 # The same for the digitizer back end (make_keys .. job_stats of one step), per single.
 DIGITIZER_SOURCES = ("device.cuh", "sort.cu")
-DIGITIZER_TRAFFIC = dict(sha1="acc7df8abf6195697b232951e87d48800a455c4c", bytes_per_single=531.0,
+DIGITIZER_TRAFFIC = dict(sha1="2c0cf6e39bd87f29aa4aae4dd038e6438f83e12e", bytes_per_single=527.8,
                          capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
 
 
@@ -311,13 +311,15 @@ def run_sensitivity(G, args):
         wall.append(time.perf_counter() - t0)
         dev.append((tot["transport_ms"] + tot["digitizer_ms"]) / 1000.0)
     # the naive form: one plain run per (design, position, window)
-    tp = time.perf_counter()
-    for sc in scs:
-        for p, x in enumerate(pos):
-            for lo, hi in W.SENS_WINDOWS_KEV:
-                sc.simulate(W.point_source(tuple(x)), dict(dg, e_lo=lo, e_hi=hi), n, 2603 + p,
-                            kernel=args.kernel).free()
-    tp = time.perf_counter() - tp
+    tp = float("nan")
+    if args.sens_plain:
+        tp = time.perf_counter()
+        for sc in scs:
+            for p, x in enumerate(pos):
+                for lo, hi in W.SENS_WINDOWS_KEV:
+                    sc.simulate(W.point_source(tuple(x)), dict(dg, e_lo=lo, e_hi=hi), n, 2603 + p,
+                                kernel=args.kernel).free()
+        tp = time.perf_counter() - tp
     for sc in scs:
         sc.close()
     d = G.delta_sym(S[0], S[1])
@@ -529,6 +531,8 @@ def main():
     ap.add_argument("--no-sensitivity", dest="sensitivity", action="store_false")
     ap.add_argument("--sens-pairs", type=int, default=2_000_000)
     ap.add_argument("--sens-reps", type=int, default=3)
+    ap.add_argument("--no-sens-plain", dest="sens_plain", action="store_false", default=True,
+                    help="skip the per-window plain runs that the map is compared with")
     ap.add_argument("--served-plain-sample", type=int, default=300)
     args = ap.parse_args()
     if args.impl == "reference":
