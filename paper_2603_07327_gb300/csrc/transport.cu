@@ -65,7 +65,7 @@ __device__ __forceinline__ void warp_refill(const WorkDev &W, uint32_t need, uin
             job = pool_job;
         }
         pool_next += take;
-        for (uint32_t i = 0; i < take; ++i) need &= need - 1u;  // drop the served (lowest) lanes
+        need &= ~__ballot_sync(kFullMask, ((need >> lane) & 1u) && rank < take);  // drop the served lanes
     }
 }
 

@@ -135,7 +135,7 @@ __device__ void cta_refill(const WorkDev &W, uint32_t need, uint64_t &pool_next,
             job = pool_job;
         }
         pool_next += take;
-        for (uint32_t i = 0; i < take; ++i) need &= need - 1u;
+        need &= ~__ballot_sync(kFullMask, ((need >> lane) & 1u) && rank < take);  // drop the served lanes
     }
 }
 

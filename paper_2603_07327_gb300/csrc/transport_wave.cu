@@ -140,7 +140,7 @@ __device__ void warp_refill_wave(const WorkDev &W, uint32_t need, uint64_t &pool
             job = pool_job;
         }
         pool_next += take;
-        for (uint32_t i = 0; i < take; ++i) need &= need - 1u;
+        need &= ~__ballot_sync(kFullMask, ((need >> lane) & 1u) && rank < take);  // drop the served lanes
     }
 }
 
