@@ -251,6 +251,15 @@ enum {
  * GPET_ERR_INVALID_ARG for an array the run did not keep. */
 int gpet_result_copy(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes);
 
+/* Copy one array of the whole launch that result r belongs to -- every job of
+ * its batch, in job order (for a plain run, the same as gpet_result_copy):
+ * singles of all jobs, coincidences with indices into those singles, the
+ * tallies of all jobs one after the other.  One large copy instead of one per
+ * job.  *bytes (may be NULL) receives the array's size; dst = NULL with
+ * cap_bytes = 0 only queries it.  GPET_ERR_TOO_SMALL when cap_bytes is below
+ * the size. */
+int gpet_result_copy_run(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes, size_t *bytes);
+
 /* Device pointer of one result array (valid until gpet_result_free), or NULL. */
 const void *gpet_result_device_ptr(const gpet_result *r, int32_t which);
 void gpet_result_free(gpet_result *r);

@@ -109,6 +109,7 @@ SIGNATURES = {
     "gpet_result_counts": (C.c_int, [_P, C.POINTER(Counts)]),
     "gpet_result_copy": (C.c_int, [_P, C.c_int32, _P, C.c_size_t]),
     "gpet_result_device_ptr": (_P, [_P, C.c_int32]),
+    "gpet_result_copy_run": (C.c_int, [_P, C.c_int32, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "gpet_result_free": (None, [_P]),
     "gpet_batch_create": (C.c_int, [C.c_int32, C.POINTER(_P), C.POINTER(Source), C.POINTER(Digitizer),
                                     C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(Options), C.POINTER(_P)]),
@@ -288,6 +289,38 @@ class Result:
         buf = np.zeros(n * width, dt)
         _check(load().gpet_result_copy(self._h, which, buf.ctypes.data_as(C.c_void_p), buf.nbytes))
         return buf.reshape(-1, 3) if width == 3 else buf
+
+    def nbytes(self, which: int) -> int:
+        """Bytes of one result array (for sizing caller-owned buffers)."""
+        c = self.counts()
+        if which <= SINGLES_E_RAW or which == SINGLES_DOI:
+            n = c["singles"]
+        elif which in (COINC_A, COINC_B):
+            n = c["coincidences"]
+        elif which in (TALLY_COUNT, TALLY_EFX):
+            n = c["n_crystals"]
+        else:
+            n = c["hits"]
+        return n * np.dtype(_ARRAY_DTYPE[which]).itemsize * (3 if which == HITS_WUV else 1)
+
+    def copy_into(self, which: int, ptr: int, cap_bytes: int) -> int:
+        """gpet_result_copy into caller-owned host memory at address ptr (e.g.
+        a pinned buffer); returns the bytes written."""
+        nb = self.nbytes(which)
+        _check(load().gpet_result_copy(self._h, which, C.c_void_p(ptr), int(cap_bytes)))
+        return nb
+
+    def run_nbytes(self, which: int) -> int:
+        """Bytes of one array of the whole launch this result belongs to."""
+        nb = C.c_size_t()
+        _check(load().gpet_result_copy_run(self._h, which, None, 0, C.byref(nb)))
+        return nb.value
+
+    def copy_run_into(self, which: int, ptr: int, cap_bytes: int) -> int:
+        """gpet_result_copy_run into caller-owned host memory at ptr; returns the bytes written."""
+        nb = C.c_size_t()
+        _check(load().gpet_result_copy_run(self._h, which, C.c_void_p(ptr), int(cap_bytes), C.byref(nb)))
+        return nb.value
 
     def device_ptr(self, which: int) -> int:
         return load().gpet_result_device_ptr(self._h, which) or 0

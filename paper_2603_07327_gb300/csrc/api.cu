@@ -297,7 +297,10 @@ int gpet_build_geometry(const gpet_scanner_desc *d, GeomDev &g, int64_t &n_cryst
     g.R2 = (float)(d->inner_radius_mm * d->inner_radius_mm);
     g.rout2 = (float)(rout * rout * (1.0 + 1e-6));
     g.beta = (float)std::atan2(0.5 * U, d->inner_radius_mm);
-    g.phi0 = (float)d->first_angle_rad;
+    // the culling works with the first panel's angle reduced to [0, 2 pi)
+    double phi0 = std::fmod(d->first_angle_rad, 2.0 * M_PI);
+    if (phi0 < 0.0) phi0 += 2.0 * M_PI;
+    g.phi0 = (float)phi0;
     g.dphi = (float)(2.0 * M_PI / d->n_panels);
     g.inv_dphi = (float)(d->n_panels / (2.0 * M_PI));
     if (posed) {

@@ -390,11 +390,14 @@ __device__ __forceinline__ void flight_sector(const GeomDev &g, float x, float y
     else if (p1 - p2 > 3.14159265f) p2 += 6.28318531f;
     const float lo = fminf(p1, p2) - g.beta - 1e-3f, hi = fmaxf(p1, p2) + g.beta + 1e-3f;
     const int jlo = (int)ceilf(lo * g.inv_dphi), jhi = (int)floorf(hi * g.inv_dphi);
-    for (int j = jlo; j <= jhi && j < jlo + g.n_panels; ++j) {
-        int k = j % g.n_panels;
-        if (k < 0) k += g.n_panels;
-        if (k == skip) continue;
-        panel_slab(g, k, x, y, z, dx, dy, dz, best, bi, bo);
+    // jlo mod n by a float floor: (jlo + 1/2) / n lies at least 1/(2n) from an
+    // integer, far beyond the rounding of the quotient for the |jlo| < 4n that
+    // phi0 in [0, 2 pi) allows; then step through the panels with a wrap
+    const int n = g.n_panels;
+    int k = jlo - n * (int)floorf(((float)jlo + 0.5f) * __frcp_rn((float)n));
+    for (int j = jlo; j <= jhi && j < jlo + n; ++j) {
+        if (k != skip) panel_slab(g, k, x, y, z, dx, dy, dz, best, bi, bo);
+        k = k + 1 == n ? 0 : k + 1;
     }
 }
 

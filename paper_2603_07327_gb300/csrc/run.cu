@@ -524,6 +524,42 @@ extern "C" int gpet_result_copy(const gpet_result *r, int32_t which, void *dst, 
     return GPET_OK;
 }
 
+extern "C" int gpet_result_copy_run(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes,
+                                    size_t *bytes) {
+    if (!r || (!dst && cap_bytes)) return gpet_fail(GPET_ERR_INVALID_ARG, "NULL argument");
+    const Run &R = *r->run;
+    const size_t nj = R.jobs.size();
+    if (R.s_off.size() != nj + 1 || R.c_off.size() != nj + 1)
+        return gpet_fail(GPET_ERR_INVALID_ARG, "the run has no collected results");
+    const uint64_t ns = R.s_off[nj], nc = R.c_off[nj];
+    ArrayView v;
+    switch (which) {
+        case GPET_SINGLES_T_PS: v = {R.SD.t, ns * 8}; break;
+        case GPET_SINGLES_H: v = {R.SD.h, ns * 8}; break;
+        case GPET_SINGLES_UNIT: v = {R.SD.unit, ns * 4}; break;
+        case GPET_SINGLES_PANEL: v = {R.SD.panel, ns * 4}; break;
+        case GPET_SINGLES_E: v = {R.SD.e, ns * 4}; break;
+        case GPET_SINGLES_E_RAW: v = {R.SD.eraw, ns * 4}; break;
+        case GPET_SINGLES_DOI: v = {R.SD.doi, ns * 4}; break;
+        case GPET_COINC_A: v = {R.C.a, nc * 4}; break;
+        case GPET_COINC_B: v = {R.C.b, nc * 4}; break;
+        case GPET_TALLY_COUNT: v = {R.d_tally_count, (size_t)R.total_crystals * 8}; break;
+        case GPET_TALLY_EFX: v = {R.d_tally_efx, (size_t)R.total_crystals * 8}; break;
+        default: {
+            const int st = result_array(r, which, v);  // hit lists: single-job runs only
+            if (st != GPET_OK) return st;
+        }
+    }
+    if (bytes) *bytes = v.bytes;
+    if (!dst) return GPET_OK;
+    if (cap_bytes < v.bytes)
+        return gpet_fail(GPET_ERR_TOO_SMALL, "array %d needs %zu bytes, got %zu", which, v.bytes, cap_bytes);
+    if (v.bytes == 0) return GPET_OK;
+    cudaError_t e = cudaMemcpy(dst, v.ptr, v.bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "result copy");
+    return GPET_OK;
+}
+
 extern "C" const void *gpet_result_device_ptr(const gpet_result *r, int32_t which) {
     if (!r) return nullptr;
     ArrayView v;

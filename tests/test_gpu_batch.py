@@ -105,3 +105,31 @@ def test_history_shards_merge_to_the_whole_run(G):
     order = np.lexsort((fs["h"], fs["unit"], fs["t_ps"]))
     for f in shard.SINGLE_FIELDS:
         assert np.array_equal(m[f], fs[f][order]), f
+
+
+def test_whole_launch_copy_equals_the_job_views(G):
+    """gpet_result_copy_run: one copy per array for the whole batch equals the
+    per-job views concatenated in job order; its coincidence indices count
+    from the batch's first single (the job view's plus the job's offset)."""
+    designs = W.config4(n_designs=4, scale=0.02)
+    jobs = [dict(scanner=G.Scanner(d["scanner"]), source=d["source"], digitizer=d["digitizer"],
+                 n_decays=d["n_decays"], seed=d["seed"]) for d in designs]
+    res = G.simulate_batch(jobs)
+    dtypes = {G.SINGLES_T_PS: np.uint64, G.SINGLES_UNIT: np.int32, G.SINGLES_E: np.float32,
+              G.COINC_A: np.int32, G.COINC_B: np.int32, G.TALLY_COUNT: np.uint64, G.TALLY_EFX: np.uint64}
+    s_off = np.cumsum([0] + [r.counts()["singles"] for r in res])
+    for w, dt in dtypes.items():
+        nb = res[0].run_nbytes(w)
+        buf = np.zeros(nb // np.dtype(dt).itemsize + 1, dtype=dt)
+        assert res[-1].copy_run_into(w, buf.ctypes.data, buf.nbytes) == nb
+        whole = buf[:nb // np.dtype(dt).itemsize]
+        parts = [r.array(w) for r in res]
+        if w in (G.COINC_A, G.COINC_B):
+            parts = [p + s_off[j] for j, p in enumerate(parts)]
+        np.testing.assert_array_equal(whole, np.concatenate(parts).astype(dt))
+    with pytest.raises(G.GpetError):
+        res[0].copy_run_into(G.SINGLES_T_PS, buf.ctypes.data, 1)
+    for r in res:
+        r.free()
+    for j in jobs:
+        j["scanner"].close()
