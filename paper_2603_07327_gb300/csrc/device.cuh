@@ -40,7 +40,9 @@ constexpr float kEfxScale = 1048576.0f;  // tally energy unit 2^-20 keV
 enum : uint32_t { kTagSource = 1u, kTagPhantom = 2u, kTagDetector = 3u, kTagDigi = 4u };
 
 // device status codes (host maps them to GPET_ERR_*)
-enum : int { kStatusOk = 0, kStatusTimeout = 1, kStatusOverflow = 2 };
+// kStatusBadPhase: a history in a phase no event handles (an internal error);
+// the history is dropped, so no event loop can spin on it
+enum : int { kStatusOk = 0, kStatusTimeout = 1, kStatusOverflow = 2, kStatusBadPhase = 4 };
 
 // ---------------------------------------------------------------------------
 // geometry descriptor (FP32, one per scanner design)

@@ -340,6 +340,8 @@ int run_collect(Run &R) {
     if (H.n_singles > R.O.s_cap || (R.keep_hits && H.n_hits > R.O.hit_cap) || H.n_ovf > R.O.ovf_cap)
         return gpet_fail(GPET_ERR_OVERFLOW, "output capacity exceeded (singles %llu/%llu, hits %llu/%llu, ovf %llu/%llu)",
                          H.n_singles, R.O.s_cap, H.n_hits, R.O.hit_cap, H.n_ovf, R.O.ovf_cap);
+    if (H.status & kStatusBadPhase)
+        return gpet_fail(GPET_ERR_CUDA, "internal error: a history reached a phase no event handles");
     if (H.status & kStatusOverflow)
         return gpet_fail(GPET_ERR_OVERFLOW, "a history touched more than 64 readout units");
     return GPET_OK;

@@ -112,9 +112,10 @@ __global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int
         switch (s.phase) {
             case kPhSource: ev_source(J, g, s, cnt); break;
             case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
-            case kPhFlight: ev_flight(J, g, s, cnt); break;
+            case kPhFlight: case kPhFlightOut: ev_flight(J, g, s, cnt); break;
             case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, S, cnt); break;
-            default: break;
+            case kPhIdle: case kPhFinish: break;
+            default: st = kStatusBadPhase; break;
         }
         if (st != kStatusOk) {          // iteration cap hit: abandon the history, flag the run
             status |= st;
@@ -161,9 +162,9 @@ __global__ void __launch_bounds__(128) k_transport_redo(WorkDev W, OutDev O) {
                 switch (s.phase) {
                     case kPhSource: ev_source(J, g, s, cnt); break;
                     case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
-                    case kPhFlight: ev_flight(J, g, s, cnt); break;
+                    case kPhFlight: case kPhFlightOut: ev_flight(J, g, s, cnt); break;
                     case kPhPanel: st = ev_panel<false>(J, g, W, O, s, SL, S, cnt); break;
-                    default: break;
+                    default: st = kStatusBadPhase; break;
                 }
                 if (st != kStatusOk) { status |= st; s.phase = kPhIdle; }
             }

@@ -15,8 +15,11 @@
 
 namespace gpet {
 
-// history phases
-enum : uint32_t { kPhIdle = 0, kPhSource = 1, kPhPhantom = 2, kPhFlight = 3, kPhPanel = 4, kPhFinish = 5 };
+// history phases.  A flight after a panel exit has its own phase: it starts
+// in the annulus of the panels, not inside the ring, and takes the other
+// branch of the flight code, so a wavefront of one kind does not diverge.
+enum : uint32_t { kPhIdle = 0, kPhSource = 1, kPhPhantom = 2, kPhFlight = 3, kPhPanel = 4, kPhFinish = 5,
+                  kPhFlightOut = 6 };
 
 // per-history singles list: unit ids, energy sums, earliest time offset
 // (t - t0 in ps); `stride` separates consecutive entries of one history
@@ -357,7 +360,7 @@ __device__ __forceinline__ int ev_panel(const JobDev &J, const GeomDev &g, const
         to_global(g, s);
         s.last = s.panel;
         s.panel = -1;
-        s.phase = kPhFlight;
+        s.phase = kPhFlightOut;
         return kStatusOk;
     }
     s.x = fmaf(step, s.dx, s.x); s.y = fmaf(step, s.dy, s.y); s.z = fmaf(step, s.dz, s.z);

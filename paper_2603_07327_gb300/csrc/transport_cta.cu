@@ -18,7 +18,7 @@ namespace {
 
 constexpr int kCtaS = 6;     // singles-list entries per history (overflow -> redo kernel)
 constexpr int kCtaWords = 23;
-constexpr int kNumPh = 6;    // phases 0..5
+constexpr int kNumPh = 7;    // phases 0..6
 
 enum : int {
     kCh0 = 0, kCh1, kCt0, kCt1, kCx, kCy, kCz, kCdx, kCdy, kCdz, kCx0, kCy0, kCz0, kCox, kCoy, kCoz, kCE, kCpath,
@@ -259,9 +259,9 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
             switch (best_p) {
                 case kPhSource: ev_source(J, g, s, cnt); break;
                 case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
-                case kPhFlight: ev_flight(J, g, s, cnt); break;
+                case kPhFlight: case kPhFlightOut: ev_flight(J, g, s, cnt); break;
                 case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, kCtaS, cnt); break;
-                default: break;
+                default: st = kStatusBadPhase; break;
             }
             if (st != kStatusOk) {
                 status |= st;

@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
         int best_n = 0;
         uint32_t best_p = kPhIdle;
 #pragma unroll
-        for (uint32_t p = kPhSource; p <= kPhFinish; ++p) {
+        for (uint32_t p = kPhSource; p <= kPhFlightOut; ++p) {
             uint32_t b[SPL];
             int n = 0;
 #pragma unroll
@@ -245,9 +245,9 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
                 switch (best_p) {
                     case kPhSource: ev_source(J, g, s, cnt); break;
                     case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
-                    case kPhFlight: ev_flight(J, g, s, cnt); break;
+                    case kPhFlight: case kPhFlightOut: ev_flight(J, g, s, cnt); break;
                     case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, kWaveS, cnt); break;
-                    default: break;
+                    default: st = kStatusBadPhase; break;
                 }
                 if (st != kStatusOk) {
                     status |= st;
