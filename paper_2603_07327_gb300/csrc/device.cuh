@@ -403,6 +403,32 @@ __device__ __forceinline__ void flight_sector(const GeomDev &g, float x, float y
     }
 }
 
+// Axial screen of a ray that starts inside the ring (c0 = x^2 + y^2 below
+// 0.9999 R^2): true when it runs parallel to the axis, or when it is beyond
+// the panels' axial extent (1e-3 mm margin) on reaching the circle R and moving
+// away; t1 receives the distance to that circle.
+__device__ __forceinline__ bool inside_screened(const GeomDev &g, float z, float dz, float a, float b, float c0,
+                                                float &t1) {
+    if (a <= 0.0f) return true;
+    const float d1 = g.R2 - c0;
+    const float s1 = sqrtf(fmaf(b, b, a * d1));
+    t1 = b > 0.0f ? __fdividef(d1, b + s1) : __fdividef(s1 - b, a);
+    const float z1 = fmaf(t1, dz, z);
+    return (z1 > g.half_v + 1e-3f && dz >= 0.0f) || (z1 < -g.half_v - 1e-3f && dz <= 0.0f);
+}
+
+// The screen flight() applies first to a ray from (x, d): the same test,
+// for deciding at a photon's start that its flight cannot reach a panel.
+__device__ __forceinline__ bool start_screened(const GeomDev &g, float x, float y, float z, float dx, float dy,
+                                               float dz) {
+    if (g.posed || g.n_panels <= 2) return false;
+    const float c0 = fmaf(x, x, y * y);
+    if (!(c0 < g.R2 * 0.9999f)) return false;
+    const float a = fmaf(dx, dx, dy * dy), b = fmaf(x, dx, y * dy);
+    float t1;
+    return inside_screened(g, z, dz, a, b, c0, t1);
+}
+
 // Line-plane flight (Sec. 2.1): nearest panel entered along (x, d), skipping
 // `skip`.  Every panel box lies in the annulus between the circle of radius
 // R (every inner face is tangent to it) and the circle through the outer
@@ -430,23 +456,17 @@ __device__ __forceinline__ int flight(const GeomDev &g, float x, float y, float 
             panel_slab(g, k, x, y, z, dx, dy, dz, best, bi, bo);
         }
     } else if (c0 < g.R2 * 0.9999f) {
-        if (a <= 0.0f) {
-            t_in = bi;
-            t_out = bo;
-            return kFlightScreened;  // parallel to the axis inside the ring: never reaches a panel
-        }
-        // exit distances of the circles R and R_out (stable roots, c0 < R^2)
-        const float d1 = g.R2 - c0, d2 = g.rout2 - c0;
-        const float s1 = sqrtf(fmaf(b, b, a * d1)), s2 = sqrtf(fmaf(b, b, a * d2));
-        const float t1 = b > 0.0f ? __fdividef(d1, b + s1) : __fdividef(s1 - b, a);
-        // axial early out: beyond the panels' axial extent when it reaches the
-        // annulus and moving away (1e-3 mm margin)
-        const float z1 = fmaf(t1, dz, z);
-        if ((z1 > g.half_v + 1e-3f && dz >= 0.0f) || (z1 < -g.half_v - 1e-3f && dz <= 0.0f)) {
+        // parallel to the axis, or axially beyond the panels when it reaches
+        // the annulus: screened; else t1 = exit distance of the circle R
+        float t1 = 0.0f;
+        if (inside_screened(g, z, dz, a, b, c0, t1)) {
             t_in = bi;
             t_out = bo;
             return kFlightScreened;
         }
+        // exit distance of the circle R_out (stable root, c0 < R^2)
+        const float d2 = g.rout2 - c0;
+        const float s2 = sqrtf(fmaf(b, b, a * d2));
         const float t2 = b > 0.0f ? __fdividef(d2, b + s2) : __fdividef(s2 - b, a);
         flight_sector(g, x, y, z, dx, dy, dz, t1, t2, skip, best, bi, bo);
     } else if (a > 0.0f) {

@@ -119,17 +119,30 @@ __device__ __forceinline__ bool in_phantom(const JobDev &J, float x, float y, fl
            z < J.ph_hi[2];
 }
 
+// Start photon s.gamma of the pair at the decay point.  A photon whose first
+// flight would be screened at once (flight() applies the same test first) is
+// finished here as a screened flight, without a flight event: photon 0 hands
+// over to photon 1, photon 1 ends the history.
 __device__ __forceinline__ void start_photon(const JobDev &J, const GeomDev &g, PState &s, Counters &cnt) {
-    const float sg = s.gamma == 0 ? 1.0f : -1.0f;
-    s.x = s.x0; s.y = s.y0; s.z = s.z0;
-    s.dx = sg * s.ox; s.dy = sg * s.oy; s.dz = sg * s.oz;
-    s.E = kE0;
-    s.path = 0.0f;
-    s.sph = 0; s.sdet = 0;
-    s.panel = -1; s.last = -1;
-    s.phase = (J.has_phantom && in_phantom(J, s.x, s.y, s.z)) ? kPhPhantom : kPhFlight;
-    (void)g;
-    (void)cnt;
+    for (;;) {
+        const float sg = s.gamma == 0 ? 1.0f : -1.0f;
+        s.x = s.x0; s.y = s.y0; s.z = s.z0;
+        s.dx = sg * s.ox; s.dy = sg * s.oy; s.dz = sg * s.oz;
+        s.E = kE0;
+        s.path = 0.0f;
+        s.sph = 0; s.sdet = 0;
+        s.panel = -1; s.last = -1;
+        s.phase = (J.has_phantom && in_phantom(J, s.x, s.y, s.z)) ? kPhPhantom : kPhFlight;
+        if (s.phase != kPhFlight || !start_screened(g, s.x, s.y, s.z, s.dx, s.dy, s.dz)) return;
+        cnt.flights++;
+        cnt.screened++;
+        if (s.gamma == 0) {
+            s.gamma = 1;
+            continue;
+        }
+        s.phase = (s.nsing == 0 && !s.ovf) ? kPhIdle : kPhFinish;
+        return;
+    }
 }
 
 __device__ __forceinline__ void photon_done(const JobDev &J, const GeomDev &g, PState &s, Counters &cnt) {
