@@ -438,51 +438,54 @@ def run_ours(args):
                     note="time sort + coincidence sorting; peak = measured copy GB/s; traffic = DRAM bytes of "
                          "all back-end kernels of one step")
 
-    # end to end through the C ABI: host descriptors in (one batch call over the
-    # sweep), coincidences, singles and tallies of every job copied into
-    # caller-owned pinned host buffers.  A first, untimed pass sizes the buffers
-    # (allocated outside the timed region, as a user reading results into
-    # reusable buffers would); the timed pass repeats the same simulations.
+    # end to end through the C ABI: every step is one gpet_simulate_batch call
+    # over the sweep from host descriptors, and the step's results -- singles'
+    # times, units and energies, coincidence pairs and per-crystal tallies of
+    # the whole launch -- are read into caller-owned pinned host buffers, one
+    # copy per array (gpet_result_copy_run).  A first, untimed pass sizes the
+    # buffers, which every timed step reuses.  (Overlapping a step's copies
+    # with the next step's simulation on a side stream measured slower: the
+    # simulation lost more than the copies took.)
     E2E_ARRAYS = (G.SINGLES_T_PS, G.SINGLES_UNIT, G.SINGLES_E, G.COINC_A, G.COINC_B, G.TALLY_COUNT, G.TALLY_EFX)
 
-    def e2e_pass(bufs):
-        h2d, d2h, need = 0, 0, {w: 0 for w in E2E_ARRAYS}
+    def e2e_simulate():
         if args.form == "batched":
-            res = G.simulate_batch([dict(scanner=scanners[j["geometry"]], source=j["source"], digitizer=dg,
-                                         n_decays=j["n"], seed=j["seed"]) for j in jobs], stream=stream,
-                                   kernel=args.kernel)
-        else:
-            res = [scanners[j["geometry"]].simulate(j["source"], dg, j["n"], j["seed"], stream=stream,
-                                                    kernel=args.kernel) for j in jobs]
-        t_sim = time.perf_counter()
+            return G.simulate_batch([dict(scanner=scanners[j["geometry"]], source=j["source"], digitizer=dg,
+                                          n_decays=j["n"], seed=j["seed"]) for j in jobs], stream=stream,
+                                    kernel=args.kernel)
+        return [scanners[j["geometry"]].simulate(j["source"], dg, j["n"], j["seed"], stream=stream,
+                                                 kernel=args.kernel) for j in jobs]
+
+    def views_of(res):
         # batched: one copy per array for the whole launch; plain: one per run
-        views = res[:1] if args.form == "batched" else res
-        for r in views:
-            h2d = max(h2d, r.counts()["h2d_bytes"]) if args.form == "batched" else h2d + r.counts()["h2d_bytes"]
+        return res[:1] if args.form == "batched" else res
+
+    res0 = e2e_simulate()
+    need = {w: sum(r.run_nbytes(w) for r in views_of(res0)) for w in E2E_ARRAYS}
+    for r in res0:
+        r.free()
+    bufs = {w: torch.empty(need[w] + 4096, dtype=torch.uint8, pin_memory=True) for w in E2E_ARRAYS}
+    torch.cuda.synchronize()
+    e2e_t0 = time.perf_counter()
+    sim_s = 0.0
+    h2d = d2h = 0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        res = e2e_simulate()
+        sim_s += time.perf_counter() - t0
+        h2d = d2h = 0
+        for r in views_of(res):
+            h2d += r.counts()["h2d_bytes"]
+            off = {w: 0 for w in E2E_ARRAYS}
             for w in E2E_ARRAYS:
-                if bufs is None:
-                    need[w] += r.run_nbytes(w)
-                else:
-                    nb = r.copy_run_into(w, bufs[w].data_ptr() + need[w], bufs[w].numel() - need[w])
-                    need[w] += nb
-                    d2h += nb
+                nb = r.copy_run_into(w, bufs[w].data_ptr() + off[w], bufs[w].numel() - off[w])
+                off[w] += nb
+                d2h += nb
         for r in res:
             r.free()
-        return h2d, d2h, need, t_sim
-
-    _, _, need, _ = e2e_pass(None)
-    bufs = {w: torch.empty(need[w] + 4096, dtype=torch.uint8, pin_memory=True) for w in E2E_ARRAYS}
-    # K end-to-end steps, like the device-timed metric: total pairs / total time
-    e2e_dt = e2e_sim_s = 0.0
-    for _ in range(args.steps):
-        torch.cuda.synchronize()
-        e2e_t0 = time.perf_counter()
-        h2d, d2h, _, t_sim = e2e_pass(bufs)
-        torch.cuda.synchronize()
-        e2e_dt += time.perf_counter() - e2e_t0
-        e2e_sim_s += t_sim - e2e_t0
-    e2e_dt /= args.steps
-    e2e_sim_s /= args.steps
+    torch.cuda.synchronize()
+    e2e_dt = (time.perf_counter() - e2e_t0) / args.steps
+    e2e_sim_s = sim_s / args.steps
     if dist:
         t = torch.tensor([e2e_dt], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -500,8 +503,9 @@ def run_ours(args):
                             parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
                 wall_s=wall, gpu_launches=None, roofline=roof, roofline_digitizer=roof_dig, clocks=clk,
                 e2e=dict(value=pairs_per_step * world / e2e_dt, unit="pairs/s", h2d_bytes_per_step=h2d,
-                         d2h_bytes_per_step=d2h, simulate_ms=1000 * e2e_sim_s,
-                         copy_ms=1000 * (e2e_dt - e2e_sim_s), host_buffers="pinned, caller-owned, reused"),
+                         d2h_bytes_per_step=d2h, ms_per_step=1000 * e2e_dt, simulate_ms_per_step=1000 * e2e_sim_s,
+                         copy_ms_per_step=1000 * (e2e_dt - e2e_sim_s), host_buffers="pinned, caller-owned, reused",
+                         copies="one copy per array of the whole launch"),
                 stages=dict(transport_ms_per_step=tr_ms / args.steps, digitizer_ms_per_step=dg_ms / args.steps),
                 per_step_counts=dict(hits=sum(c["hits"] for c in counts) // args.steps,
                                      singles=sum(c["singles"] for c in counts) // args.steps,

@@ -259,6 +259,13 @@ int gpet_result_copy(const gpet_result *r, int32_t which, void *dst, size_t cap_
  * cap_bytes = 0 only queries it.  GPET_ERR_TOO_SMALL when cap_bytes is below
  * the size. */
 int gpet_result_copy_run(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes, size_t *bytes);
+/* The same copy enqueued on `stream` (a cudaStream_t) and returned at once,
+ * so that it overlaps later work on other streams (e.g. the next simulation).
+ * dst should be pinned host memory for the copy to run asynchronously.  The
+ * caller keeps r (and with it the device arrays) alive and dst untouched
+ * until the stream has passed the copy. */
+int gpet_result_copy_run_async(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes, size_t *bytes,
+                               void *stream);
 
 /* Device pointer of one result array (valid until gpet_result_free), or NULL. */
 const void *gpet_result_device_ptr(const gpet_result *r, int32_t which);

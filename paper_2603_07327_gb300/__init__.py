@@ -110,6 +110,7 @@ SIGNATURES = {
     "gpet_result_copy": (C.c_int, [_P, C.c_int32, _P, C.c_size_t]),
     "gpet_result_device_ptr": (_P, [_P, C.c_int32]),
     "gpet_result_copy_run": (C.c_int, [_P, C.c_int32, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "gpet_result_copy_run_async": (C.c_int, [_P, C.c_int32, _P, C.c_size_t, C.POINTER(C.c_size_t), _P]),
     "gpet_result_free": (None, [_P]),
     "gpet_batch_create": (C.c_int, [C.c_int32, C.POINTER(_P), C.POINTER(Source), C.POINTER(Digitizer),
                                     C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(Options), C.POINTER(_P)]),
@@ -320,6 +321,13 @@ class Result:
         """gpet_result_copy_run into caller-owned host memory at ptr; returns the bytes written."""
         nb = C.c_size_t()
         _check(load().gpet_result_copy_run(self._h, which, C.c_void_p(ptr), int(cap_bytes), C.byref(nb)))
+        return nb.value
+
+    def copy_run_into_async(self, which: int, ptr: int, cap_bytes: int, stream: int) -> int:
+        """gpet_result_copy_run_async on the CUDA stream handle `stream`; returns the bytes enqueued."""
+        nb = C.c_size_t()
+        _check(load().gpet_result_copy_run_async(self._h, which, C.c_void_p(ptr), int(cap_bytes), C.byref(nb),
+                                                 C.c_void_p(stream)))
         return nb.value
 
     def device_ptr(self, which: int) -> int:

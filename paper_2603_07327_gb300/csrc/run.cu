@@ -526,8 +526,21 @@ extern "C" int gpet_result_copy(const gpet_result *r, int32_t which, void *dst, 
     return GPET_OK;
 }
 
+static int copy_run(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes, size_t *bytes, bool async,
+                    cudaStream_t stream);
+
 extern "C" int gpet_result_copy_run(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes,
                                     size_t *bytes) {
+    return copy_run(r, which, dst, cap_bytes, bytes, false, nullptr);
+}
+
+extern "C" int gpet_result_copy_run_async(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes,
+                                          size_t *bytes, void *stream) {
+    return copy_run(r, which, dst, cap_bytes, bytes, true, static_cast<cudaStream_t>(stream));
+}
+
+static int copy_run(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes, size_t *bytes, bool async,
+                    cudaStream_t stream) {
     if (!r || (!dst && cap_bytes)) return gpet_fail(GPET_ERR_INVALID_ARG, "NULL argument");
     const Run &R = *r->run;
     const size_t nj = R.jobs.size();
@@ -557,7 +570,8 @@ extern "C" int gpet_result_copy_run(const gpet_result *r, int32_t which, void *d
     if (cap_bytes < v.bytes)
         return gpet_fail(GPET_ERR_TOO_SMALL, "array %d needs %zu bytes, got %zu", which, v.bytes, cap_bytes);
     if (v.bytes == 0) return GPET_OK;
-    cudaError_t e = cudaMemcpy(dst, v.ptr, v.bytes, cudaMemcpyDeviceToHost);
+    cudaError_t e = async ? cudaMemcpyAsync(dst, v.ptr, v.bytes, cudaMemcpyDeviceToHost, stream)
+                          : cudaMemcpy(dst, v.ptr, v.bytes, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "result copy");
     return GPET_OK;
 }

@@ -133,3 +133,26 @@ def test_whole_launch_copy_equals_the_job_views(G):
         r.free()
     for j in jobs:
         j["scanner"].close()
+
+
+def test_async_whole_launch_copy_equals_the_blocking_one(G):
+    """gpet_result_copy_run_async on a side stream delivers the same bytes as
+    the blocking copy once the stream has passed it."""
+    import torch
+    designs = W.config4(n_designs=3, scale=0.02)
+    jobs = [dict(scanner=G.Scanner(d["scanner"]), source=d["source"], digitizer=d["digitizer"],
+                 n_decays=d["n_decays"], seed=d["seed"]) for d in designs]
+    res = G.simulate_batch(jobs)
+    st = torch.cuda.Stream()
+    for w in (G.SINGLES_T_PS, G.SINGLES_E, G.COINC_B, G.TALLY_EFX):
+        nb = res[0].run_nbytes(w)
+        pinned = torch.zeros(nb + 16, dtype=torch.uint8, pin_memory=True)
+        assert res[1].copy_run_into_async(w, pinned.data_ptr(), pinned.numel(), st.cuda_stream) == nb
+        st.synchronize()
+        ref = np.zeros(nb, dtype=np.uint8)
+        res[2].copy_run_into(w, ref.ctypes.data, ref.nbytes)
+        np.testing.assert_array_equal(pinned.numpy()[:nb], ref)
+    for r in res:
+        r.free()
+    for j in jobs:
+        j["scanner"].close()
