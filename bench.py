@@ -128,11 +128,11 @@ class Clocks:
 # were taken on: the entry carries their SHA-1, and `traffic` is reported as null
 # once any transport source differs.
 TRANSPORT_SOURCES = ("device.cuh", "transport.cuh", "transport.cu", "transport_cta.cu")
-TRANSPORT_TRAFFIC = dict(sha1="3beaf4eafb368d78083e80e0f9c46891321a0d91", bytes_per_pair=8.408,
+TRANSPORT_TRAFFIC = dict(sha1="988451dc1e63547dad1ea1182110a1fe44194e4b", bytes_per_pair=8.407,
                          capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
 # The same for the digitizer back end (make_keys .. job_stats of one step), per single.
 DIGITIZER_SOURCES = ("device.cuh", "sort.cu")
-DIGITIZER_TRAFFIC = dict(sha1="2c0cf6e39bd87f29aa4aae4dd038e6438f83e12e", bytes_per_single=527.8,
+DIGITIZER_TRAFFIC = dict(sha1="9862d78703d829e7fb42a8d99e50ef7a6cc25827", bytes_per_single=530.0,
                          capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
 
 
