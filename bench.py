@@ -337,6 +337,63 @@ def run_sensitivity(G, args):
                 sensitivity_centre_350_700=[float(S[0, 0, 2]), float(S[1, 0, 2])])
 
 
+def run_design_sweep(G, args):
+    """The batched design sweep: 64 candidate scanners drawn from seed 4 (1-3
+    layers, 8-20 mm total depth, 0.8-2.0 mm pitch, 40-80 mm ring radius, layer
+    offset 0 or half a pitch), each with a point source at a random radial
+    offset and a log-uniform 1e5-1e7 decays.  Batched: the launch form is
+    autotuned on a pilot of the largest design, then all 64 jobs run as one
+    graph-captured persistent launch (gpet_batch_run, host-timed including the
+    read-back of the counters).  Plain: 64 sequential gpet_simulate calls.
+    The per-job coincidence counts of the two forms must agree exactly."""
+    import torch
+    designs = W.config4()
+    scs = [G.Scanner(d["scanner"]) for d in designs]
+    pairs = sum(d["n_decays"] for d in designs)
+    big = max(range(len(designs)), key=lambda i: designs[i]["n_decays"])
+    tuned, tuned_ms = scs[big].autotune(designs[big]["source"], designs[big]["digitizer"], pilot_decays=2_000_000)
+    jobs = [dict(scanner=scs[i], source=d["source"], digitizer=d["digitizer"], n_decays=d["n_decays"],
+                 seed=d["seed"]) for i, d in enumerate(designs)]
+    b = G.Batch(jobs)
+    for _ in range(args.warmup):
+        b.run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.run()
+    batched_s = (time.perf_counter() - t0) / args.steps
+    tot = b.counts()
+    batched_coinc = []
+    for i in range(len(jobs)):
+        r = b.result(i)
+        batched_coinc.append(r.counts()["coincidences"])
+        r.free()
+
+    def plain(collect=None):
+        for d, sc in zip(designs, scs):
+            r = sc.simulate(d["source"], d["digitizer"], d["n_decays"], d["seed"])
+            if collect is not None:
+                collect.append(r.counts()["coincidences"])
+            r.free()
+
+    plain()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_coinc = []
+    plain(plain_coinc)
+    plain_s = time.perf_counter() - t0
+    b.close()
+    for sc in scs:
+        sc.close()
+    return dict(workload="64 designs drawn from seed 4 (1-3 layers, 8-20 mm, pitch 0.8-2.0 mm, R 40-80 mm), "
+                         "point sources at 0-50 mm radial offset, log-uniform 1e5-1e7 pairs each",
+                pairs=pairs, batched_ms=1000 * batched_s, batched_pairs_per_s=pairs / batched_s,
+                transport_ms=tot["transport_ms"], digitizer_ms=tot["digitizer_ms"],
+                plain_ms=1000 * plain_s, plain_pairs_per_s=pairs / plain_s, batched_over_plain=plain_s / batched_s,
+                tuned=tuned, tuned_pilot_transport_ms=tuned_ms,
+                coincidences_identical=batched_coinc == plain_coinc)
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -528,6 +585,8 @@ def run_ours(args):
         line["batched_over_plain"] = value / line["plain_pairs_per_s"]
     if rank == 0 and args.served:
         line["served"] = run_served(G, args)
+    if rank == 0 and args.design_sweep:
+        line["design_sweep"] = run_design_sweep(G, args)
     if rank == 0 and args.sensitivity:
         line["sensitivity_map"] = run_sensitivity(G, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -557,6 +616,8 @@ def main():
     ap.add_argument("--served", action="store_true", default=True)
     ap.add_argument("--no-served", dest="served", action="store_false")
     ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--design-sweep", action="store_true", default=True)
+    ap.add_argument("--no-design-sweep", dest="design_sweep", action="store_false")
     ap.add_argument("--sensitivity", action="store_true", default=True)
     ap.add_argument("--no-sensitivity", dest="sensitivity", action="store_false")
     ap.add_argument("--sens-pairs", type=int, default=2_000_000)

@@ -57,6 +57,32 @@ struct JobStatsDev {
     const long long *tally_off, *tally_n; // [n_jobs]
 };
 
+// Geometry descriptors a transport launch stages in shared memory: as many of
+// the first min(n_geoms, max_geoms) as fit without fewer resident CTAs than a
+// launch that stages none (the rest are read through L1).  Sets the kernel's
+// dynamic shared-memory limit to the chosen size.
+template <class Kernel>
+cudaError_t staged_geometry(Kernel k, int block, size_t pool_smem, int n_geoms, int max_geoms, int *ng_out,
+                            size_t *smem_out, int *occ_out) {
+    int ng = n_geoms < max_geoms ? n_geoms : max_geoms;
+    if (ng < 0) ng = 0;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(pool_smem + (size_t)ng * sizeof(GeomDev)));
+    if (e != cudaSuccess) return e;
+    int occ0 = 0, occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k, block, pool_smem);
+    if (e != cudaSuccess) return e;
+    for (;; --ng) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, pool_smem + (size_t)ng * sizeof(GeomDev));
+        if (e != cudaSuccess) return e;
+        if (occ >= occ0 || ng == 0) break;
+    }
+    *ng_out = ng;
+    *smem_out = pool_smem + (size_t)ng * sizeof(GeomDev);
+    *occ_out = occ;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem_out);
+}
+
 cudaError_t launch_job_stats(const SinglesDev &s, const CoincDev &C, const JobStatsDev &J, cudaStream_t st);
 cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
 cudaError_t launch_transport_wave(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);

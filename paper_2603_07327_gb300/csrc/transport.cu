@@ -188,17 +188,13 @@ static size_t loop_smem(int ng_smem, int block, int S) {
 }
 
 // dynamic shared memory and resident CTAs of the per-lane loop kernel
-static cudaError_t loop_shape(int n_geoms, const LaunchCfg &cfg, size_t *smem, int *ctas) {
+static cudaError_t loop_shape(int n_geoms, const LaunchCfg &cfg, size_t *smem, int *ctas, int *ng) {
     constexpr int S = 8;
-    const int ng = min(n_geoms, cfg.max_smem_geoms);
-    *smem = loop_smem(ng, cfg.block_size, S);
-    cudaError_t e = cudaFuncSetAttribute(k_transport_loop<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)*smem);
+    int occ = 0;
+    cudaError_t e = staged_geometry(k_transport_loop<S>, cfg.block_size, loop_smem(0, cfg.block_size, S), n_geoms,
+                                    cfg.max_smem_geoms, ng, smem, &occ);
     if (e != cudaSuccess) return e;
     // persistent grid: never more CTAs than can be resident at once
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_loop<S>, cfg.block_size, *smem);
-    if (e != cudaSuccess) return e;
     *ctas = cfg.sm_count * max(1, min(occ, cfg.grid / max(cfg.sm_count, 1)));
     return cudaSuccess;
 }
@@ -207,8 +203,8 @@ cudaError_t transport_resident_warps(int n_geoms, const LaunchCfg &cfg, long lon
     if (cfg.kernel == kKernelWave) return wave_resident_warps(n_geoms, cfg, warps);
     if (cfg.kernel == kKernelCta) return cta_resident_warps(n_geoms, cfg, warps);
     size_t smem = 0;
-    int ctas = 0;
-    cudaError_t e = loop_shape(n_geoms, cfg, &smem, &ctas);
+    int ctas = 0, ng = 0;
+    cudaError_t e = loop_shape(n_geoms, cfg, &smem, &ctas, &ng);
     *warps = (long long)ctas * (cfg.block_size / 32);
     return e;
 }
@@ -223,10 +219,10 @@ cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg 
         if (e != cudaSuccess) return e;
     } else {
         size_t smem = 0;
-        int ctas = 0;
-        cudaError_t e = loop_shape(W.n_geoms, cfg, &smem, &ctas);
+        int ctas = 0, ng = 0;
+        cudaError_t e = loop_shape(W.n_geoms, cfg, &smem, &ctas, &ng);
         if (e != cudaSuccess) return e;
-        k_transport_loop<S><<<ctas, cfg.block_size, smem, st>>>(W, O, min(W.n_geoms, cfg.max_smem_geoms));
+        k_transport_loop<S><<<ctas, cfg.block_size, smem, st>>>(W, O, ng);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

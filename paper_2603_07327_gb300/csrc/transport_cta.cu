@@ -289,14 +289,10 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
 
 // dynamic shared memory and resident CTAs of one instantiation
 template <int SPL, int WARPS>
-static cudaError_t cta_shape(int n_geoms, const LaunchCfg &cfg, size_t *smem, int *ctas) {
-    const int ng = min(n_geoms, cfg.max_smem_geoms);
-    *smem = (size_t)ng * sizeof(GeomDev) + sizeof(CtaPool<SPL>) * WARPS;
-    cudaError_t e = cudaFuncSetAttribute(k_transport_cta<SPL, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)*smem);
-    if (e != cudaSuccess) return e;
+static cudaError_t cta_shape(int n_geoms, const LaunchCfg &cfg, size_t *smem, int *ctas, int *ng) {
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_cta<SPL, WARPS>, WARPS * 32, *smem);
+    cudaError_t e = staged_geometry(k_transport_cta<SPL, WARPS>, WARPS * 32, sizeof(CtaPool<SPL>) * WARPS, n_geoms,
+                                    cfg.max_smem_geoms, ng, smem, &occ);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     *ctas = cfg.sm_count * occ;
@@ -306,18 +302,18 @@ static cudaError_t cta_shape(int n_geoms, const LaunchCfg &cfg, size_t *smem, in
 template <int SPL, int WARPS>
 static cudaError_t launch_cta(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
     size_t smem = 0;
-    int ctas = 0;
-    cudaError_t e = cta_shape<SPL, WARPS>(W.n_geoms, cfg, &smem, &ctas);
+    int ctas = 0, ng = 0;
+    cudaError_t e = cta_shape<SPL, WARPS>(W.n_geoms, cfg, &smem, &ctas, &ng);
     if (e != cudaSuccess) return e;
-    k_transport_cta<SPL, WARPS><<<ctas, WARPS * 32, smem, st>>>(W, O, min(W.n_geoms, cfg.max_smem_geoms));
+    k_transport_cta<SPL, WARPS><<<ctas, WARPS * 32, smem, st>>>(W, O, ng);
     return cudaGetLastError();
 }
 
 template <int SPL, int WARPS>
 static cudaError_t warps_cta(int n_geoms, const LaunchCfg &cfg, long long *warps) {
     size_t smem = 0;
-    int ctas = 0;
-    cudaError_t e = cta_shape<SPL, WARPS>(n_geoms, cfg, &smem, &ctas);
+    int ctas = 0, ng = 0;
+    cudaError_t e = cta_shape<SPL, WARPS>(n_geoms, cfg, &smem, &ctas, &ng);
     *warps = (long long)ctas * WARPS;
     return e;
 }

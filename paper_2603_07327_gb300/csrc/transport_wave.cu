@@ -275,14 +275,10 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
 }
 
 template <int SPL>
-static cudaError_t wave_shape(int n_geoms, const LaunchCfg &cfg, size_t *smem, int *ctas) {
-    const int ng = min(n_geoms, cfg.max_smem_geoms);
-    *smem = (size_t)ng * sizeof(GeomDev) + sizeof(WarpPool<SPL>) * kWaveWarps;
-    cudaError_t e = cudaFuncSetAttribute(k_transport_wave<SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)*smem);
-    if (e != cudaSuccess) return e;
+static cudaError_t wave_shape(int n_geoms, const LaunchCfg &cfg, size_t *smem, int *ctas, int *ng) {
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_wave<SPL>, kWaveWarps * 32, *smem);
+    cudaError_t e = staged_geometry(k_transport_wave<SPL>, kWaveWarps * 32, sizeof(WarpPool<SPL>) * kWaveWarps,
+                                    n_geoms, cfg.max_smem_geoms, ng, smem, &occ);
     if (e != cudaSuccess) return e;
     const int per_sm = max(1, cfg.grid >= cfg.sm_count && cfg.grid / cfg.sm_count < occ ? cfg.grid / cfg.sm_count : occ);
     *ctas = cfg.sm_count * per_sm;
@@ -292,10 +288,10 @@ static cudaError_t wave_shape(int n_geoms, const LaunchCfg &cfg, size_t *smem, i
 template <int SPL>
 static cudaError_t launch_wave_spl(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
     size_t smem = 0;
-    int ctas = 0;
-    cudaError_t e = wave_shape<SPL>(W.n_geoms, cfg, &smem, &ctas);
+    int ctas = 0, ng = 0;
+    cudaError_t e = wave_shape<SPL>(W.n_geoms, cfg, &smem, &ctas, &ng);
     if (e != cudaSuccess) return e;
-    k_transport_wave<SPL><<<ctas, kWaveWarps * 32, smem, st>>>(W, O, min(W.n_geoms, cfg.max_smem_geoms),
+    k_transport_wave<SPL><<<ctas, kWaveWarps * 32, smem, st>>>(W, O, ng,
                                                               max(1, cfg.compact_every));
     return cudaGetLastError();
 }
@@ -311,12 +307,12 @@ cudaError_t launch_transport_wave(const WorkDev &W, const OutDev &O, const Launc
 // resident warps of the launch that launch_transport_wave makes
 cudaError_t wave_resident_warps(int n_geoms, const LaunchCfg &cfg, long long *warps) {
     size_t smem = 0;
-    int ctas = 0;
+    int ctas = 0, ng = 0;
     cudaError_t e;
     switch (cfg.pool_depth) {
-        case 3: e = wave_shape<3>(n_geoms, cfg, &smem, &ctas); break;
-        case 4: e = wave_shape<4>(n_geoms, cfg, &smem, &ctas); break;
-        default: e = wave_shape<2>(n_geoms, cfg, &smem, &ctas); break;
+        case 3: e = wave_shape<3>(n_geoms, cfg, &smem, &ctas, &ng); break;
+        case 4: e = wave_shape<4>(n_geoms, cfg, &smem, &ctas, &ng); break;
+        default: e = wave_shape<2>(n_geoms, cfg, &smem, &ctas, &ng); break;
     }
     *warps = (long long)ctas * kWaveWarps;
     return e;
