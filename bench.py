@@ -128,11 +128,11 @@ class Clocks:
 # were taken on: the entry carries their SHA-1, and `traffic` is reported as null
 # once any transport source differs.
 TRANSPORT_SOURCES = ("device.cuh", "transport.cuh", "transport.cu", "transport_cta.cu")
-TRANSPORT_TRAFFIC = dict(sha1="988451dc1e63547dad1ea1182110a1fe44194e4b", bytes_per_pair=8.407,
+TRANSPORT_TRAFFIC = dict(sha1="c42443e218da70df0188d3d5b2bc5ba802fbd458", bytes_per_pair=8.403,
                          capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
 # The same for the digitizer back end (make_keys .. job_stats of one step), per single.
 DIGITIZER_SOURCES = ("device.cuh", "sort.cu")
-DIGITIZER_TRAFFIC = dict(sha1="9862d78703d829e7fb42a8d99e50ef7a6cc25827", bytes_per_single=530.0,
+DIGITIZER_TRAFFIC = dict(sha1="0649a7067c2b412d768c3ebe6c07ef788865953a", bytes_per_single=530.1,
                          capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
 
 

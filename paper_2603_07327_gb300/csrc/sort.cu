@@ -182,7 +182,14 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(SortDev S, int p) {
             k[j] = ok ? kin[i] : 0ull;
             v[j] = ok ? vin[i] : 0u;
             const uint32_t d = ok ? (uint32_t)((k[j] >> (8 * p)) & 0xFF) : 256u;
-            const uint32_t peers = __match_any_sync(kFullMask, d);
+            // lanes with the same digit: intersect the eight bit-plane ballots
+            // (and the ninth bit that marks lanes past the end)
+            uint32_t peers = kFullMask;
+#pragma unroll
+            for (int bit = 0; bit < 9; ++bit) {
+                const uint32_t m = __ballot_sync(kFullMask, (d >> bit) & 1u);
+                peers &= ((d >> bit) & 1u) ? m : ~m;
+            }
             const uint32_t before = (d < 256u) ? sm.wh[w][d] : 0u;
             rank[j] = before + __popc(peers & lane_lt());
             __syncwarp();

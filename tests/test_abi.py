@@ -199,3 +199,14 @@ def test_sensitivity_map_refuses_bad_arguments_before_any_launch(G):
             assert e.value.code == -1, str(e.value)
     finally:
         sc.close()
+
+
+def test_whole_launch_copy_refuses_null_arguments(G):
+    """gpet_result_copy_run(_async) with a NULL result, or a NULL destination
+    with a non-zero capacity, is GPET_ERR_INVALID_ARG (no device work)."""
+    import ctypes as C
+    L = G.load()
+    nb = C.c_size_t()
+    assert L.gpet_result_copy_run(None, G.SINGLES_T_PS, None, 0, C.byref(nb)) == -1
+    assert L.gpet_result_copy_run_async(None, G.SINGLES_T_PS, None, 0, C.byref(nb), None) == -1
+    assert L.gpet_result_copy(None, G.SINGLES_T_PS, None, 0) == -1

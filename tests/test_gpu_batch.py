@@ -156,3 +156,22 @@ def test_async_whole_launch_copy_equals_the_blocking_one(G):
         r.free()
     for j in jobs:
         j["scanner"].close()
+
+
+def test_batch_of_more_designs_than_staged_geometries(G):
+    """24 distinct designs in one launch: the kernels stage at most 16 geometry
+    descriptors in shared memory (fewer when the pool leaves no room) and read
+    the rest through L1.  Every job must still equal its plain run."""
+    designs = W.config4(n_designs=24, scale=0.01)
+    jobs = [dict(scanner=G.Scanner(d["scanner"]), source=d["source"], digitizer=d["digitizer"],
+                 n_decays=d["n_decays"], seed=d["seed"]) for d in designs]
+    res = G.simulate_batch(jobs)
+    for j, r in zip(jobs, res):
+        p = j["scanner"].simulate(j["source"], j["digitizer"], j["n_decays"], j["seed"])
+        assert np.array_equal(r.tallies()[0], p.tallies()[0])
+        assert np.array_equal(r.tallies()[1], p.tallies()[1])
+        assert r.counts()["coincidences"] == p.counts()["coincidences"]
+        p.free()
+        r.free()
+    for j in jobs:
+        j["scanner"].close()
