@@ -394,6 +394,36 @@ def run_design_sweep(G, args):
                 coincidences_identical=batched_coinc == plain_coinc)
 
 
+def run_variants(G, args):
+    """Throughput of the other parity-tested forms, each one plain run after a
+    warm-up, device-timed by the library's stage events (transport + digitizer):
+    the offset dual-layer ring with the hot-rod water phantom as the source
+    (1e8 pairs at 1e5 Bq: 1000 s of acquisition, inside the 2^52 ps time key),
+    four posed heads in non-repetition mode, the four-layer ring,
+    and module-level readout on the H2RSPET split ring (1e7 pairs each)."""
+    dg = W.digitizer()
+    split = W.h2rspet("split", modules_v=2)
+    split["readout_level"] = W.READOUT_MODULE
+    cases = [("offset_dual_layer_phantom", W.config3_scanner(), W.phantom_source(activity_bq=1e5), W.hot_rod_phantom(),
+              100_000_000, 3),
+             ("posed_heads", W.box_scanner(), W.point_source((4.0, -3.0, 2.5)), None, 10_000_000, 41),
+             ("four_layer_ring", W.four_layer_scanner(), W.point_source((6.0, 2.0, -4.0)), None, 10_000_000, 47),
+             ("module_readout", split, W.point_source((21.0, -13.0, 9.0)), None, 10_000_000, 77)]
+    out = {}
+    for name, scd, src, ph, n, seed in cases:
+        sc = G.Scanner(scd, ph)
+        sc.simulate(src, dg, 1_000_000, seed, kernel=args.kernel).free()
+        r = sc.simulate(src, dg, n, seed, kernel=args.kernel)
+        c = r.counts()
+        r.free()
+        sc.close()
+        ms = c["transport_ms"] + c["digitizer_ms"]
+        out[name] = dict(pairs=n, device_ms=ms, pairs_per_s=n / (ms / 1000.0), transport_ms=c["transport_ms"],
+                         hits=c["hits"], singles=c["singles"], coincidences=c["coincidences"],
+                         phantom_steps=c["phantom_steps"])
+    return out
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -587,6 +617,8 @@ def run_ours(args):
         line["served"] = run_served(G, args)
     if rank == 0 and args.design_sweep:
         line["design_sweep"] = run_design_sweep(G, args)
+    if rank == 0 and args.variants:
+        line["variants"] = run_variants(G, args)
     if rank == 0 and args.sensitivity:
         line["sensitivity_map"] = run_sensitivity(G, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -616,6 +648,8 @@ def main():
     ap.add_argument("--served", action="store_true", default=True)
     ap.add_argument("--no-served", dest="served", action="store_false")
     ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--variants", action="store_true", default=True)
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--design-sweep", action="store_true", default=True)
     ap.add_argument("--no-design-sweep", dest="design_sweep", action="store_false")
     ap.add_argument("--sensitivity", action="store_true", default=True)
