@@ -1,6 +1,6 @@
 // api.cu -- host side of the C ABI declared in include/gpet.h: scanner
-// descriptions (Sec. 2.1 hierarchy, repetition mode), phantom upload, the
-// plain simulation call and result access.
+// descriptions (Sec. 2.1 hierarchy; repetition mode or panels placed one by
+// one), phantom upload and validation, the cross-section table, errors.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>

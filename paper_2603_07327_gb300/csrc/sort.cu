@@ -6,8 +6,9 @@
 // digits: one fused pass builds the eight digit histograms, a plan kernel
 // drops the passes whose digit is the same for every key (high time bytes,
 // unused job bits), and every remaining pass is tile histogram -> per-digit
-// scan -> stable scatter.  Stable ranks inside a tile come from warp
-// __match_any_sync groups in input order.  The element count is read on the
+// scan -> stable scatter.  Stable ranks inside a tile come from the lanes of
+// a warp with the same digit (the intersection of bit-plane ballots), in input
+// order.  The element count is read on the
 // device, so the whole chain is enqueued without a host round trip.
 #include "internal.h"
 

@@ -4,6 +4,8 @@
 //                       one event per loop iteration; idle lanes are refilled
 //                       warp-wide (one atomic per chunk of histories).
 //   k_transport_wave  : wavefront form with warp-ballot regrouping (transport_wave.cu).
+//   k_transport_cta   : wavefront form with one event per CTA and iteration, the
+//                       default launch form (transport_cta.cu).
 //   k_transport_redo  : exact fallback for the rare history whose on-chip
 //                       singles list overflowed: re-simulated alone with a
 //                       long list (the RNG is addressed by history id, so the

@@ -1,7 +1,7 @@
 // transport.cuh -- per-history photon-pair transport as a set of events that
-// advance one history by one step.  Both transport kernels (the per-lane event
-// loop and the warp-regrouping wavefront) run these same events, so they
-// produce identical histories.
+// advance one history by one step.  Every transport kernel (the per-lane event
+// loop, the per-warp wavefront, the CTA-synchronous wavefront and the overflow
+// re-simulation) runs these same events, so they produce identical histories.
 //
 // Paper anchors (arxiv 2603.07327): Sec. 2.1 (flight by line-plane
 // intersection, panel-local frame, Woodcock stepping until the photon leaves

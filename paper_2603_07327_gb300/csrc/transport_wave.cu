@@ -4,7 +4,7 @@
 // arrays, one 32-bit word per field and slot).  Every iteration the warp
 //   1. refills idle slots with new history ids from the chunked work queue,
 //   2. ballots the phase of all slots (decay, phantom step, flight, panel
-//      step, finish) and picks the most populated phase,
+//      step, flight after a panel exit, finish) and picks the most populated,
 //   3. maps its 32 lanes onto the slots in that phase (__fns over the ballot
 //      masks), so every lane runs the same event code,
 //   4. runs up to `compact_every` events of that phase per lane and stores

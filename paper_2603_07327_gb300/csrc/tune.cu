@@ -1,7 +1,8 @@
 // tune.cu -- autotuner of the transport launch.  It times the candidate
 // launch forms on a pilot run of the caller's own workload (same scanner,
-// source and digitizer): the per-lane event loop at 1 or 2 CTAs per SM, and
-// the wavefront kernel at several regrouping intervals.  The fastest form is
+// source and digitizer): the per-lane event loop at 2 CTAs per SM, the per-warp
+// wavefront, and the CTA-synchronous wavefront at 128, 256 and 512 threads
+// (slot pool depth 2) and at 256 threads with depth 3.  The fastest form is
 // returned and remembered per design class (panels, layers, phantom) and SM
 // count; launches that leave gpet_options.kernel at 0 use it.
 #include <algorithm>
