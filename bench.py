@@ -128,20 +128,27 @@ class Clocks:
 # were taken on: the entry carries their SHA-1, and `traffic` is reported as null
 # once any transport source differs.
 TRANSPORT_SOURCES = ("device.cuh", "transport.cuh", "transport.cu", "transport_cta.cu")
-TRANSPORT_TRAFFIC = dict(sha1="c42443e218da70df0188d3d5b2bc5ba802fbd458", bytes_per_pair=8.403,
+TRANSPORT_TRAFFIC = dict(sha1="87e57fcd9aa7cb59d899026efddc142b5f3510ae", bytes_per_pair=8.403,
                          capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
 # The same for the digitizer back end (make_keys .. job_stats of one step), per single.
 DIGITIZER_SOURCES = ("device.cuh", "sort.cu")
-DIGITIZER_TRAFFIC = dict(sha1="0649a7067c2b412d768c3ebe6c07ef788865953a", bytes_per_single=530.1,
+DIGITIZER_TRAFFIC = dict(sha1="9db5c407da2338e68a7faa3e663ec2cacd980dc3", bytes_per_single=530.1,
                          capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
 
 
 def _sources_sha1(names):
+    """SHA-1 of the code of the named sources: comments and blank lines are
+    dropped, so that editing a comment does not disown a capture."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for name in names:
-        with open(os.path.join(ROOT, "paper_2603_07327_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2603_07327_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(code.encode())
     return h.hexdigest()
 
 
