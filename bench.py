@@ -136,6 +136,24 @@ DIGITIZER_TRAFFIC = dict(sha1="9db5c407da2338e68a7faa3e663ec2cacd980dc3", bytes_
                          capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
 
 
+# SM issue view of the transport kernel from one ncu --set full capture (the
+# 2e6-pair sweep position of profiles/k_transport_cta_sweep_position_2e6.md):
+# issue-active fraction of the schedulers, SIMT efficiency (thread
+# instructions per warp instruction / 32), warp instructions per pair.
+# Reported while the transport code is the captured one, null otherwise.
+TRANSPORT_ISSUE = dict(sha1="", issue_active=None, simt_efficiency=None, warp_inst_per_pair=None,
+                       capture="profiles/k_transport_cta_sweep_position_2e6.md")
+
+
+def _transport_issue():
+    t = TRANSPORT_ISSUE
+    if not t or not t["sha1"] or t["sha1"] != _sources_sha1(TRANSPORT_SOURCES):
+        return None
+    return dict(issue_active=t["issue_active"], simt_efficiency=t["simt_efficiency"],
+                lane_utilisation=t["issue_active"] * t["simt_efficiency"],
+                warp_inst_per_pair=t["warp_inst_per_pair"], source="ncu --set full, " + t["capture"])
+
+
 def _sources_sha1(names):
     """SHA-1 of the code of the named sources: comments and blank lines are
     dropped, so that editing a comment does not disown a capture."""
@@ -516,7 +534,8 @@ def run_ours(args):
     roof = dict(bound="alu", achieved=achieved, peak=peak, unit="lane-ops/s", frac=achieved / peak,
                 traffic=traffic, kernel=kname,
                 peak_note="152 SMs x 128 FP32/INT lanes x 2070 MHz (recipe unit counts and max clock)",
-                transport_share=tr_ms / (tr_ms + dg_ms))
+                transport_share=tr_ms / (tr_ms + dg_ms),
+                issue=_transport_issue() if args.kernel in (0, 3) else None)
 
     # digitizer back end (time sort + coincidences), HBM-bound: algorithmic bytes
     # per single = key build 24 + 8 radix passes x 32 (histogram read 8, scatter
