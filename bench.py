@@ -141,7 +141,7 @@ DIGITIZER_TRAFFIC = dict(sha1="9db5c407da2338e68a7faa3e663ec2cacd980dc3", bytes_
 # issue-active fraction of the schedulers, SIMT efficiency (thread
 # instructions per warp instruction / 32), warp instructions per pair.
 # Reported while the transport code is the captured one, null otherwise.
-TRANSPORT_ISSUE = dict(sha1="", issue_active=None, simt_efficiency=None, warp_inst_per_pair=None,
+TRANSPORT_ISSUE = dict(sha1="87e57fcd9aa7cb59d899026efddc142b5f3510ae", issue_active=0.4947, simt_efficiency=0.5803, warp_inst_per_pair=142.2,
                        capture="profiles/k_transport_cta_sweep_position_2e6.md")
 
 
