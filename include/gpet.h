@@ -197,7 +197,13 @@ int gpet_load_phantom(gpet_scanner *sc, int32_t nx, int32_t ny, int32_t nz, cons
  * Random numbers come from Philox4x32-10 addressed by (history, region,
  * photon, step, sub-draw), so any history is reproducible on its own.
  * Enqueues transport, digitizer, time sort and coincidence sorting on
- * opt->stream and synchronises it.  On success *out holds the result. */
+ * opt->stream and synchronises it.  On success *out holds the result.
+ * n_decays must be >= 1, and the acquisition n_decays / activity_bq below
+ * 4000 s (time stamps in ps share a 64-bit sort key with the job index, which
+ * leaves 2^52 ps, about 4500 s): GPET_ERR_INVALID_ARG otherwise.  GPET_ERR_TIMEOUT when a photon
+ * exceeded 1000 Woodcock steps in one region or 1000 Klein-Nishina trials
+ * (the photon is dropped, nothing waits); the run's other outputs are not
+ * returned. */
 int gpet_simulate(gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg, uint64_t n_decays,
                   uint64_t seed, const gpet_options *opt, gpet_result **out);
 

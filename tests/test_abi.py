@@ -210,3 +210,33 @@ def test_whole_launch_copy_refuses_null_arguments(G):
     assert L.gpet_result_copy_run(None, G.SINGLES_T_PS, None, 0, C.byref(nb)) == -1
     assert L.gpet_result_copy_run_async(None, G.SINGLES_T_PS, None, 0, C.byref(nb), None) == -1
     assert L.gpet_result_copy(None, G.SINGLES_T_PS, None, 0) == -1
+
+
+def test_empty_and_out_of_range_sizes_are_refused_on_the_host(G):
+    """Degenerate and maximum sizes: zero decays, a shard outside the run, more
+    than 64 panels, 8 layers or 8 materials, and an acquisition past the 2^52 ps
+    time key are GPET_ERR_INVALID_ARG before any device work; the largest
+    accepted descriptor sizes (64 panels, 8 layers, 8 materials) are accepted."""
+    import ctypes as C
+    L = G.load()
+    sc = G.Scanner(W.config1_scanner())
+    try:
+        for n, opts in ((0, {}), (100, dict(h_begin=50, h_end=200)), (100, dict(h_begin=60, h_end=60))):
+            with pytest.raises(G.GpetError) as e:
+                sc.simulate(W.point_source(), W.digitizer(), n, 1, **opts)
+            assert e.value.code == -1
+        with pytest.raises(G.GpetError) as e:   # 1e9 decays at 1 Bq: far past 2^52 ps
+            sc.simulate(W.point_source(activity_bq=1.0), W.digitizer(), 10**9, 1)
+        assert e.value.code == -1
+    finally:
+        sc.close()
+    big = W.scanner(64, 400.0, [W.layer(4, 4, 1.0, 0.1, 1.0, gap_before=0.05 if l else 0.0) for l in range(8)],
+                    materials=[W.AIR] + [W.LYSO] * 7)
+    assert _create(G, big) == 0
+    for key, val in (("n_panels", 65),):
+        bad = dict(big, **{key: val})
+        assert _create(G, bad) == -1
+    nine = dict(big, layers=big["layers"] + [W.layer(4, 4, 1.0, 0.1, 1.0, gap_before=0.05)])
+    assert _create(G, nine) == -1
+    mats = dict(big, materials=big["materials"] + [W.LYSO])
+    assert _create(G, mats) == -1
