@@ -251,3 +251,26 @@ def test_posed_scanner_in_a_batch_keeps_its_own_poses(G):
         assert np.array_equal(r.singles()["t_ps"], p.singles()["t_ps"])
     # the rotated scanner sees the source from elsewhere: its tallies differ
     assert not np.array_equal(plain[0].tallies()[0], plain[1].tallies()[0])
+
+
+def test_per_crystal_counts_agree_in_distribution_on_independent_seeds(G, oracle):
+    """The statistical form of the bar: GPU and oracle runs on different Philox
+    keys give per-crystal counts that a two-sample chi-square test accepts at
+    p > 0.01.  The counted events are singles (window opened to 0-5000 keV):
+    a history adds at most one single to a crystal, so the counts are Poisson.
+    (Interaction tallies are not: one photon's Compton chain often leaves
+    several interactions in one crystal, which inflates their variance by about
+    a quarter and fails the Poisson test on the same, correct runs.)"""
+    from scipy import stats
+    sc, src, n = W.config2_scanner("B"), W.point_source((0.0, 0.0, 7.0)), 400_000
+    dg = W.digitizer(e_lo=0.0, e_hi=5000.0)
+    n_cry = oracle.n_crystals(sc)
+    gs = G.simulate(sc, src, dg, n, 101).singles()
+    os_ = oracle.simulate(sc, src, dg, n, 202, threads=8, tallies=False)["singles"]
+    g = np.bincount(gs["unit"].astype(np.int64), minlength=n_cry).astype(np.float64)
+    o = np.bincount(os_[os_["kept"] == 1]["unit"].astype(np.int64), minlength=n_cry).astype(np.float64)
+    keep = (g + o) >= 20
+    chi2 = float((((g[keep] - o[keep]) ** 2) / (g[keep] + o[keep])).sum())
+    dof = int(keep.sum())
+    p = float(stats.chi2.sf(chi2, dof))
+    assert dof > 1000 and p > 0.01, (chi2, dof, p)
