@@ -555,10 +555,11 @@ def run_ours(args):
     # over the sweep from host descriptors, and the step's results -- singles'
     # times, units and energies, coincidence pairs and per-crystal tallies of
     # the whole launch -- are read into caller-owned pinned host buffers, one
-    # copy per array (gpet_result_copy_run).  A first, untimed pass sizes the
-    # buffers, which every timed step reuses.  (Overlapping a step's copies
-    # with the next step's simulation on a side stream measured slower: the
-    # simulation lost more than the copies took.)
+    # copy per array, the arrays concurrently on their own streams
+    # (gpet_result_copy_run_async), all landed before the step ends.  A first,
+    # untimed pass sizes the buffers, which every timed step reuses.
+    # (Overlapping a step's copies with the next step's simulation measured
+    # slower: the simulation lost more than the copies took.)
     E2E_ARRAYS = (G.SINGLES_T_PS, G.SINGLES_UNIT, G.SINGLES_E, G.COINC_A, G.COINC_B, G.TALLY_COUNT, G.TALLY_EFX)
 
     def e2e_simulate():
@@ -578,6 +579,8 @@ def run_ours(args):
     for r in res0:
         r.free()
     bufs = {w: torch.empty(need[w] + 4096, dtype=torch.uint8, pin_memory=True) for w in E2E_ARRAYS}
+    # one copy stream per array: the arrays travel concurrently once the step is done
+    copy_streams = {w: torch.cuda.Stream() for w in E2E_ARRAYS}
     torch.cuda.synchronize()
     e2e_t0 = time.perf_counter()
     sim_s = 0.0
@@ -591,9 +594,12 @@ def run_ours(args):
             h2d += r.counts()["h2d_bytes"]
             off = {w: 0 for w in E2E_ARRAYS}
             for w in E2E_ARRAYS:
-                nb = r.copy_run_into(w, bufs[w].data_ptr() + off[w], bufs[w].numel() - off[w])
+                nb = r.copy_run_into_async(w, bufs[w].data_ptr() + off[w], bufs[w].numel() - off[w],
+                                           copy_streams[w].cuda_stream)
                 off[w] += nb
                 d2h += nb
+        for cs in copy_streams.values():
+            cs.synchronize()
         for r in res:
             r.free()
     torch.cuda.synchronize()
@@ -618,7 +624,7 @@ def run_ours(args):
                 e2e=dict(value=pairs_per_step * world / e2e_dt, unit="pairs/s", h2d_bytes_per_step=h2d,
                          d2h_bytes_per_step=d2h, ms_per_step=1000 * e2e_dt, simulate_ms_per_step=1000 * e2e_sim_s,
                          copy_ms_per_step=1000 * (e2e_dt - e2e_sim_s), host_buffers="pinned, caller-owned, reused",
-                         copies="one copy per array of the whole launch"),
+                         copies="one async copy per array of the whole launch, arrays on concurrent streams"),
                 stages=dict(transport_ms_per_step=tr_ms / args.steps, digitizer_ms_per_step=dg_ms / args.steps),
                 per_step_counts=dict(hits=sum(c["hits"] for c in counts) // args.steps,
                                      singles=sum(c["singles"] for c in counts) // args.steps,
