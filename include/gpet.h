@@ -181,10 +181,15 @@ void gpet_destroy_scanner(gpet_scanner *sc);
  * with C the crystal count of one module summed over layers. */
 int gpet_scanner_crystals(const gpet_scanner *sc, int64_t *n_crystals);
 
-/* Load (or replace) the voxelised phantom used by the next simulations.
+/* Load (or replace) the voxelised phantom used by the next simulations
+ * (Sec. 2.3: the phantom attenuates and, with an activity map, is the source).
+ * Grid: nx x ny x nz voxels of voxel_mm, low corner at origin_mm (global mm).
  * material_ids: host, nx*ny*nz bytes, x fastest, indices into materials.
  * activity: host, nx*ny*nz floats (>= 0) or NULL when the phantom only
- * attenuates.  The grid must lie inside the ring's inner radius. */
+ * attenuates.  Photons never re-enter the phantom after reaching a panel, so
+ * the grid must clear the detector: inside the ring's inner radius, or, for a
+ * scanner with panel poses, overlapping no panel box (GPET_ERR_GEOMETRY
+ * otherwise).  All arrays are copied; the device copies are the scanner's. */
 int gpet_load_phantom(gpet_scanner *sc, int32_t nx, int32_t ny, int32_t nz, const double voxel_mm[3],
                       const double origin_mm[3], const uint8_t *material_ids, const float *activity,
                       int32_t n_materials, const gpet_material *materials);
