@@ -92,6 +92,8 @@ CASES["near_ring_offcentre"] = (lambda: W.config2_scanner("B"), lambda: W.point_
 CASES["box4_posed"] = (W.box_scanner, lambda: W.point_source((4.0, -3.0, 2.5)), None, 150_000, 41)
 CASES["box4_posed_phantom"] = (W.box_scanner, W.phantom_source, W.hot_rod_phantom, 40_000, 43)
 CASES["ring12_4layer"] = (W.four_layer_scanner, lambda: W.point_source((6.0, 2.0, -4.0)), None, 100_000, 47)
+CASES["box4_posed_module_readout"] = (lambda: W.box_scanner(readout_level=W.READOUT_MODULE),
+                                      lambda: W.point_source((-3.0, 5.0, -1.0)), None, 100_000, 49)
 
 KERNELS = {"loop": 1, "wave": 2, "cta": 3}
 
