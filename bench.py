@@ -645,17 +645,24 @@ def run_ours(args):
         t1.synchronize()
         line["plain_pairs_per_s"] = pairs_per_step / (t0.elapsed_time(t1) / 1000.0)
         line["batched_over_plain"] = value / line["plain_pairs_per_s"]
+    def aux(key, fn):
+        # an auxiliary measurement that fails is reported, not fatal: the main line still prints
+        try:
+            line[key] = fn()
+        except Exception as exc:  # noqa: BLE001
+            line[key] = dict(error=f"{type(exc).__name__}: {exc}")
+            print(f"bench: {key} failed: {exc!r}", file=sys.stderr, flush=True)
+
     if rank == 0 and args.served:
-        line["served"] = run_served(G, args)
+        aux("served", lambda: run_served(G, args))
     if rank == 0 and args.design_sweep:
-        line["design_sweep"] = run_design_sweep(G, args)
+        aux("design_sweep", lambda: run_design_sweep(G, args))
     if rank == 0 and args.variants:
-        line["variants"] = run_variants(G, args)
+        aux("variants", lambda: run_variants(G, args))
     if rank == 0 and args.sensitivity:
-        line["sensitivity_map"] = run_sensitivity(G, args)
+        aux("sensitivity_map", lambda: run_sensitivity(G, args))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb, _, _ = cpu_baseline()
-        line["cpu_baseline"] = cb
+        aux("cpu_baseline", lambda: cpu_baseline()[0])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
