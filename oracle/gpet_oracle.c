@@ -191,7 +191,9 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
 /* uniform in (0,1) from the top 23 bits: (k + 1/2) * 2^-23 (exact in FP32 too) */
 double or_uniform(uint32_t w) { return ((double)(w >> 9) + 0.5) * 0x1p-23; }
 
-/* draw block for (history, tag, photon, step, sub) under key = seed */
+/* draw block for (history, tag, photon, step, sub) under key = seed.  The paper
+ * names no generator; every draw is addressed so that one history can be
+ * replayed alone and compared with the GPU's, draw for draw. */
 static void or_draw(uint64_t seed, uint64_t h, uint32_t tag, uint32_t gamma, uint32_t step,
                     uint32_t sub, uint32_t out[4]) {
     uint32_t ctr[4] = {(uint32_t)h, (uint32_t)(h >> 32),
@@ -214,7 +216,10 @@ double or_sigma_kn(double e_kev) {
     return 2.0 * OR_PI * OR_RE_CM * OR_RE_CM * (t1 + t2 - t3);
 }
 
-/* linear attenuation coefficients in 1/cm */
+/* linear attenuation coefficients in 1/cm of the synthetic physics model used
+ * for this study (Sec. 2.1 defers the physics to gPET): photoelectric scaled
+ * by (511/E)^3 from its 511 keV value, Compton by the Klein-Nishina total
+ * cross section, no Rayleigh scattering */
 double or_mu_photo(const om_material *m, double e_kev) {
     double r = OR_E0_KEV / e_kev;
     return m->mu_total_511_cm * m->photo_frac_511 * r * r * r;
@@ -262,7 +267,9 @@ int or_kahn(uint64_t seed, uint64_t h, uint32_t tag, uint32_t gamma, uint32_t st
     return -1;
 }
 
-/* rotate unit vector d by polar angle (cos c, sin s) and azimuth phi = 2 pi u */
+/* rotate unit vector d by polar angle (cos c, sin s) and azimuth phi = 2 pi u:
+ * the direction change of a Compton scatter (Sec. 2.1, interactions sampled
+ * along the photon's path) */
 static void or_rotate(double d[3], double c, double s, double u_phi) {
     double cp = cos(2.0 * OR_PI * u_phi), sp = sin(2.0 * OR_PI * u_phi);
     double dx = d[0], dy = d[1], dz = d[2];
@@ -299,6 +306,8 @@ typedef struct {
     int32_t mat;
 } or_loc;
 
+/* the detector of Sec. 2.1: panel extents from the modules, layer depths in
+ * order, crystal-id offsets, and the panel placements (ring or poses) */
 static int or_geom_init(or_geom *g, const om_scanner *sc) {
     if (sc->n_panels < 1 || sc->n_panels > OR_MAX_PANELS || sc->n_layers < 1 ||
         sc->n_layers > OR_MAX_LAYERS || sc->n_materials < 1 || sc->n_materials > OR_MAX_MATERIALS)
@@ -351,6 +360,7 @@ static void or_to_local(const or_geom *g, int k, const double x[3], double *w, d
     *v = x[2];
 }
 
+/* a direction in panel k's frame (Sec. 2.1, panel-local coordinates) */
 static void or_dir_local(const or_geom *g, int k, const double d[3], double *dw, double *du, double *dv) {
     if (g->posed) {
         *dw = or_dot3(d, g->ax[k][0]);
@@ -401,7 +411,8 @@ void or_locate(const or_geom *g, int k, double w, double u, double v, or_loc *ou
     out->crystal = module_global * g->crystals_per_module + g->layer_off[l] + iv * L->n_u + iu;
 }
 
-/* slab test of the ray (x, d) against panel k's box; returns 1 on a hit with t_in < t_out */
+/* slab test of the ray (x, d) against panel k's box in the panel frame (Sec. 2.1:
+ * line-plane intersection with the panel); returns 1 on a hit with t_in < t_out */
 static int or_panel_hit(const or_geom *g, int k, const double x[3], const double d[3],
                         double *t_in, double *t_out) {
     double p[3], q[3];
@@ -427,7 +438,8 @@ static int or_panel_hit(const or_geom *g, int k, const double x[3], const double
     return 1;
 }
 
-/* line-plane flight: nearest panel entered along (x, d), skipping panel `skip` */
+/* line-plane flight (Sec. 2.1): nearest panel entered along (x, d), skipping
+ * panel `skip`, by testing every panel */
 int or_flight(const or_geom *g, const double x[3], const double d[3], int skip, double *t_in,
               double *t_out) {
     int best = -1;
@@ -452,6 +464,8 @@ typedef struct {
     int64_t last_active;
 } or_phantom;
 
+/* the voxel phantom of Sec. 2.3: grid bounds and, with an activity map, its
+ * prefix sums in voxel order */
 static int or_phantom_init(or_phantom *P, const om_phantom *ph) {
     memset(P, 0, sizeof(*P));
     P->ph = ph;
@@ -479,7 +493,9 @@ static int or_phantom_init(or_phantom *P, const om_phantom *ph) {
     return OR_OK;
 }
 
-/* smallest voxel i with cdf[i] > target (plain linear scan: obviously correct) */
+/* smallest voxel i with cdf[i] > target (plain linear scan: obviously correct):
+ * a voxel with probability proportional to its activity (Sec. 2.3, phantom
+ * activity as the source) */
 static int64_t or_pick_voxel(const or_phantom *P, double target) {
     int64_t n = (int64_t)P->ph->nx * P->ph->ny * P->ph->nz;
     if (target >= P->total) return P->last_active;
@@ -488,12 +504,14 @@ static int64_t or_pick_voxel(const or_phantom *P, double target) {
     return P->last_active;
 }
 
+/* point inside the phantom grid (half-open box) */
 static int or_inside_phantom(const or_phantom *P, const double x[3]) {
     for (int a = 0; a < 3; ++a)
         if (!(x[a] >= P->lo[a] && x[a] < P->hi[a])) return 0;
     return 1;
 }
 
+/* distance along d from x to the phantom grid's exit */
 static double or_phantom_exit(const or_phantom *P, const double x[3], const double d[3]) {
     double t = INFINITY;
     for (int a = 0; a < 3; ++a) {
@@ -503,6 +521,7 @@ static double or_phantom_exit(const or_phantom *P, const double x[3], const doub
     return t < 0.0 ? 0.0 : t;
 }
 
+/* material of the voxel holding x */
 static int or_phantom_mat(const or_phantom *P, const double x[3]) {
     const om_phantom *ph = P->ph;
     int i[3];
@@ -564,7 +583,7 @@ typedef struct {
     uint32_t ph_real;                      /* real interactions in the phantom */
 } or_energy;
 
-/* majorant over a material list at energy E */
+/* majorant over a material list at energy E (Woodcock tracking, Sec. 2.1) */
 static double or_majorant(const om_material *mats, int n, double e) {
     double m = 0.0;
     for (int i = 0; i < n; ++i) {
@@ -574,6 +593,11 @@ static double or_majorant(const om_material *mats, int n, double e) {
     return m;
 }
 
+/* one annihilation photon through the transport of Sec. 2.1: Woodcock steps in
+ * the phantom, flight to a panel by line-plane intersection, Woodcock steps in
+ * the panel with the layer-selection step, photoelectric absorption or
+ * Klein-Nishina Compton scatter, hits in crystals, and on to the next panel
+ * until the photon escapes, is absorbed or falls below the cutoff */
 static int or_transport_photon(const or_ctx *C, uint64_t h, uint32_t gamma, double x[3], double d[3],
                                uint64_t t0_ps, or_sink *S, om_hit *hist_hits, int *n_hist_hits,
                                int cap_hist, or_energy *en) {
@@ -755,6 +779,9 @@ static void or_decay(const or_ctx *C, uint64_t h, uint64_t *t0, double x0[3], do
     }
 }
 
+/* one decay (Sec. 2.3): the back-to-back pair transported photon by photon,
+ * tallies, then the singles of the history per readout unit (Sec. 2.1) with
+ * energy blur and window (Sec. 2.3) */
 static int or_history(const or_ctx *C, uint64_t h, or_sink *S, uint64_t *tc, uint64_t *tefx,
                       double *tedep, double *balance, uint32_t *ph_real) {
     uint64_t t0;
