@@ -429,6 +429,65 @@ def test_coincidence_policy_brute_force(oracle):
         assert got == brute_force_coincidences(t, panel, 2000), trial
 
 
+def _renewal_coincidences(rate_per_ps, tau_ps, span_ps, p_diff):
+    """Expected coincidences of the single-window, kill-multiples sorter on a
+    Poisson stream: windows open at rate rate/(1 + rate tau) (the stream is
+    memoryless, so each window closes and the next opens at the first later
+    single), and a window holds exactly one more single with probability
+    rate tau exp(-rate tau)."""
+    x = rate_per_ps * tau_ps
+    return span_ps * rate_per_ps / (1.0 + x) * x * math.exp(-x) * p_diff
+
+
+@pytest.mark.parametrize("x", [0.05, 0.5, 2.0])
+def test_window_sorter_on_poisson_singles(oracle, x):
+    """Poisson singles with uniform panels: the coincidence count follows the
+    renewal formula at any rate.  Catches a sliding instead of a consumed
+    window, multiples kept or counted, and the same-panel rule."""
+    rng = np.random.default_rng(int(x * 100))
+    tau = 2000
+    rate = x / tau
+    n = 200_000
+    span = n / rate
+    t = np.sort(rng.uniform(0.0, span, n)).astype(np.uint64)
+    n_panels = 4
+    s = np.zeros(n, dtype=[("t_ps", "<u8"), ("unit", "<i4"), ("panel", "<i4"), ("h", "<u8")])
+    s["t_ps"] = t
+    s["panel"] = rng.integers(0, n_panels, n)
+    s["unit"] = s["panel"] * 100
+    s["h"] = np.arange(n)
+    _, a, _ = oracle.coincidences(s, tau / 1000.0)
+    want = _renewal_coincidences(rate, tau, span, 1.0 - 1.0 / n_panels)
+    assert abs(len(a) - want) < 5.0 * math.sqrt(want), (len(a), want)
+
+
+def test_randoms_rate_at_high_activity(oracle):
+    """Whole chain at 1e9 Bq: coincidences of two histories (randoms) against
+    the renewal form of 2 tau S_i S_j.  Histories arrive as a Poisson process
+    (uniform decay times on [0, n/A], Sec. 2.3); a random needs an opening
+    history with exactly one kept single in panel i, one more such history
+    within tau in panel j != i, and no third.  Pins the time model (the span
+    n/A in picoseconds) together with the sorter."""
+    sc = W.config1_scanner()
+    dg = W.digitizer()
+    n, act = 10_000_000, 1e9
+    r = oracle.simulate(sc, W.point_source(activity_bq=act), dg, n, seed=2024, threads=8, tallies=False)
+    span = r["t_span_ps"]
+    assert span == pytest.approx(n / act * 1e12, rel=1e-12)
+    s, a, b = oracle.coincidences(r["singles"], dg["window_ns"])
+    randoms = int((s["h"][a] != s["h"][b]).sum())
+    # histories with at least one kept single, and those with exactly one, per panel
+    hs, first, cnt = np.unique(s["h"], return_index=True, return_counts=True)
+    lam = len(hs) / span
+    one = s["panel"][first[cnt == 1]]
+    R = np.bincount(one, minlength=sc["n_panels"]) / span
+    tau = dg["window_ns"] * 1000.0
+    x = lam * tau
+    want = span * tau * math.exp(-x) / (1.0 + x) * (R.sum() ** 2 - (R ** 2).sum())
+    assert x > 0.03 and want > 5000
+    assert abs(randoms - want) < 5.0 * math.sqrt(want), (randoms, want)
+
+
 def test_split_and_offset_relations_h2rspet(oracle):
     """Context check on the paper's Table 1 relations, centred point source on
     reduced H2RSPET rings: split == 1CL within Poisson error; 2CL lower."""
