@@ -41,8 +41,10 @@ enum : uint32_t { kTagSource = 1u, kTagPhantom = 2u, kTagDetector = 3u, kTagDigi
 
 // device status codes (host maps them to GPET_ERR_*)
 // kStatusBadPhase: a history in a phase no event handles (an internal error);
-// the history is dropped, so no event loop can spin on it
-enum : int { kStatusOk = 0, kStatusTimeout = 1, kStatusOverflow = 2, kStatusBadPhase = 4 };
+// the history is dropped, so no event loop can spin on it.
+// kStatusSortStall: a radix-sort tile copy did not complete within the wait
+// limit; the sort stops and its output is invalid (an internal error).
+enum : int { kStatusOk = 0, kStatusTimeout = 1, kStatusOverflow = 2, kStatusBadPhase = 4, kStatusSortStall = 8 };
 
 // ---------------------------------------------------------------------------
 // geometry descriptor (FP32, one per scanner design)

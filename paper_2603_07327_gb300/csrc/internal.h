@@ -31,6 +31,7 @@ struct SortDev {
     unsigned long long cap;
     const unsigned long long *n_in;  // device count of unsorted singles
     const RawSingle *in_raw;         // unsorted singles
+    int *status;                     // run status word (kStatusSortStall), or NULL: unstaged passes
 };
 
 // time-ordered singles

@@ -247,6 +247,7 @@ int run_plan(Run &R) {
     S.max_tiles = tiles;
     S.cap = cap;
     S.n_in = &H->n_singles;
+    S.status = &H->status;
     S.in_raw = O.s_raw;
     SD.n = &H->n_sorted;
     C.n = &H->n_coinc;
@@ -342,6 +343,8 @@ int run_collect(Run &R) {
                          H.n_singles, R.O.s_cap, H.n_hits, R.O.hit_cap, H.n_ovf, R.O.ovf_cap);
     if (H.status & kStatusBadPhase)
         return gpet_fail(GPET_ERR_CUDA, "internal error: a history reached a phase no event handles");
+    if (H.status & kStatusSortStall)
+        return gpet_fail(GPET_ERR_CUDA, "internal error: a time-sort tile copy did not complete");
     if (H.status & kStatusOverflow)
         return gpet_fail(GPET_ERR_OVERFLOW, "a history touched more than 64 readout units");
     return GPET_OK;

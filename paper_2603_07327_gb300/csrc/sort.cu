@@ -8,8 +8,11 @@
 // unused job bits), and every remaining pass is tile histogram -> per-digit
 // scan -> stable scatter.  Stable ranks inside a tile come from the lanes of
 // a warp with the same digit (the intersection of bit-plane ballots), in input
-// order.  The element count is read on the
-// device, so the whole chain is enqueued without a host round trip.
+// order.  In the simulation path the scatter's input tiles are streamed into
+// shared memory by the bulk-copy engine (cp.async.bulk completing on an
+// mbarrier), one tile ahead of the tile being ranked.  The element count is
+// read on the device, so the whole chain is enqueued without a host round
+// trip.
 #include "internal.h"
 
 namespace gpet {
@@ -18,6 +21,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kTile = kSortThreads * kSortItems;  // 4096 keys per tile
 constexpr int kPasses = 8;
+static_assert(kSortThreads == 256, "one thread per 8-bit digit in the scatter's prefix step");
 
 __device__ __forceinline__ uint32_t lane_lt() {
     uint32_t m;
@@ -80,14 +84,22 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_hist(SortDev S, int p) {
     const unsigned long long n = sort_n(S);
     const unsigned long long tiles = (n + kTile - 1) / kTile;
     __shared__ uint32_t h[256];
-    const uint64_t *keys = S.keys[src];
+    const uint64_t *keys = src ? S.keys[1] : S.keys[0];
     for (unsigned long long t = blockIdx.x; t < tiles; t += gridDim.x) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
         __syncthreads();
         const unsigned long long b = t * kTile;
+        // all of the tile's loads are issued before the first shared atomic
+        uint64_t k[kSortItems];
+#pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const unsigned long long i = b + (unsigned long long)j * kSortThreads + threadIdx.x;
-            if (i < n) atomicAdd(&h[(keys[i] >> (8 * p)) & 0xFF], 1u);
+            k[j] = i < n ? __ldg(keys + i) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const unsigned long long i = b + (unsigned long long)j * kSortThreads + threadIdx.x;
+            if (i < n) atomicAdd(&h[(k[j] >> (8 * p)) & 0xFF], 1u);
         }
         __syncthreads();
         for (int d = threadIdx.x; d < 256; d += blockDim.x) S.tile_hist[(size_t)d * S.max_tiles + t] = h[d];
@@ -154,34 +166,135 @@ struct ScatterSmem {
     uint32_t gdelta[256];   // global run start - local run start (mod 2^32)
     uint32_t sw[32];
 };
+// Staged form: while a tile is ranked and written, the bulk-copy engine
+// streams the CTA's next tile (keys and indices) into shared memory, so each
+// CTA keeps 48 KB of reads in flight through all of its tile's work instead
+// of waiting for its loads at the start of every tile.
+struct ScatterStage {
+    uint64_t keys[kTile];
+    uint32_t vals[kTile];
+    unsigned long long bar;  // mbarrier: the copy of the staged tile has landed
+};
 constexpr size_t kScatterSmem = sizeof(ScatterSmem);
+constexpr size_t kScatterSmemStaged = sizeof(ScatterSmem) + sizeof(ScatterStage);
+constexpr uint32_t kStageBytes = kTile * (sizeof(uint64_t) + sizeof(uint32_t));
+static_assert(sizeof(ScatterSmem) % 16 == 0, "staging buffer must start on a 16-byte boundary");
+static_assert((kTile * sizeof(uint32_t)) % 16 == 0 && (kTile * sizeof(uint64_t)) % 16 == 0,
+              "bulk copies move multiples of 16 bytes");
+// mbarrier waits give up after this many polls (each poll may suspend the
+// thread for a bounded time); a tile copy that never lands is reported, not
+// waited for forever
+constexpr int kStageWaitPolls = 1 << 22;
 
-__global__ void __launch_bounds__(kSortThreads) k_scatter(SortDev S, int p) {
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool stage_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < kStageWaitPolls; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// one thread: expect the tile's bytes on the barrier, start both copies
+__device__ __forceinline__ void stage_issue(ScatterStage &sg, const uint64_t *kin, const uint32_t *vin,
+                                            unsigned long long t) {
+    const uint32_t bar = smem_addr(&sg.bar);
+    // the staging buffer was last read by ordinary loads; order them before
+    // the copy engine's writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kStageBytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(sg.keys)), "l"(kin + t * kTile), "r"((uint32_t)(kTile * sizeof(uint64_t))), "r"(bar)
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(sg.vals)), "l"(vin + t * kTile), "r"((uint32_t)(kTile * sizeof(uint32_t))), "r"(bar)
+        : "memory");
+}
+
+template <bool kStaged>
+__global__ void __launch_bounds__(kSortThreads, 2) k_scatter(SortDev S, int p) {
     if (!S.plan[p]) return;
     extern __shared__ __align__(16) unsigned char scatter_raw[];
     ScatterSmem &sm = *reinterpret_cast<ScatterSmem *>(scatter_raw);
+    ScatterStage &sg = *reinterpret_cast<ScatterStage *>(scatter_raw + sizeof(ScatterSmem));
     const int src = S.plan[kPasses + p];
     const unsigned long long n = sort_n(S);
     const unsigned long long tiles = (n + kTile - 1) / kTile;
+    const unsigned long long full_tiles = n / kTile;  // tiles the copy engine stages
     constexpr int kWarps = kSortThreads / 32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint64_t *kin = S.keys[src];
-    const uint32_t *vin = S.vals[src];
-    uint64_t *kout = S.keys[src ^ 1];
-    uint32_t *vout = S.vals[src ^ 1];
+    // selects, not an index: a dynamic index would copy the argument to the stack
+    const uint64_t *kin = src ? S.keys[1] : S.keys[0];
+    const uint32_t *vin = src ? S.vals[1] : S.vals[0];
+    uint64_t *kout = src ? S.keys[0] : S.keys[1];
+    uint32_t *vout = src ? S.vals[0] : S.vals[1];
+    uint32_t parity = 0;
+    if (kStaged) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sg.bar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            if (blockIdx.x < full_tiles) stage_issue(sg, kin, vin, blockIdx.x);
+        }
+        __syncthreads();
+    }
     for (unsigned long long t = blockIdx.x; t < tiles; t += gridDim.x) {
         for (int i = threadIdx.x; i < kWarps * 256; i += blockDim.x) (&sm.wh[0][0])[i] = 0;
-        __syncthreads();
         const unsigned long long wb = t * kTile + (unsigned long long)w * (32 * kSortItems);
+        // this tile's global start of digit threadIdx.x, fetched with the keys
+        const uint32_t gstart = S.tile_hist[(size_t)threadIdx.x * S.max_tiles + t];
         uint64_t k[kSortItems];
         uint32_t v[kSortItems];
         uint32_t rank[kSortItems];
+        const bool staged = kStaged && t < full_tiles;
+        if (staged) {
+            // every thread sees the copy land; the CTA gives up together
+            const bool ok = stage_wait(smem_addr(&sg.bar), parity);
+            if (!__syncthreads_and(ok)) {
+                if (threadIdx.x == 0) {
+                    atomicOr(S.status, kStatusSortStall);
+                    stage_wait(smem_addr(&sg.bar), parity);  // let the copy in flight land
+                }
+                return;
+            }
+            parity ^= 1u;
+            const int lb = w * (32 * kSortItems) + lane;
+#pragma unroll
+            for (int j = 0; j < kSortItems; ++j) {
+                k[j] = sg.keys[lb + j * 32];
+                v[j] = sg.vals[lb + j * 32];
+            }
+            __syncthreads();  // the staging buffer is free: stream in the next tile
+            const unsigned long long nt = t + gridDim.x;
+            if (threadIdx.x == 0 && nt < full_tiles) stage_issue(sg, kin, vin, nt);
+        } else {
+            // Every load of the tile is in flight before the ranking starts:
+            // the ranking's shared-memory stores would otherwise order each
+            // item's load after the previous item's ranking.
+#pragma unroll
+            for (int j = 0; j < kSortItems; ++j) {
+                const unsigned long long i = wb + (unsigned long long)j * 32 + lane;
+                k[j] = i < n ? __ldg(kin + i) : 0ull;
+                v[j] = i < n ? __ldg(vin + i) : 0u;
+            }
+            __syncthreads();  // the warp histograms are cleared
+        }
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const unsigned long long i = wb + (unsigned long long)j * 32 + lane;
             const bool ok = i < n;
-            k[j] = ok ? kin[i] : 0ull;
-            v[j] = ok ? vin[i] : 0u;
             const uint32_t d = ok ? (uint32_t)((k[j] >> (8 * p)) & 0xFF) : 256u;
             // lanes with the same digit: intersect the eight bit-plane ballots
             // (and the ninth bit that marks lanes past the end)
@@ -212,7 +325,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(SortDev S, int p) {
             const uint32_t lstart = block_exscan(c, tot, sm.sw);
 #pragma unroll
             for (int ww = 0; ww < kWarps; ++ww) sm.wh[ww][d] += lstart;
-            sm.gdelta[d] = S.tile_hist[(size_t)d * S.max_tiles + t] - lstart;
+            sm.gdelta[d] = gstart - lstart;
         }
         __syncthreads();
 #pragma unroll
@@ -238,14 +351,18 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(SortDev S, int p) {
 }
 
 static cudaError_t scatter_smem_attr() {
-    return cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kScatterSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kScatterSmemStaged);
 }
 
 // singles into time order
 __global__ void k_gather(SortDev S, SinglesDev out) {
     const unsigned long long n = sort_n(S);
     const int fin = S.plan[2 * kPasses];
-    const uint32_t *perm = S.vals[fin];
+    const uint32_t *perm = fin ? S.vals[1] : S.vals[0];
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint4 *r = reinterpret_cast<const uint4 *>(S.in_raw + perm[i]);
@@ -401,26 +518,27 @@ cudaError_t launch_radix_passes(const SortDev &S, int sm_count, cudaStream_t st)
                                                                               : (unsigned long long)sm_count * 8);
         k_tile_hist<<<tg, kSortThreads, 0, st>>>(S, p);
         k_digit_scan<<<256, 1024, 0, st>>>(S, p);
-        k_scatter<<<tg, kSortThreads, kScatterSmem, st>>>(S, p);
+        k_scatter<false><<<tg, kSortThreads, kScatterSmem, st>>>(S, p);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const CoincDev &C, int sm_count,
                               cudaStream_t st) {
+    if (!S.status) return cudaErrorInvalidValue;  // the staged passes report a stalled copy there
     cudaError_t e = scatter_smem_attr();
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(S.ghist, 0, sizeof(uint32_t) * kPasses * 256, st);
     if (e != cudaSuccess) return e;
-    const int grid = sm_count * 4;
-    k_make_keys<<<grid, kSortThreads, 0, st>>>(S);
+    k_make_keys<<<sm_count * 4, kSortThreads, 0, st>>>(S);
     k_plan<<<1, kPasses * 32, 0, st>>>(S);
     for (int p = 0; p < kPasses; ++p) {
         const int tg = (int)(S.max_tiles < (unsigned long long)sm_count * 8 ? S.max_tiles : (unsigned long long)sm_count * 8);
         k_tile_hist<<<tg, kSortThreads, 0, st>>>(S, p);
         k_digit_scan<<<256, 1024, 0, st>>>(S, p);
-        k_scatter<<<tg, kSortThreads, kScatterSmem, st>>>(S, p);
+        k_scatter<true><<<tg, kSortThreads, kScatterSmemStaged, st>>>(S, p);
     }
+    const int grid = sm_count * 4;
     k_gather<<<grid, 256, 0, st>>>(S, out);
     // a cluster's flags are written by the thread at its start, possibly past
     // its own grid-stride range: clear them all before the flag kernel

@@ -59,8 +59,8 @@ __global__ void k_noalloc_set_n(unsigned long long *n_slot, unsigned long long n
 __global__ void k_noalloc_out(SortDev S, uint64_t *__restrict__ t_out, uint32_t *__restrict__ perm_out) {
     const unsigned long long n = *S.n_in;
     const int fin = S.plan[16];
-    const uint64_t *k = S.keys[fin];
-    const uint32_t *v = S.vals[fin];
+    const uint64_t *k = fin ? S.keys[1] : S.keys[0];
+    const uint32_t *v = fin ? S.vals[1] : S.vals[0];
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         t_out[i] = k[i];
