@@ -128,11 +128,11 @@ class Clocks:
 # were taken on: the entry carries their SHA-1, and `traffic` is reported as null
 # once any transport source differs.
 TRANSPORT_SOURCES = ("device.cuh", "transport.cuh", "transport.cu", "transport_cta.cu")
-TRANSPORT_TRAFFIC = dict(sha1="87e57fcd9aa7cb59d899026efddc142b5f3510ae", bytes_per_pair=8.403,
+TRANSPORT_TRAFFIC = dict(sha1="28a8dadaa6a6fbf2b2581aa848d1c05d23eb668d", bytes_per_pair=8.408,
                          capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
 # The same for the digitizer back end (make_keys .. job_stats of one step), per single.
 DIGITIZER_SOURCES = ("device.cuh", "sort.cu")
-DIGITIZER_TRAFFIC = dict(sha1="9db5c407da2338e68a7faa3e663ec2cacd980dc3", bytes_per_single=530.1,
+DIGITIZER_TRAFFIC = dict(sha1="e89c00f723ab94c4c2a9e21ce83ac296c1ea3af2", bytes_per_single=528.7,
                          capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
 
 
@@ -141,7 +141,8 @@ DIGITIZER_TRAFFIC = dict(sha1="9db5c407da2338e68a7faa3e663ec2cacd980dc3", bytes_
 # issue-active fraction of the schedulers, SIMT efficiency (thread
 # instructions per warp instruction / 32), warp instructions per pair.
 # Reported while the transport code is the captured one, null otherwise.
-TRANSPORT_ISSUE = dict(sha1="87e57fcd9aa7cb59d899026efddc142b5f3510ae", issue_active=0.4947, simt_efficiency=0.5803, warp_inst_per_pair=142.2,
+TRANSPORT_ISSUE = dict(sha1="28a8dadaa6a6fbf2b2581aa848d1c05d23eb668d", issue_active=0.4943, simt_efficiency=0.5803,
+                       warp_inst_per_pair=142.2,
                        capture="profiles/k_transport_cta_sweep_position_2e6.md")
 
 
