@@ -429,6 +429,22 @@ def test_coincidence_policy_brute_force(oracle):
         assert got == brute_force_coincidences(t, panel, 2000), trial
 
 
+def test_window_edges(oracle):
+    """The window [t, t + tau] is closed at both ends (the reading the sorter
+    follows); a third single on the far edge makes a multiple; a single just
+    past it opens the next window."""
+    def count(times, panels):
+        n = len(times)
+        s = np.zeros(n, dtype=[("t_ps", "<u8"), ("unit", "<i4"), ("panel", "<i4"), ("h", "<u8")])
+        s["t_ps"], s["panel"], s["unit"], s["h"] = times, panels, np.array(panels) * 10, np.arange(n)
+        return len(oracle.coincidences(s, 2.0)[1])
+    assert count([1000, 3000], [0, 1]) == 1
+    assert count([1000, 3001], [0, 1]) == 0
+    assert count([1000, 2000, 3000], [0, 1, 2]) == 0
+    assert count([1000, 3000, 3001, 5001], [0, 1, 2, 3]) == 2
+    assert count([1000, 3000], [1, 1]) == 0
+
+
 def _renewal_coincidences(rate_per_ps, tau_ps, span_ps, p_diff):
     """Expected coincidences of the single-window, kill-multiples sorter on a
     Poisson stream: windows open at rate rate/(1 + rate tau) (the stream is
