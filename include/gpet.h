@@ -46,7 +46,10 @@ extern "C" {
 #define GPET_ERR_INVALID_ARG (-1) /* a NULL pointer, a negative size, an out-of-range field */
 #define GPET_ERR_GEOMETRY (-2)    /* panels overlap, a layer leaves its module, zero pitch  */
 #define GPET_ERR_OOM (-3)         /* a device or host allocation failed                    */
-#define GPET_ERR_CUDA (-4)        /* a CUDA runtime call failed (message has the CUDA text)  */
+#define GPET_ERR_CUDA (-4)        /* a CUDA runtime call failed (message has the CUDA text),  */
+                                  /* or a kernel reported an internal error: a history in   */
+                                  /* a phase no event handles, or a time-sort tile copy     */
+                                  /* that did not land within its bounded wait             */
 #define GPET_ERR_TIMEOUT (-5)     /* a device loop hit its iteration cap (steps, trials)     */
 #define GPET_ERR_OVERFLOW (-6)    /* an output buffer was too small; the run is flagged      */
 #define GPET_ERR_BUSY (-7)        /* server admission denied (non-blocking submit)          */
