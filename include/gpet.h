@@ -208,7 +208,9 @@ int gpet_load_phantom(gpet_scanner *sc, int32_t nx, int32_t ny, int32_t nz, cons
  * opt->stream and synchronises it.  On success *out holds the result.
  * n_decays must be >= 1, and the acquisition n_decays / activity_bq below
  * 4000 s (time stamps in ps share a 64-bit sort key with the job index, which
- * leaves 2^52 ps, about 4500 s): GPET_ERR_INVALID_ARG otherwise.  GPET_ERR_TIMEOUT when a photon
+ * leaves 2^52 ps, about 4500 s): GPET_ERR_INVALID_ARG otherwise.  One launch holds at most
+ * 2^31 - 1 singles (coincidences index them with int32): GPET_ERR_OVERFLOW
+ * beyond, and the run is to be split by history range.  GPET_ERR_TIMEOUT when a photon
  * exceeded 1000 Woodcock steps in one region or 1000 Klein-Nishina trials
  * (the photon is dropped, nothing waits); the run's other outputs are not
  * returned. */

@@ -47,6 +47,11 @@ int gpet_make_job(const gpet_scanner *sc, const gpet_source *src, const gpet_dig
 
 namespace gpet {
 
+// Most singles one launch holds: coincidences index the time-ordered singles
+// with int32 (GPET_COINC_A/B), and the sort's indices and scatter positions
+// are 32-bit.  Larger runs are split by history range or into fewer jobs.
+constexpr uint64_t kMaxSinglesPerLaunch = 0x7FFFFFFFull;
+
 // capacities of one run's output buffers
 struct RunCaps {
     uint64_t singles = 0, hits = 0, ovf = 0;

@@ -118,11 +118,12 @@ int run_plan(Run &R) {
     for (int j = 0; j < nj; ++j)
         R.chunk_start[j + 1] = R.chunk_start[j] + (R.jobs[j].n_hist + cs - 1) / cs;
 
-    const uint64_t cap = std::max<uint64_t>(R.caps.singles, 1);
+    // the first guess may exceed the launch limit; the device counts past the
+    // capacity, so a run with more singles than the limit is still detected
+    const uint64_t cap = std::min<uint64_t>(std::max<uint64_t>(R.caps.singles, 1), kMaxSinglesPerLaunch);
     const uint64_t hcap = R.keep_hits ? std::max<uint64_t>(R.caps.hits, 1) : 0;
     const uint64_t ocap = std::max<uint64_t>(R.caps.ovf, 1);
     const uint64_t tiles = (cap + 4095) / 4096;
-    if (cap >= 0xFFFFFFFFull) return gpet_fail(GPET_ERR_INVALID_ARG, "more than 2^32 singles per launch");
 
     Carver cv;
     // zeroed before every launch
@@ -370,7 +371,7 @@ Run::~Run() {
 }
 
 size_t run_footprint(uint64_t total_decays, int64_t total_crystals, int n_jobs, size_t n_geoms, bool keep_hits) {
-    const uint64_t cap = std::max<uint64_t>(65536, total_decays * 6 / 10);
+    const uint64_t cap = std::min<uint64_t>(std::max<uint64_t>(65536, total_decays * 6 / 10), kMaxSinglesPerLaunch);
     const uint64_t hcap = keep_hits ? std::max<uint64_t>(65536, total_decays * 5 / 2) : 0;
     const uint64_t ocap = std::max<uint64_t>(4096, total_decays / 256);
     const uint64_t tiles = (cap + 4095) / 4096;
@@ -393,6 +394,11 @@ int run_with_retry(Run &R) {
         st = run_plan(R);
         if (st == GPET_OK) st = run_enqueue(R);
         if (st == GPET_OK) st = run_collect(R);
+        if (st == GPET_ERR_OVERFLOW && R.h_hdr.n_singles > kMaxSinglesPerLaunch) {
+            st = gpet_fail(GPET_ERR_OVERFLOW, "%llu singles in one launch, more than %llu: split the run",
+                           R.h_hdr.n_singles, (unsigned long long)kMaxSinglesPerLaunch);
+            break;
+        }
         if (st == GPET_ERR_OVERFLOW && attempt == 0 && !(R.h_hdr.status & kStatusOverflow)) {
             // the device counters kept counting past the capacities: re-run with exact sizes
             R.caps.singles = std::max<uint64_t>(R.caps.singles, R.h_hdr.n_singles + 1024);
