@@ -445,7 +445,8 @@ extern "C" int gpet_load_phantom(gpet_scanner *sc, int32_t nx, int32_t ny, int32
         e = cudaMemcpy(sc->ph_cdf, cdf.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { free_phantom(sc); return gpet_cuda_fail(e, "cudaMemcpy(activity)"); }
         // guide table: guide[k] = first voxel whose prefix sum lies in bucket >= k
-        if (total > 0.0) {
+        // (int32 entries: a grid of 2^31 voxels or more is searched without it)
+        if (total > 0.0 && n <= (int64_t)INT32_MAX) {
             const int32_t G = (int32_t)std::min<int64_t>(65536, std::max<int64_t>(1, n));
             const double gscale = (double)G / total;
             std::vector<int32_t> guide((size_t)G, (int32_t)(n - 1));
