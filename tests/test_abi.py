@@ -127,6 +127,44 @@ def test_phantom_must_clear_posed_panels(G):
         L.gpet_destroy_scanner(h)
 
 
+def test_phantom_validation(G):
+    """gpet_load_phantom's argument checks, all before any device work: an
+    empty grid, a material count outside [1, 8], a non-positive voxel, a voxel
+    naming a missing material, a negative or non-finite activity
+    (GPET_ERR_INVALID_ARG), and a grid reaching past the ring's inner radius
+    (GPET_ERR_GEOMETRY)."""
+    import ctypes as C
+    import numpy as np
+    L = G.load()
+    h = C.c_void_p()
+    assert L.gpet_create_scanner(C.byref(G.scanner_desc(W.config1_scanner())), C.byref(h)) == 0
+    u8 = C.POINTER(C.c_uint8)
+    f32 = C.POINTER(C.c_float)
+    try:
+        mats = G._materials([W.AIR, W.WATER])
+        ids = np.ones(27, dtype=np.uint8)
+        act = np.ones(27, dtype=np.float32)
+        vox = (C.c_double * 3)(1.0, 1.0, 1.0)
+        org = (C.c_double * 3)(-1.5, -1.5, -1.5)
+
+        def load(nx=3, voxel=vox, origin=org, i=ids, a=act, nm=2):
+            return L.gpet_load_phantom(h, nx, 3, 3, voxel, origin, i.ctypes.data_as(u8),
+                                       None if a is None else a.ctypes.data_as(f32), nm, mats)
+        assert load(nx=0) == -1
+        assert load(nm=0) == -1 and load(nm=9) == -1
+        assert load(voxel=(C.c_double * 3)(1.0, 0.0, 1.0)) == -1
+        bad = ids.copy()
+        bad[13] = 2
+        assert load(i=bad) == -1 and "voxel 13" in L.gpet_last_error().decode()
+        for v in (-1.0, float("nan"), float("inf")):
+            a = act.copy()
+            a[5] = v
+            assert load(a=a) == -1
+        assert load(origin=(C.c_double * 3)(38.0, 0.0, 0.0)) == -2   # reaches x = 41: C1 ring radius 40 mm
+    finally:
+        L.gpet_destroy_scanner(h)
+
+
 def test_crystal_count_matches_oracle(G, oracle):
     for sc in (W.config1_scanner(), W.config2_scanner("B"), W.config3_scanner(), W.h2rspet("2CL")):
         h = C.c_void_p()
