@@ -437,7 +437,9 @@ int gpet_server_submit(gpet_server *s, gpet_scanner *sc, const gpet_source *src,
                        uint64_t n_decays, uint64_t seed, int32_t block, uint64_t *req_id);
 /* *out = NULL while the request runs; its result (ownership passes to the
  * caller, latency in gpet_counts.latency_ms) once done; the request's error
- * code if it failed.  A taken request id is forgotten. */
+ * code if it failed.  A taken request id is forgotten.  wait blocks until the
+ * request is done; if another caller takes the same id meanwhile, wait
+ * returns GPET_ERR_INVALID_ARG. */
 int gpet_server_poll(gpet_server *s, uint64_t req_id, gpet_result **out);
 int gpet_server_wait(gpet_server *s, uint64_t req_id, gpet_result **out);
 int gpet_server_stats_get(gpet_server *s, gpet_server_stats *out);

@@ -258,9 +258,15 @@ extern "C" int gpet_server_wait(gpet_server *S, uint64_t req_id, gpet_result **o
     std::unique_lock<std::mutex> lk(S->core->mu);
     auto it = S->reqs.find(req_id);
     if (it == S->reqs.end()) return gpet_fail(GPET_ERR_INVALID_ARG, "unknown request %llu", (unsigned long long)req_id);
-    Req *r = it->second;
-    S->core->done_cv.wait(lk, [r] { return r->done; });
-    return take_result(S, S->reqs.find(req_id), out);
+    // Re-find the request after every wake-up: another caller polling or
+    // waiting on the same id may have taken (and freed) it meanwhile.
+    S->core->done_cv.wait(lk, [&] {
+        it = S->reqs.find(req_id);
+        return it == S->reqs.end() || it->second->done;
+    });
+    if (it == S->reqs.end())
+        return gpet_fail(GPET_ERR_INVALID_ARG, "request %llu was taken by another caller", (unsigned long long)req_id);
+    return take_result(S, it, out);
 }
 
 extern "C" int gpet_server_stats_get(gpet_server *S, gpet_server_stats *out) {

@@ -86,3 +86,30 @@ def test_admission_by_footprint(G):
     assert st["completed"] == len(ids)
     assert st["rejected"] == busy and busy > 0
     srv.close()
+
+
+def test_two_waiters_on_one_request(G):
+    """Two callers wait on the same request: one takes the result, the other
+    is told the id was taken (GPET_ERR_INVALID_ARG), and nothing reads a
+    freed request."""
+    sc = G.Scanner(W.config2_scanner("A"))
+    srv = G.Server(hbm_budget_bytes=8 * 10**9, workers=1)
+    rid = srv.submit(sc, W.point_source(), W.digitizer(), 2 * 10**6, 5)
+    got, errs = [], []
+
+    def waiter():
+        try:
+            got.append(srv.wait(rid))
+        except G.GpetError as e:
+            errs.append(e.code)
+
+    ths = [threading.Thread(target=waiter) for _ in range(2)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    assert len(got) == 1 and errs == [-1]
+    assert got[0].counts()["singles"] > 0
+    got[0].free()
+    srv.close()
+    sc.close()
