@@ -236,6 +236,13 @@ double or_mu_total(const om_material *m, double e_kev) {
     return or_mu_photo(m, e_kev) + or_mu_compton(m, e_kev);
 }
 
+/* the kind of a real collision (Sec. 2.1): photoelectric with probability
+ * mu_pe(E) / mu_total(E) (mu_m = mu_total(E) of the material), decided by the
+ * uniform u; Compton otherwise */
+static int or_is_photo(const om_material *m, double e_kev, double mu_m, double u) {
+    return u * mu_m < or_mu_photo(m, e_kev);
+}
+
 /* Kahn's rejection sampling of the Klein-Nishina distribution (Kahn 1954, as
  * written in the Monte Carlo transport literature).  Returns the number of
  * trials used, fills eta - 1 = E/E' - 1 (>= 0).  Draws block (h, tag, gamma,
@@ -629,7 +636,7 @@ static int or_transport_photon(const or_ctx *C, uint64_t h, uint32_t gamma, doub
             double mu_m = or_mu_total(m, E);
             if (or_uniform(r[1]) * mu_maj >= mu_m) continue;          /* virtual */
             en->ph_real++;
-            if (or_uniform(r[2]) * mu_m < or_mu_photo(m, E)) {        /* photoelectric */
+            if (or_is_photo(m, E, mu_m, or_uniform(r[2]))) {          /* photoelectric */
                 en->phantom += E;
                 return OR_OK;
             }
@@ -685,7 +692,7 @@ static int or_transport_photon(const or_ctx *C, uint64_t h, uint32_t gamma, doub
             if (or_uniform(r[1]) * mu_maj >= mu_m) continue;           /* virtual */
             double dep;
             int dead = 0;
-            if (or_uniform(r[2]) * mu_m < or_mu_photo(m, E)) {         /* photoelectric */
+            if (or_is_photo(m, E, mu_m, or_uniform(r[2]))) {           /* photoelectric */
                 dep = E;
                 dead = 1;
             } else {                                                   /* Compton */
@@ -1010,6 +1017,19 @@ int64_t or_coincidences(int64_t n, const uint64_t *t_ps, const int32_t *unit, co
 /* ------------------------------------------------------------------------- */
 /* small entry points used by the pins                                        */
 /* ------------------------------------------------------------------------- */
+/* photoelectric decisions of n real collisions in material m at energy E, with
+ * the uniforms of the detector-step blocks of histories h0 .. h0 + n - 1 */
+int64_t or_photo_count(const om_material *m, double e_kev, uint64_t seed, uint64_t h0, int64_t n) {
+    const double mu_m = or_mu_total(m, e_kev);
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t r[4];
+        or_draw(seed, h0 + (uint64_t)i, OR_TAG_DETECTOR, 0u, 0u, 0u, r);
+        c += or_is_photo(m, e_kev, mu_m, or_uniform(r[2]));
+    }
+    return c;
+}
+
 int or_kahn_batch(uint64_t seed, uint64_t h0, int64_t n, double e_kev, double *cos_theta, double *e_out,
                   int32_t *trials) {
     for (int64_t i = 0; i < n; ++i) {

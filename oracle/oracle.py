@@ -129,6 +129,8 @@ def lib():
             L.or_coincidences.argtypes = [C.c_int64, _P, _P, _P, _P, C.c_uint64, _P, _P]
             L.or_coincidences.restype = C.c_int64
             L.or_kahn_batch.argtypes = [C.c_uint64, C.c_uint64, C.c_int64, C.c_double, _P, _P, _P]
+            L.or_photo_count.restype = C.c_int64
+            L.or_photo_count.argtypes = [C.POINTER(Material), C.c_double, C.c_uint64, C.c_uint64, C.c_int64]
             L.or_flight_batch.argtypes = [C.POINTER(Scanner), C.c_int64, _P, _P, _P, _P]
             L.or_locate_batch.argtypes = [C.POINTER(Scanner), C.c_int, C.c_int64, _P, _P]
             L.or_panel_extent.argtypes = [C.POINTER(Scanner), _P]
@@ -298,6 +300,13 @@ def mu(material, e_kev, kind="total"):
     m = Material(material["mu_total_511_cm"], material["photo_frac_511"], material.get("electron_density_cm3", 0.0))
     f = dict(total=lib().or_mu_total, photo=lib().or_mu_photo, compton=lib().or_mu_compton)[kind]
     return float(f(C.byref(m), float(e_kev)))
+
+
+def photo_count(material, e_kev, seed, h0, n):
+    """Photoelectric decisions of n real collisions at energy e_kev (the
+    transport's own branch function on its own draws)."""
+    m = _materials([material])
+    return int(lib().or_photo_count(m, float(e_kev), int(seed), int(h0), int(n)))
 
 
 def kahn(seed, h0, n, e_kev):

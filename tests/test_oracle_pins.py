@@ -54,6 +54,24 @@ def test_sigma_kn_equals_integral_of_differential(oracle, e):
     assert oracle.sigma_kn(e) == pytest.approx(2 * math.pi * val, rel=1e-9, abs=0)
 
 
+@pytest.mark.parametrize("e", [511.0, 300.0, 200.0, 100.0])
+def test_photoelectric_share_follows_the_energy(oracle, e):
+    """The kind of a real collision at energy E: photoelectric with
+    probability mu_pe(E) / mu_total(E), where mu_pe scales as (511/E)^3 from
+    its 511 keV value and the Compton part as the Klein-Nishina total cross
+    section (here from a quadrature of dsigma/dOmega, not the oracle's closed
+    form).  Binomial test on the transport's own branch function; catches a
+    share frozen at its 511 keV value or a wrong power of the E^-3 law."""
+    mat = W.LYSO
+    n = 200_000
+    sig = lambda en: 2 * math.pi * integrate.quad(lambda c: kn_dsigma_domega(en, c), -1.0, 1.0, epsrel=1e-12)[0]
+    mu_pe = mat["mu_total_511_cm"] * mat["photo_frac_511"] * (511.0 / e) ** 3
+    mu_c = mat["mu_total_511_cm"] * (1.0 - mat["photo_frac_511"]) * sig(e) / sig(511.0)
+    p = mu_pe / (mu_pe + mu_c)
+    got = oracle.photo_count(dict(mat, electron_density_cm3=0.0), e, 77, 0, n)
+    assert abs(got / n - p) < 5.0 * math.sqrt(p * (1 - p) / n), (got / n, p)
+
+
 def test_sigma_kn_thomson_limit(oracle):
     """sigma -> (8 pi/3) r_e^2 (1 - 2k + 26/5 k^2 - 133/10 k^3 + 1144/35 k^4) at
     low energy.  (Below ~2 keV the closed form loses digits to cancellation in
