@@ -284,6 +284,29 @@ def test_geometric_acceptance_offcentre(oracle):
 # ---------------------------------------------------------------------------
 # hierarchy indexing
 # ---------------------------------------------------------------------------
+def test_flight_enters_the_nearest_panel(oracle):
+    """Two posed heads one behind the other on the +x axis (the far one listed
+    first): a ray meets the near head first, from either side, and a ray
+    that misses the near head meets the far one.  Slab-test distances are
+    exact.  Catches a flight that returns the first listed or the farthest
+    panel it crosses."""
+    base = W.scanner(2, 45.0, [W.layer(8, 8, 2.0, 0.1, 12.0)])
+    sc = W.with_poses(base, np.stack([W.pose((1, 0, 0), (0, 1, 0), (70.0, 0.0, 0.0)),
+                                      W.pose((1, 0, 0), (0, 1, 0), (45.0, 0.0, 0.0))]))
+    x = np.array([[0.0, 0.0, 0.0], [60.0, 1.0, -2.0], [100.0, 0.5, 0.5], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    d = np.array([[1.0, 0.0, 0.0], [1.0, 0.0, 0.0], [-1.0, 0.0, 0.0], [1.0, 0.1, 0.0], [1.0, 0.0, -0.3]])
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    pn, ti = oracle.flight(sc, x, d)
+    # near head: x in [45, 57]; far head: x in [70, 82]; both 16 mm wide in u and v
+    assert list(pn[:3]) == [1, 0, 0]
+    np.testing.assert_allclose(ti[:3], [45.0, 10.0, 18.0], atol=1e-12)
+    # slope 0.1 in y: at x = 45 the ray is at y = 4.5, inside the near head
+    assert pn[3] == 1 and ti[3] == pytest.approx(45.0 * math.sqrt(1.01), abs=1e-12)
+    # slope -0.3 in z: it passes below the near head (z = -13.5 at x = 45) and
+    # below the far one (z = -21 at x = 70): no panel
+    assert pn[4] == -1
+
+
 def test_locate_lattice_points(oracle):
     """Crystal centres locate to their own (layer, module, crystal) id; points in
     the inter-crystal gaps, the reflector gap and the module gap are interval."""
@@ -648,6 +671,57 @@ def test_phantom_no_scatter_fraction(oracle):
     p_exp = np.exp(-0.0096 * chord).mean()
     assert abs(p_obs - p_exp) < 4 * math.sqrt(p_exp * (1 - p_exp) / n) + 3e-4, (p_obs, p_exp)
     np.testing.assert_allclose(r["balance"], 1022.0, atol=1e-9)
+
+
+def test_phantom_single_scatter_escape(oracle):
+    """Pencil pair from the centre of a 100 mm water cube (Compton only): a
+    photon has exactly one real phantom interaction with probability
+    p1 = P(first collision) x E[exp(-mu(E') L')], over the first-collision
+    depth, the Klein-Nishina angle at 511 keV and the exit chord L' of the
+    scattered photon, with mu(E') = mu(511) sigma(E') / sigma(511).  Computed
+    here by an independent numpy Monte Carlo (its own KN rejection sampler and
+    box chords); a history's count is 1 with probability 2 p0 p1.  Catches a
+    Woodcock majorant or cross section taken at the wrong energy after a
+    scatter, which the unscattered fraction cannot see."""
+    half = 50.0
+    ph = dict(nx=10, ny=10, nz=10, voxel=(10.0, 10.0, 10.0), origin=(-half, -half, -half),
+              material=np.ones((10, 10, 10), np.uint8), activity=None, materials=[W.AIR, W.WATER])
+    sc = W.scanner(8, 80.0, [W.layer(8, 8, 1.6, 0.1, 10.0)])
+    n = 400_000
+    r = oracle.simulate(sc, W.pencil_source(direction=(1, 0, 0)), W.digitizer(), n, seed=31, phantom=ph,
+                        threads=8, tallies=False, phantom_real=True)
+    cnt = r["phantom_real"]
+    mu511 = 0.096 / 10.0                        # 1/mm
+    p0 = math.exp(-mu511 * half)
+    # independent Monte Carlo of p1
+    rng = np.random.default_rng(5)
+    m = 2_000_000
+    s = -np.log(1.0 - rng.uniform(size=m) * (1.0 - p0)) / mu511          # first collision depth in [0, half)
+    k = 511.0 / MEC2
+    ct = np.empty(0)
+    fmax = kn_dsigma_domega(511.0, 1.0)
+    while len(ct) < m:
+        c = rng.uniform(-1.0, 1.0, 2 * m)
+        ct = np.concatenate([ct, c[rng.uniform(size=2 * m) * fmax < kn_dsigma_domega(511.0, c)]])
+    ct = ct[:m]
+    st = np.sqrt(1.0 - ct * ct)
+    phi = rng.uniform(0.0, 2 * math.pi, m)
+    d = np.stack([ct, st * np.cos(phi), st * np.sin(phi)], 1)
+    x = np.stack([s, np.zeros(m), np.zeros(m)], 1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = np.min(np.where(d > 0, (half - x) / d, np.where(d < 0, (-half - x) / d, np.inf)), axis=1)
+    e1 = 511.0 / (1.0 + k * (1.0 - ct))
+    grid = np.linspace(160.0, 512.0, 353)
+    sig = np.array([integrate.quad(lambda c: kn_dsigma_domega(e, c), -1, 1, epsrel=1e-10)[0] for e in grid])
+    sig511 = integrate.quad(lambda c: kn_dsigma_domega(511.0, c), -1, 1, epsrel=1e-10)[0]
+    mu1 = mu511 * np.interp(e1, grid, sig) / sig511
+    surv = np.exp(-mu1 * t)
+    p1 = (1.0 - p0) * surv.mean()
+    p1_err = (1.0 - p0) * surv.std() / math.sqrt(m)
+    want = 2.0 * p0 * p1
+    got = (cnt == 1).mean()
+    assert abs((cnt == 0).mean() - p0 * p0) < 5.0 * math.sqrt(p0 * p0 * (1 - p0 * p0) / n)
+    assert abs(got - want) < 5.0 * math.sqrt(want * (1 - want) / n) + 2 * p0 * 5.0 * p1_err, (got, want)
 
 
 def test_decay_sampling_follows_activity(oracle):
