@@ -724,6 +724,27 @@ def test_phantom_single_scatter_escape(oracle):
     assert abs(got - want) < 5.0 * math.sqrt(want * (1 - want) / n) + 2 * p0 * 5.0 * p1_err, (got, want)
 
 
+def test_phantom_material_layout(oracle):
+    """Voxel materials are indexed x fastest, then y, then z (the layout the
+    ABI documents).  A 4 x 2 x 2 grid of 10 mm voxels holds an absorber
+    (photoelectric only, 0.5/cm) only where ix >= 2, iy = 1 and iz = 1; a pencil
+    pair from the centre along x crosses 20 mm of it with photon 0 and none
+    with photon 1, so a pair is untouched with probability exp(-1).  Catches a
+    transposed material index (which moves the absorber off the beam)."""
+    absorber = dict(name="absorber", mu_total_511_cm=0.5, photo_frac_511=1.0, electron_density_cm3=0.0)
+    mat = np.zeros((2, 2, 4), np.uint8)          # [iz][iy][ix]
+    mat[1, 1, 2:] = 1
+    ph = dict(nx=4, ny=2, nz=2, voxel=(10.0, 10.0, 10.0), origin=(-20.0, -10.0, -10.0), material=mat,
+              activity=None, materials=[W.AIR, absorber])
+    n = 200_000
+    r = oracle.simulate(W.config1_scanner(), W.pencil_source(direction=(1, 0, 0)), W.digitizer(), n, seed=8,
+                        phantom=ph, threads=8, tallies=False, phantom_real=True)
+    p = math.exp(-0.5 * 2.0)
+    got = (r["phantom_real"] == 0).mean()
+    assert abs(got - p) < 5.0 * math.sqrt(p * (1 - p) / n), (got, p)
+    assert r["phantom_real"].max() == 1                 # the absorber ends photon 0; photon 1 meets none
+
+
 def test_decay_sampling_follows_activity(oracle):
     """Decay points: voxel counts follow the activity map (chi-square), the
     point is uniform inside its voxel, directions are isotropic, times uniform."""
