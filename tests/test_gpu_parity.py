@@ -95,6 +95,11 @@ CASES["ring12_4layer"] = (W.four_layer_scanner, lambda: W.point_source((6.0, 2.0
 CASES["box4_posed_module_readout"] = (lambda: W.box_scanner(readout_level=W.READOUT_MODULE),
                                       lambda: W.point_source((-3.0, 5.0, -1.0)), None, 100_000, 49)
 
+# three modules across each panel with 4 mm transaxial gaps, and an axial 2 mm gap
+CASES["ring6_3x2_module_gaps"] = (lambda: W.scanner(6, 60.0, [W.layer(8, 8, 2.0, 0.2, 10.0)], modules_u=3,
+                                                    modules_v=2, module_gap_u=4.0, module_gap_v=2.0),
+                                  lambda: W.point_source((7.0, -4.0, 3.0)), None, 150_000, 53)
+
 KERNELS = {"loop": 1, "wave": 2, "cta": 3}
 
 

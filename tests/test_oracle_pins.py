@@ -658,6 +658,28 @@ def test_module_gap_is_interval(oracle):
     assert abs(frac - want) < 4 * math.sqrt(want * (1 - want) / n)
 
 
+def test_transaxial_module_gap(oracle):
+    """Three modules across the panel with 4 mm gaps between them: the panel is
+    3 x 16 + 2 x 4 = 56 mm wide, a point in a gap is interval material, the
+    modules sit where the widths put them, and crystals fill 3 x 64 x 1.8^2 mm^2
+    of the 56 x 16 mm^2 face.  Catches a panel width or module origin that
+    drops the transaxial gaps."""
+    sc = W.scanner(6, 60.0, [W.layer(8, 8, 2.0, 0.2, 10.0)], modules_u=3, module_gap_u=4.0)
+    U, V, Wd = oracle.panel_extent(sc)
+    assert (U, V, Wd) == pytest.approx((56.0, 16.0, 10.0), abs=1e-12)
+    got = oracle.locate(sc, 0, [(5.0, -10.0, 0.5), (5.0, -7.5, 0.5), (5.0, 27.5, 0.5), (5.0, -27.5, 0.5)])
+    assert got[0, 2] == -1 and got[0, 3] == 0
+    assert list(got[1:, 1]) == [1, 2, 0] and np.all(got[1:, 2] >= 0)
+    # crystal columns: first of module 1, last of module 2, first of module 0
+    assert list(got[1:, 2] % 8) == [0, 7, 0]
+    rng = np.random.default_rng(4)
+    n = 400_000
+    p = np.stack([rng.uniform(0, 10, n), rng.uniform(-U / 2, U / 2, n), rng.uniform(-V / 2, V / 2, n)], 1)
+    frac = (oracle.locate(sc, 0, p)[:, 2] >= 0).mean()
+    want = 3 * 64 * 1.8 ** 2 / (U * V)
+    assert abs(frac - want) < 4 * math.sqrt(want * (1 - want) / n)
+
+
 def box_chord_pairs(lo, hi, n, rng):
     """Independent quadrature: mean of exp(-mu * chord) over uniform points in a
     box and isotropic lines through them (chord = exit distance both ways)."""
