@@ -1,5 +1,7 @@
 """Batched form: many designs and sources in one persistent launch (and its
 CUDA-graph replay) give, job by job, exactly the results of the plain call."""
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -175,3 +177,33 @@ def test_batch_of_more_designs_than_staged_geometries(G):
         r.free()
     for j in jobs:
         j["scanner"].close()
+
+
+def test_batch_job_count(G):
+    """gpet_batch_jobs reports the batch's job count."""
+    sc = G.Scanner(W.config2_scanner("A"))
+    jobs = [dict(scanner=sc, source=W.point_source((0.0, 0.0, z)), digitizer=W.digitizer(), n_decays=200_000,
+                 seed=9 + i) for i, z in enumerate((-5.0, 5.0))]
+    b = G.Batch(jobs)
+    try:
+        n = C.c_int32()
+        assert G.load().gpet_batch_jobs(b._h, C.byref(n)) == 0 and n.value == 2
+    finally:
+        b.close()
+        sc.close()
+
+
+def test_autotune_choice_gives_the_same_results(G):
+    """gpet_autotune times the launch forms on a pilot and returns one of them;
+    a run with the chosen form equals a run with the default one (every form
+    gives the same results).  A seven-panel ring: a design class of its own,
+    so the remembered choice touches no other test."""
+    sc = G.Scanner(W.scanner(7, 50.0, [W.layer(8, 8, 1.6, 0.1, 10.0)]))
+    try:
+        opts, ms = sc.autotune(W.point_source(), W.digitizer(), pilot_decays=100_000)
+        assert opts["kernel"] in (1, 2, 3) and ms > 0
+        a = sc.simulate(W.point_source((1.0, 2.0, 0.0)), W.digitizer(), 200_000, 6, **opts)
+        b = sc.simulate(W.point_source((1.0, 2.0, 0.0)), W.digitizer(), 200_000, 6, kernel=2)
+        assert_same(canon(a), canon(b))
+    finally:
+        sc.close()
