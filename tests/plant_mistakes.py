@@ -138,30 +138,36 @@ def apply(text, edits):
     return text
 
 
-def main(names):
+def run(name):
+    """Build the oracle with mistake `name` planted and return the pins that fail."""
     c_src = open(os.path.join(ROOT, "oracle", "gpet_oracle.c")).read()
     py_src = open(os.path.join(ROOT, "oracle", "oracle.py")).read()
+    edits = MUTS[name]
+    d = os.path.join(ROOT, "tests", "_mutants", name)
+    os.makedirs(d, exist_ok=True)
+    with open(os.path.join(d, "oracle.py"), "w") as f:
+        f.write(apply(py_src, [e for e in edits if len(e) > 3 and e[3] == "py"]))
+    with open(os.path.join(d, "gpet_oracle.c"), "w") as f:
+        f.write(apply(c_src, [e for e in edits if not (len(e) > 3 and e[3] == "py")]))
+    spec = importlib.util.spec_from_file_location("mutant_" + name, os.path.join(d, "oracle.py"))
+    O = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(O)
+    O.build(force=True)
+    failed = []
+    for cname, f, kw in cases():
+        try:
+            f(O, **kw) if "oracle" in inspect.signature(f).parameters else f(**kw)
+        except AssertionError:
+            failed.append(cname)
+        except Exception as e:  # a crash is caught too
+            failed.append(f"{cname}<{type(e).__name__}>")
+    return failed
+
+
+def main(names):
     for name in names or sorted(MUTS):
-        edits = MUTS[name]
-        d = os.path.join(ROOT, "tests", "_mutants", name)
-        os.makedirs(d, exist_ok=True)
-        with open(os.path.join(d, "oracle.py"), "w") as f:
-            f.write(apply(py_src, [e for e in edits if len(e) > 3 and e[3] == "py"]))
-        with open(os.path.join(d, "gpet_oracle.c"), "w") as f:
-            f.write(apply(c_src, [e for e in edits if not (len(e) > 3 and e[3] == "py")]))
-        spec = importlib.util.spec_from_file_location("mutant_" + name, os.path.join(d, "oracle.py"))
-        O = importlib.util.module_from_spec(spec)
-        spec.loader.exec_module(O)
-        O.build(force=True)
         t0 = time.time()
-        failed = []
-        for cname, f, kw in cases():
-            try:
-                f(O, **kw)
-            except AssertionError:
-                failed.append(cname)
-            except Exception as e:  # a crash is caught too
-                failed.append(f"{cname}<{type(e).__name__}>")
+        failed = run(name)
         print(f"{name:26s} caught by {len(failed)}: {failed[:4]} ({time.time() - t0:.0f} s)", flush=True)
 
 
