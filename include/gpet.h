@@ -179,7 +179,8 @@ typedef struct gpet_result gpet_result;
 int gpet_create_scanner(const gpet_scanner_desc *desc, gpet_scanner **out);
 void gpet_destroy_scanner(gpet_scanner *sc);
 
-/* Number of crystals of the scanner (global crystal ids are 0 .. n-1):
+/* Number of crystals of the scanner (crystal identification from the
+ * repetitive structure, Sec. 2.1; global crystal ids are 0 .. n-1):
  * id = (((panel * modules_v + m_v) * modules_u + m_u) * C + layer_offset + i_v * n_u + i_u)
  * with C the crystal count of one module summed over layers. */
 int gpet_scanner_crystals(const gpet_scanner *sc, int64_t *n_crystals);
@@ -201,7 +202,9 @@ int gpet_load_phantom(gpet_scanner *sc, int32_t nx, int32_t ny, int32_t nz, cons
 /* simulation (plain form: one scanner, one source)                          */
 /* ------------------------------------------------------------------------ */
 
-/* Simulate histories 0 .. n_decays-1 of one source with RNG key `seed`.
+/* Simulate histories 0 .. n_decays-1 of one source with RNG key `seed`: the
+ * decays of Sec. 2.3, the transport of Sec. 2.1, and the digitizer and
+ * coincidence sorting of Sec. 2.3.
  * Random numbers come from Philox4x32-10 addressed by (history, region,
  * photon, step, sub-draw), so any history is reproducible on its own.
  * Enqueues transport, digitizer, time sort and coincidence sorting on
@@ -236,7 +239,10 @@ typedef struct {
 } gpet_counts;
 int gpet_result_counts(const gpet_result *r, gpet_counts *out);
 
-/* Result arrays.  Singles are sorted by time (ties in any order).
+/* Result arrays: the hits and tallies of Sec. 2.1 and the singles and
+ * coincidences of Sec. 2.3.  (The accessors themselves are library
+ * infrastructure; the paper defines no interface.)  Singles are sorted by
+ * time (ties in any order).
  * Coincidence indices copied by gpet_result_copy number the result's own
  * singles; through gpet_result_device_ptr of a batch view they count from the
  * first single of the whole batch. */
@@ -291,7 +297,9 @@ void gpet_result_free(gpet_result *r);
 /* batched form: many designs and sources in one persistent launch           */
 /* ------------------------------------------------------------------------ */
 
-/* A batch runs n_jobs independent simulations -- job j is (scanners[j],
+/* The paper runs one simulation per design (Sec. 3); a batch, which it does
+ * not define, runs several in one launch.
+ * A batch runs n_jobs independent simulations -- job j is (scanners[j],
  * sources[j], digitizers[j], n_decays[j], seeds[j]) exactly as gpet_simulate
  * would run it -- in one persistent transport launch over a shared work
  * queue, one time sort segmented by job and one coincidence pass.  The
@@ -392,7 +400,9 @@ int gpet_sort_times_noalloc(const uint64_t *d_t_in, uint64_t n, uint64_t *d_t_ou
 /* autotuner                                                                 */
 /* ------------------------------------------------------------------------ */
 
-/* Time the candidate launch forms of the transport kernel -- the per-lane
+/* Library infrastructure with no counterpart in the paper: a launch-form
+ * choice for the transport of Sec. 2.1.
+ * Time the candidate launch forms of the transport kernel -- the per-lane
  * event loop, the per-warp wavefront, the CTA-synchronous wavefront at 128,
  * 256 or 512 threads and pool depth 2 or 3 -- on a pilot run
  * (pilot_decays >= 1000, seed)
@@ -408,7 +418,9 @@ int gpet_autotune(gpet_scanner *sc, const gpet_source *src, const gpet_digitizer
 /* serving loop: continuous batching of simulation requests                  */
 /* ------------------------------------------------------------------------ */
 
-/* A server accepts simulation requests from any host thread while earlier
+/* Library infrastructure with no counterpart in the paper: simulations of
+ * Sec. 2.1-2.3 served as requests.
+ * A server accepts simulation requests from any host thread while earlier
  * ones run.  Worker threads (each with its own stream) repeatedly admit the
  * queued requests that fit the device-memory budget, first come first
  * served, and run them together as one batched launch; the batches of
