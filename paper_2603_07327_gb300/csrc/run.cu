@@ -516,7 +516,7 @@ static int result_array(const gpet_result *r, int32_t which, ArrayView &v) {
 
 extern "C" int gpet_result_copy(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes) {
     if (!r || (!dst && cap_bytes)) return gpet_fail(GPET_ERR_INVALID_ARG, "NULL argument");
-    ArrayView v;
+    ArrayView v{nullptr, 0};
     int st = result_array(r, which, v);
     if (st != GPET_OK) return st;
     if (cap_bytes < v.bytes)
@@ -556,7 +556,7 @@ static int copy_run(const gpet_result *r, int32_t which, void *dst, size_t cap_b
     if (R.s_off.size() != nj + 1 || R.c_off.size() != nj + 1)
         return gpet_fail(GPET_ERR_INVALID_ARG, "the run has no collected results");
     const uint64_t ns = R.s_off[nj], nc = R.c_off[nj];
-    ArrayView v;
+    ArrayView v{nullptr, 0};
     switch (which) {
         case GPET_SINGLES_T_PS: v = {R.SD.t, ns * 8}; break;
         case GPET_SINGLES_H: v = {R.SD.h, ns * 8}; break;
@@ -587,7 +587,7 @@ static int copy_run(const gpet_result *r, int32_t which, void *dst, size_t cap_b
 
 extern "C" const void *gpet_result_device_ptr(const gpet_result *r, int32_t which) {
     if (!r) return nullptr;
-    ArrayView v;
+    ArrayView v{nullptr, 0};
     if (result_array(r, which, v) != GPET_OK) return nullptr;
     return v.ptr;
 }
