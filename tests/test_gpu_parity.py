@@ -6,8 +6,6 @@ within 1 ps; blurred energies within 1e-5 relative + 1e-3 keV with window
 flips only at the window edges; coincidences identical outside mismatched
 histories; per-crystal tallies identical outside mismatched histories.
 """
-import math
-
 import numpy as np
 import pytest
 

@@ -3,7 +3,6 @@ every result equals the same request run alone; admission by HBM footprint."""
 import threading
 import time
 
-import numpy as np
 import pytest
 
 import workloads as W
