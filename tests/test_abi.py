@@ -278,3 +278,26 @@ def test_empty_and_out_of_range_sizes_are_refused_on_the_host(G):
     assert _create(G, nine) == -1
     mats = dict(big, materials=big["materials"] + [W.LYSO])
     assert _create(G, mats) == -1
+
+
+def test_no_cpu_fallback_without_a_gpu(G):
+    """On a machine without a usable GPU the compute calls fail with
+    GPET_ERR_CUDA and a message naming the CUDA error; nothing falls back to a
+    CPU path.  (Skipped where a GPU is present.)"""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    sc = G.Scanner(W.config1_scanner())
+    try:
+        with pytest.raises(G.GpetError) as e:
+            sc.simulate(W.point_source(), W.digitizer(), 1000, 1)
+        assert e.value.code == -4 and "cuda" in str(e.value).lower()
+        with pytest.raises(G.GpetError) as e:
+            G.simulate_batch([dict(scanner=sc, source=W.point_source(), digitizer=W.digitizer(), n_decays=1000,
+                                   seed=1)])
+        assert e.value.code == -4
+    finally:
+        sc.close()
