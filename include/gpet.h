@@ -210,8 +210,7 @@ int gpet_load_phantom(gpet_scanner *sc, int32_t nx, int32_t ny, int32_t nz, cons
  * Enqueues transport, digitizer, time sort and coincidence sorting on
  * opt->stream and synchronises it.  On success *out holds the result.
  * n_decays must be >= 1, and the acquisition n_decays / activity_bq below
- * 4000 s (time stamps in ps share a 64-bit sort key with the job index, which
- * leaves 2^52 ps, about 4500 s): GPET_ERR_INVALID_ARG otherwise.  One launch holds at most
+ * 2^62 ps (53 days): GPET_ERR_INVALID_ARG otherwise.  One launch holds at most
  * 2^31 - 1 singles (coincidences index them with int32): GPET_ERR_OVERFLOW
  * beyond, and the run is to be split by history range.  GPET_ERR_TIMEOUT when a photon
  * exceeded 1000 Woodcock steps in one region or 1000 Klein-Nishina trials
@@ -307,7 +306,12 @@ void gpet_result_free(gpet_result *r);
  * gpet_batch_run.  A job's results are identical to gpet_simulate's for the
  * same inputs (every random number is addressed by seed and history id).
  * All arrays: host, n_jobs entries, copied.  Scanners must outlive the batch.
- * n_jobs <= 4095.  opt->stream NULL: the batch creates its own stream. */
+ * n_jobs <= 4095.  opt->stream NULL: the batch creates its own stream.
+ * The time sort orders (job, time) keys of 64 bits whose job field takes the
+ * fewest bits that number the jobs (7 for 65..128 jobs, 12 for 4095): every
+ * job's acquisition must fit in the rest, 2^(64 - bits) ps minus 2^32 ps of
+ * flight time (about 20 h for 256 jobs, 75 min for 4095);
+ * GPET_ERR_INVALID_ARG otherwise, before any device work. */
 typedef struct gpet_batch gpet_batch;
 int gpet_batch_create(int32_t n_jobs, gpet_scanner *const *scanners, const gpet_source *sources,
                       const gpet_digitizer *digitizers, const uint64_t *n_decays, const uint64_t *seeds,
@@ -388,11 +392,16 @@ int gpet_delta_sym(int64_t n, const double *s_a, const double *s_b, double *out)
  *              the sort is stable (equal keys keep their input order)
  *   n          <= 1048576 (2^20); larger n returns GPET_ERR_INVALID_ARG
  *   stream     cudaStream_t; the call is asynchronous on it
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array and overwrites its previous
- * contents, so calls that overlap on the GPU (other streams, other host
- * threads) race: serialise them. */
+ * The first call on a device, made with that device current, is its set-up:
+ * CUDA loads a library's kernels and device arrays lazily, so that call loads
+ * the code it runs and the 24.3 MiB array, which takes device memory then.
+ * Make that first call before the process hands its device memory to another
+ * allocator, and before any stream capture; later calls allocate nothing.
+ * Every call looks up the array's device address afresh (a host-side lookup),
+ * so a cudaDeviceReset, which reloads the array, leaves no stale address.
+ * Every call shares the one array and overwrites its previous contents, so
+ * calls that overlap on the GPU (other streams, other host threads) race:
+ * serialise them. */
 int gpet_sort_times_noalloc(const uint64_t *d_t_in, uint64_t n, uint64_t *d_t_out, uint32_t *d_perm_out,
                             void *stream);
 

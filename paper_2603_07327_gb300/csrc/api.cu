@@ -494,7 +494,9 @@ int gpet_make_job(const gpet_scanner *sc, const gpet_source *src, const gpet_dig
         !(dg->doi_fwhm_mm >= 0.0))
         return gpet_fail(GPET_ERR_INVALID_ARG, "digitizer settings out of range");
     const double span = (double)n_decays / src->activity_bq * 1e12;
-    if (!(span < 4.0e15)) return gpet_fail(GPET_ERR_INVALID_ARG, "acquisition longer than 4000 s (time key limit)");
+    // time stamps are uint64 ps; a launch of several jobs checks that its
+    // longest acquisition also fits beside the job bits of the sort key
+    if (!(span < 0x1p62)) return gpet_fail(GPET_ERR_INVALID_ARG, "acquisition longer than 2^62 ps (53 days)");
     if (src->kind == GPET_SOURCE_PENCIL) {
         const double nn = src->dir[0] * src->dir[0] + src->dir[1] * src->dir[1] + src->dir[2] * src->dir[2];
         if (!(std::fabs(nn - 1.0) < 1e-6)) return gpet_fail(GPET_ERR_INVALID_ARG, "pencil direction must be a unit vector");

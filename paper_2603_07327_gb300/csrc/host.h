@@ -55,6 +55,7 @@ constexpr uint64_t kMaxSinglesPerLaunch = 0x7FFFFFFFull;
 // capacities of one run's output buffers
 struct RunCaps {
     uint64_t singles = 0, hits = 0, ovf = 0;
+    bool guess = true;   // first guesses (clamped to the free device memory), not exact counts
 };
 
 // device header read back after a run (all zeroed before launch)

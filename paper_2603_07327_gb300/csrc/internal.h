@@ -32,7 +32,21 @@ struct SortDev {
     const unsigned long long *n_in;  // device count of unsorted singles
     const RawSingle *in_raw;         // unsorted singles
     int *status;                     // run status word (kStatusSortStall), or NULL: unstaged passes
+    int job_shift;                   // sort key = (job << job_shift) | t_ps; 64: the key is t_ps alone
 };
+
+// Bit position of the job index in the 64-bit sort keys of a launch of n_jobs
+// jobs: the job takes the fewest high bits that number the jobs, the time stamp
+// the rest (64 for one job: the key is the time alone).
+inline int sort_job_shift(int n_jobs) {
+    int bits = 0;
+    while ((1ll << bits) < (long long)n_jobs) ++bits;
+    return 64 - bits;
+}
+// Largest time stamp a key with this shift holds (2^64 - 1 without job bits).
+inline unsigned long long sort_time_limit(int job_shift) {
+    return job_shift >= 64 ? ~0ull : (1ull << job_shift) - 1ull;
+}
 
 // time-ordered singles
 struct SinglesDev {

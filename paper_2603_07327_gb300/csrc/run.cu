@@ -99,6 +99,16 @@ int run_plan(Run &R) {
     const int nj = (int)R.jobs.size();
     if (nj < 1) return gpet_fail(GPET_ERR_INVALID_ARG, "no jobs");
     if (nj > 4095) return gpet_fail(GPET_ERR_INVALID_ARG, "at most 4095 jobs per launch");
+    // sort keys: the job index above the time stamps; every job's latest time
+    // (its span plus the longest flight a uint32 ps offset holds) must fit below it
+    R.S.job_shift = sort_job_shift(nj);
+    for (int j = 0; j < nj; ++j)
+        if (R.jobs[j].t_span_ps > sort_time_limit(R.S.job_shift) - 0xFFFFFFFFull)
+            return gpet_fail(GPET_ERR_INVALID_ARG,
+                             "job %d: acquisition of %.0f s does not fit beside %d job bits of the time key "
+                             "(at most %.0f s in a launch of %d jobs): use fewer jobs per launch",
+                             j, R.jobs[j].t_span_ps * 1e-12, 64 - R.S.job_shift,
+                             (sort_time_limit(R.S.job_shift) - 0xFFFFFFFFull) * 1e-12, nj);
     // tallies per job
     R.tally_off.resize(nj);
     int64_t tc = 0;
@@ -118,8 +128,22 @@ int run_plan(Run &R) {
     for (int j = 0; j < nj; ++j)
         R.chunk_start[j + 1] = R.chunk_start[j] + (R.jobs[j].n_hist + cs - 1) / cs;
 
-    // the first guess may exceed the launch limit; the device counts past the
-    // capacity, so a run with more singles than the limit is still detected
+    // The first guess of the singles capacity (0.6 per history) may exceed what
+    // a long run needs by far (a narrow energy window keeps few singles): it
+    // takes at most a quarter of the free device memory.  The device counts
+    // past the capacity, so a run with more singles is detected and re-run once
+    // with its exact count; so is a run with more than the launch limit.
+    if (R.caps.guess) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            // arena bytes per single of capacity: raw record, two key and index
+            // buffers, the time-ordered arrays, coincidence flag and pair slots
+            const uint64_t per_single = sizeof(RawSingle) + 2 * 8 + 2 * 4 + 8 + 8 + 6 * 4 + 1 + 4;
+            R.caps.singles = std::min<uint64_t>(R.caps.singles, std::max<uint64_t>(65536, free_b / 4 / per_single));
+        } else {
+            cudaGetLastError();
+        }
+    }
     const uint64_t cap = std::min<uint64_t>(std::max<uint64_t>(R.caps.singles, 1), kMaxSinglesPerLaunch);
     const uint64_t hcap = R.keep_hits ? std::max<uint64_t>(R.caps.hits, 1) : 0;
     const uint64_t ocap = std::max<uint64_t>(R.caps.ovf, 1);
@@ -401,6 +425,7 @@ int run_with_retry(Run &R) {
         }
         if (st == GPET_ERR_OVERFLOW && attempt == 0 && !(R.h_hdr.status & kStatusOverflow)) {
             // the device counters kept counting past the capacities: re-run with exact sizes
+            R.caps.guess = false;
             R.caps.singles = std::max<uint64_t>(R.caps.singles, R.h_hdr.n_singles + 1024);
             R.caps.hits = std::max<uint64_t>(R.caps.hits, R.h_hdr.n_hits + 1024);
             R.caps.ovf = std::max<uint64_t>(R.caps.ovf, R.h_hdr.n_ovf + 1024);

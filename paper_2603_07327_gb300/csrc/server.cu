@@ -36,6 +36,7 @@ struct Req {
     gpet_digitizer dg{};
     uint64_t n = 0, seed = 0;
     size_t est = 0;
+    uint64_t span_ps = 0;             // acquisition span (decay times lie in [0, span_ps))
     bool done = false;
     int status = GPET_OK;
     std::string error;
@@ -74,6 +75,7 @@ static void worker_main(gpet_server *S, int widx) {
     for (;;) {
         std::vector<Req *> batch;
         size_t taken = 0;
+        uint64_t max_span = 0;
         {
             std::unique_lock<std::mutex> lk(C.mu);
             for (;;) {
@@ -82,6 +84,12 @@ static void worker_main(gpet_server *S, int widx) {
                 while (!S->queue.empty() && (int)batch.size() < S->max_jobs) {
                     Req *r = S->queue.front();
                     if (C.in_use + r->est > C.budget && !(batch.empty() && C.in_use == 0)) break;
+                    // the time stamps of every job must fit beside the job bits of the sort key
+                    const uint64_t span = std::max(max_span, r->span_ps);
+                    if (!batch.empty() &&
+                        span > sort_time_limit(sort_job_shift((int)batch.size() + 1)) - 0xFFFFFFFFull)
+                        break;
+                    max_span = span;
                     S->queue.pop_front();
                     C.in_use += r->est;
                     taken += r->est;
@@ -201,6 +209,7 @@ extern "C" int gpet_server_submit(gpet_server *S, gpet_scanner *sc, const gpet_s
     r->n = n_decays;
     r->seed = seed;
     r->est = run_footprint(n_decays, sc->n_crystals, 1, 1, false);
+    r->span_ps = J.t_span_ps;
     Core &C = *S->core;
     std::unique_lock<std::mutex> lk(C.mu);
     if (r->est > C.budget) {

@@ -1,8 +1,10 @@
 // sort.cu -- digitizer back end: LSD radix sort of singles by 64-bit time key,
 // gather into time order, coincidence sorting (Sec. 2.3 timing window).
 //
-// Keys are (job << 52) | t_ps, so a batch of jobs sorts as independent
-// segments.  The sort is a least-significant-digit radix sort with 8-bit
+// Keys are (job << shift) | t_ps, with the job in the fewest high bits that
+// number the launch's jobs (none for one job), so a batch of jobs sorts as
+// independent segments and a single run sorts on the whole 64-bit time.  The
+// sort is a least-significant-digit radix sort with 8-bit
 // digits: one fused pass builds the eight digit histograms, a plan kernel
 // drops the passes whose digit is the same for every key (high time bytes,
 // unused job bits), and every remaining pass is tile histogram -> per-digit
@@ -44,7 +46,8 @@ __global__ void __launch_bounds__(kSortThreads) k_make_keys(SortDev S) {
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint4 r0 = __ldg(reinterpret_cast<const uint4 *>(S.in_raw + i));
         const uint32_t job = __ldg(reinterpret_cast<const uint32_t *>(S.in_raw + i) + 6);
-        const uint64_t key = ((uint64_t)job << 52) | (((uint64_t)r0.y << 32) | r0.x);
+        const uint64_t t = ((uint64_t)r0.y << 32) | r0.x;
+        const uint64_t key = S.job_shift < 64 ? ((uint64_t)job << S.job_shift) | t : t;
         S.keys[0][i] = key;
         S.vals[0][i] = (uint32_t)i;
 #pragma unroll

@@ -11,8 +11,6 @@
 // The array is part of the library image: every GPU that loads the library
 // holds it until the process exits.  The caller still passes its inputs and
 // outputs.
-#include <mutex>
-
 #include "gpet.h"
 #include "host.h"
 
@@ -68,10 +66,6 @@ __global__ void k_noalloc_out(SortDev S, uint64_t *__restrict__ t_out, uint32_t 
     }
 }
 
-// device address of the scratch array, looked up once per device
-static std::mutex g_noalloc_mutex;
-static unsigned char *g_noalloc_addr[64] = {nullptr};
-
 }  // namespace gpet
 
 using namespace gpet;
@@ -86,20 +80,16 @@ extern "C" int gpet_sort_times_noalloc(const uint64_t *d_t_in, uint64_t n, uint6
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= 64) return gpet_fail(GPET_ERR_INVALID_ARG, "device index %d out of range", dev);
-    unsigned char *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_noalloc_mutex);
-        if (!g_noalloc_addr[dev]) {
-            // the host-side name of the array is not a device address: ask the
-            // runtime for the address of this device's copy (current device)
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_sort_scratch);
-            if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaGetSymbolAddress(sort scratch)");
-            g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
-        }
-        base = g_noalloc_addr[dev];
-    }
+    // The host-side name of the array is not a device address: ask the runtime
+    // for the address of the current device's copy.  The first lookup on a
+    // device loads the module that holds the array (modules load lazily), which
+    // is when its device memory is taken; later lookups read the loaded
+    // module's symbol table.  Looking it up on every call, rather than caching
+    // it, keeps the address right after a cudaDeviceReset reloads the module.
+    void *sym = nullptr;
+    e = cudaGetSymbolAddress(&sym, g_sort_scratch);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaGetSymbolAddress(sort scratch)");
+    unsigned char *base = static_cast<unsigned char *>(sym);
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaDeviceGetAttribute");
@@ -115,6 +105,7 @@ extern "C" int gpet_sort_times_noalloc(const uint64_t *d_t_in, uint64_t n, uint6
     S.tile_hist = reinterpret_cast<uint32_t *>(base + kOffTiles);
     S.max_tiles = kNoallocTiles;
     S.cap = kNoallocMaxKeys;
+    S.job_shift = 64;  // the keys are the caller's time stamps alone
     // the histograms keep the previous call's contents: clear them
     e = cudaMemsetAsync(S.ghist, 0, 8 * 256 * 4, st);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaMemsetAsync(sort scratch)");

@@ -139,3 +139,28 @@ def compare_coincidences(gs, ga, gb, os_sel, oa, ob, bad):
     diff = sg ^ so
     unexplained = [c for c in diff if not any(h in bad for h, _ in c)]
     return dict(n_gpu=len(sg), n_orc=len(so), n_diff=len(diff), unexplained=len(unexplained))
+
+
+def compare_tallies(tc, te, orc, gpu_hits, bad):
+    """Per-crystal count and energy tallies of a GPU run against the oracle's,
+    allowing each crystal the hits of the mismatched histories (`bad`) on both
+    sides, plus the FP32 deposit rounding (1e-5 relative) and one quantum of
+    the fixed-point energy per hit.  Returns the excess over that allowance
+    (<= 0 when within it) and the relative difference of the energy totals."""
+    badarr = np.array(sorted(bad), dtype=np.uint64)
+    ob = orc["hits"][np.isin(orc["hits"]["h"], badarr)]
+    gb = gpu_hits[np.isin(gpu_hits["h"], badarr)]
+    allow_c = np.zeros(len(tc))
+    np.add.at(allow_c, ob["crystal"], 1)
+    np.add.at(allow_c, gb["crystal"], 1)
+    dc = np.abs(tc.astype(np.int64) - orc["tally_count"].astype(np.int64))
+    allow_e = np.zeros(len(tc))
+    np.add.at(allow_e, ob["crystal"], ob["edep"] * 2 ** 20)
+    np.add.at(allow_e, gb["crystal"], gb["e"] * 2 ** 20)
+    de = np.abs(te.astype(np.float64) - orc["tally_efx"].astype(np.float64))
+    e_tot = float(orc["tally_efx"].astype(np.float64).sum())
+    return dict(count_excess=float((dc - allow_c).max()) if len(tc) else 0.0,
+                energy_excess=float((de - allow_e - E_REL * orc["tally_efx"] - tc - 1).max()) if len(tc) else 0.0,
+                crystals_differing=int((dc > 0).sum()),
+                count_total_rel=abs(float(tc.sum()) - float(orc["tally_count"].sum())) / max(float(orc["tally_count"].sum()), 1.0),
+                energy_total_rel=abs(float(te.astype(np.float64).sum()) - e_tot) / max(e_tot, 1.0))

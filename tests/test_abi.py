@@ -252,8 +252,8 @@ def test_whole_launch_copy_refuses_null_arguments(G):
 
 def test_empty_and_out_of_range_sizes_are_refused_on_the_host(G):
     """Degenerate and maximum sizes: zero decays, a shard outside the run, more
-    than 64 panels, 8 layers or 8 materials, and an acquisition past the 2^52 ps
-    time key are GPET_ERR_INVALID_ARG before any device work; the largest
+    than 64 panels, 8 layers or 8 materials, and an acquisition past 2^62 ps
+    (53 days) are GPET_ERR_INVALID_ARG before any device work; the largest
     accepted descriptor sizes (64 panels, 8 layers, 8 materials) are accepted."""
     import ctypes as C
     L = G.load()
@@ -263,7 +263,7 @@ def test_empty_and_out_of_range_sizes_are_refused_on_the_host(G):
             with pytest.raises(G.GpetError) as e:
                 sc.simulate(W.point_source(), W.digitizer(), n, 1, **opts)
             assert e.value.code == -1
-        with pytest.raises(G.GpetError) as e:   # 1e9 decays at 1 Bq: far past 2^52 ps
+        with pytest.raises(G.GpetError) as e:   # 1e9 decays at 1 Bq: 1e21 ps, far past 2^62 ps
             sc.simulate(W.point_source(activity_bq=1.0), W.digitizer(), 10**9, 1)
         assert e.value.code == -1
     finally:

@@ -37,7 +37,7 @@ def assert_same(x, y):
     assert k1["hits"] == k2["hits"] and k1["singles"] == k2["singles"] and k1["coincidences"] == k2["coincidences"]
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 def test_batch_equals_alone(G, kernel):
     designs = W.config4(n_designs=6, scale=0.05)
     ph = W.hot_rod_phantom(scale=0.7)
@@ -205,5 +205,28 @@ def test_autotune_choice_gives_the_same_results(G):
         a = sc.simulate(W.point_source((1.0, 2.0, 0.0)), W.digitizer(), 200_000, 6, **opts)
         b = sc.simulate(W.point_source((1.0, 2.0, 0.0)), W.digitizer(), 200_000, 6, kernel=2)
         assert_same(canon(a), canon(b))
+    finally:
+        sc.close()
+
+
+def test_time_key_fits_the_launch(G):
+    """The sort key holds the job index in the fewest high bits that number a
+    launch's jobs, the time stamp in the rest: a single run sorts on the whole
+    64-bit time, while an acquisition that leaves no room for the job bits of
+    a three-job batch is refused before any device work."""
+    sc = G.Scanner(W.config1_scanner())
+    try:
+        n = 20_000
+        # a span just below 2^62 ps: too long beside two job bits, fine alone
+        src = W.point_source(activity_bq=n * 1e12 / float((1 << 62) - (1 << 31)))
+        r = sc.simulate(src, W.digitizer(), n, 3)
+        t = r.array(G.SINGLES_T_PS)
+        assert len(t) > 100 and t.max() > 1 << 61 and np.all(np.diff(t) >= 0)
+        r.free()
+        jobs = [dict(scanner=sc, source=src if i == 1 else W.point_source(), digitizer=W.digitizer(),
+                     n_decays=n, seed=i) for i in range(3)]
+        with pytest.raises(G.GpetError) as e:
+            G.simulate_batch(jobs)
+        assert e.value.code == -1 and "job bits" in str(e.value)
     finally:
         sc.close()

@@ -1,5 +1,8 @@
 """Serving loop: requests submitted while others run are batched together;
-every result equals the same request run alone; admission by HBM footprint."""
+every result equals the same request run alone, and sampled requests (point
+and phantom sources) run alone match the FP64 oracle history by history;
+admission by HBM footprint.  The server runs the default launch form, the one
+the benchmark times."""
 import threading
 import time
 
@@ -7,6 +10,7 @@ import pytest
 
 import workloads as W
 from tests.test_gpu_batch import assert_same, canon
+from tests.test_gpu_parity import check_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -20,19 +24,21 @@ def G():
     return G
 
 
-def test_served_results_equal_alone(G):
+def _request_scanner(G, r, base):
+    """The request's scanner, with the hot-rod phantom scaled as the request asks."""
+    ph = None
+    if r["phantom"] is not None:
+        vs = 0.5 * r["phantom"][1]
+        ph = dict(base, voxel=(vs, vs, vs), origin=(-30 * vs, -30 * vs, -50 * vs))
+    return G.Scanner(r["scanner"], ph), ph
+
+
+def test_served_results_equal_alone(G, oracle):
     reqs = W.config5(n_requests=24, pairs_lo=2e4, pairs_hi=4e5)
     base = W.hot_rod_phantom()
-    scanners, sources = [], []
-    for r in reqs:
-        ph = None
-        if r["phantom"] is not None:
-            scale = r["phantom"][1]
-            vs = 0.5 * scale
-            ph = dict(base, voxel=(vs, vs, vs), origin=(-30 * vs, -30 * vs, -50 * vs))
-        scanners.append(G.Scanner(r["scanner"], ph))
-        sources.append(r["source"])
-    srv = G.Server(hbm_budget_bytes=8 * 10**9, workers=2, kernel=2)
+    made = [_request_scanner(G, r, base) for r in reqs]
+    scanners = [m[0] for m in made]
+    srv = G.Server(hbm_budget_bytes=8 * 10**9, workers=2)
     ids = [None] * len(reqs)
 
     def submit_all():
@@ -42,7 +48,7 @@ def test_served_results_equal_alone(G):
             dt = (r["arrival_s"] - reqs[0]["arrival_s"]) / 20.0 - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
-            ids[i] = srv.submit(scanners[i], sources[i], r["digitizer"], r["n_decays"], r["seed"])
+            ids[i] = srv.submit(scanners[i], r["source"], r["digitizer"], r["n_decays"], r["seed"])
 
     th = threading.Thread(target=submit_all)
     th.start()
@@ -52,10 +58,24 @@ def test_served_results_equal_alone(G):
     assert st["completed"] == len(reqs) and st["submitted"] == len(reqs)
     assert st["launches"] <= len(reqs)
     for i, r in enumerate(reqs):
-        alone = scanners[i].simulate(sources[i], r["digitizer"], r["n_decays"], r["seed"], kernel=2)
+        alone = scanners[i].simulate(r["source"], r["digitizer"], r["n_decays"], r["seed"])
         assert_same(canon(alone), canon(served[i]))
         assert served[i].counts()["latency_ms"] > 0
     srv.close()
+    # the served results against the oracle: three point-source and three
+    # phantom requests, run alone with their hit lists (equal to the served
+    # result, checked here again) and compared history by history
+    point = [i for i, r in enumerate(reqs) if r["phantom"] is None][:3]
+    phantom = [i for i, r in enumerate(reqs) if r["phantom"] is not None][:3]
+    assert len(point) == 3 and len(phantom) == 3
+    for i in point + phantom:
+        r = reqs[i]
+        res = scanners[i].simulate(r["source"], r["digitizer"], r["n_decays"], r["seed"], keep_hits=True)
+        assert_same(canon(res), canon(served[i]))
+        orc = oracle.simulate(r["scanner"], r["source"], r["digitizer"], r["n_decays"], r["seed"],
+                              phantom=made[i][1], threads=8)
+        check_parity(G, oracle, res, orc, r["n_decays"], r["digitizer"])
+        res.free()
 
 
 def test_admission_by_footprint(G):
