@@ -39,33 +39,21 @@ METRIC = "pairs tracked/s/GB300 batched vs plain; p50/p99 served-request latency
 N_POSITIONS = 61
 PAIRS_PER_POSITION = 10_000_000
 
-# Algorithmic lane-operations per event of the method: the arithmetic each step
-# needs at its leanest (not counted from compiled code).  One Philox4x32-10
-# block is 10 rounds x (2 wide multiplies = 4 ops, 2 three-way xors, 2 key adds)
-# = 80.
-#   decay: 1 block, 4 uniforms, 64-bit time product, isotropic direction   130
-#   flight screen (every flight): distance to the ring, axial test            20
-#   flight test (flights the screen leaves): candidate azimuths, ~2 slab tests 140
-#   panel entry: frame change                                                 12
-#   detector step: 1 block, log, cross sections, move, exit test, layer
-#     selection + module + crystal location, accept tests                    165
-#   phantom step: 1 block, log, exit distance, voxel index + gather, accept   150
-#   Compton trial: 1 block, 3 uniforms, one Kahn branch and its test          100
-#   crystal hit: kinematics/rotation share, tallies, singles-list update       60
-#   single: 1 block, Box-Muller, energy and depth blur, window, append        150
-ALG = dict(source=130, screen=20, flight_test=140, enter=12, det_step=165, ph_step=150, trial=100, hit=60,
-           single=150)
-SM_COUNT_GB300 = 152
-LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+# The transport is bound by instruction issue (no dense contraction, L2-resident
+# working set).  Its roofline peak is the SMs' issue slots: the SM count of the
+# device (queried), four warp schedulers per SM that each issue one warp
+# instruction per cycle, at the maximum SM clock (generated peaks file,
+# else the GB300's 2070 MHz).
+SCHEDULERS_PER_SM = 4
+PHASES = ("", "decay", "phantom_step", "flight", "detector_step", "finish", "flight_after_exit")
 
 
-def alg_ops(c, n_panels=None):
-    tested = c["flights"] - c.get("screened_flights", 0)
-    singles = c.get("singles_formed", 0) or c["hits"]
-    return (c["n_decays"] * ALG["source"] + c["flights"] * ALG["screen"] + tested * ALG["flight_test"]
-            + c["entered"] * ALG["enter"] + c["det_steps"] * ALG["det_step"] + c["phantom_steps"] * ALG["ph_step"]
-            + c["compton_trials"] * ALG["trial"] + c["hits"] * ALG["hit"] + singles * ALG["single"])
+def _sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        return 2070.0
 
 
 def sweep_jobs(rank=0, pairs=PAIRS_PER_POSITION, positions=N_POSITIONS):
@@ -122,37 +110,30 @@ class Clocks:
                     reasons=sorted(reasons), samples=len(sm))
 
 
-# DRAM bytes (read + write) per simulated pair of the transport kernel, from an
-# ncu capture of the full batched sweep launch (dram__bytes_read.sum +
-# dram__bytes_write.sum; one pass).  The counters hold only for the sources they
-# were taken on: the entry carries their SHA-1, and `traffic` is reported as null
-# once any transport source differs.
+# Counters of the transport kernel in the benchmark's own launch (the whole
+# sweep), per simulated pair, from one ncu capture of that launch with
+# smsp__inst_executed.sum (warp instructions), dram__bytes_read.sum and
+# dram__bytes_write.sum.  A capture holds only for the sources it was taken on:
+# each entry carries their SHA-1 and is reported as null once they differ.
+# Entries are named by capture id (the summary of each capture under that id
+# gives its command).
 TRANSPORT_SOURCES = ("device.cuh", "transport.cuh", "transport.cu", "transport_cta.cu")
-TRANSPORT_TRAFFIC = dict(sha1="28a8dadaa6a6fbf2b2581aa848d1c05d23eb668d", bytes_per_pair=8.408,
-                         capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
-# The same for the digitizer back end (make_keys .. job_stats of one step), per single.
+TRANSPORT_CAPTURE = dict(id="transport_sweep_122x1e7", sha1=None, warp_inst_per_pair=None,
+                         dram_bytes_per_pair=None)
+# Issue detail of the same kernel from one ncu --set full capture of a
+# 2e6-pair sweep position: issue-active fraction of the schedulers and SIMT
+# efficiency (thread instructions per warp instruction / 32).
+TRANSPORT_DETAIL = dict(id="k_transport_cta_sweep_position_2e6", sha1=None, issue_active=None,
+                        simt_efficiency=None)
+# DRAM bytes of the digitizer back end (make_keys .. job_stats of one step), per single.
 DIGITIZER_SOURCES = ("device.cuh", "sort.cu")
-DIGITIZER_TRAFFIC = dict(sha1="e89c00f723ab94c4c2a9e21ce83ac296c1ea3af2", bytes_per_single=528.7,
-                         capture="profiles/traffic_sensitivity_sweep_122x1e7.md")
+DIGITIZER_TRAFFIC = dict(id="traffic_sensitivity_sweep_122x1e7", sha1="e89c00f723ab94c4c2a9e21ce83ac296c1ea3af2",
+                         bytes_per_single=528.7)
 
 
-# SM issue view of the transport kernel from one ncu --set full capture (the
-# 2e6-pair sweep position of profiles/k_transport_cta_sweep_position_2e6.md):
-# issue-active fraction of the schedulers, SIMT efficiency (thread
-# instructions per warp instruction / 32), warp instructions per pair.
-# Reported while the transport code is the captured one, null otherwise.
-TRANSPORT_ISSUE = dict(sha1="28a8dadaa6a6fbf2b2581aa848d1c05d23eb668d", issue_active=0.4943, simt_efficiency=0.5803,
-                       warp_inst_per_pair=142.2,
-                       capture="profiles/k_transport_cta_sweep_position_2e6.md")
-
-
-def _transport_issue():
-    t = TRANSPORT_ISSUE
-    if not t or not t["sha1"] or t["sha1"] != _sources_sha1(TRANSPORT_SOURCES):
-        return None
-    return dict(issue_active=t["issue_active"], simt_efficiency=t["simt_efficiency"],
-                lane_utilisation=t["issue_active"] * t["simt_efficiency"],
-                warp_inst_per_pair=t["warp_inst_per_pair"], source="ncu --set full, " + t["capture"])
+def _current(entry, sources):
+    """The capture entry when it was taken on the present sources, else None."""
+    return entry if entry and entry.get("sha1") and entry["sha1"] == _sources_sha1(sources) else None
 
 
 def _sources_sha1(names):
@@ -172,17 +153,31 @@ def _sources_sha1(names):
 
 
 def _transport_traffic(pairs_per_launch):
-    t = TRANSPORT_TRAFFIC
-    if not t or t["sha1"] != _sources_sha1(TRANSPORT_SOURCES):
-        return None
-    return t["bytes_per_pair"] * pairs_per_launch
+    t = _current(TRANSPORT_CAPTURE, TRANSPORT_SOURCES)
+    return t["dram_bytes_per_pair"] * pairs_per_launch if t and t["dram_bytes_per_pair"] else None
 
 
 def _digitizer_traffic(singles_per_step):
-    t = DIGITIZER_TRAFFIC
-    if not t or t["sha1"] != _sources_sha1(DIGITIZER_SOURCES):
-        return None
-    return t["bytes_per_single"] * singles_per_step
+    t = _current(DIGITIZER_TRAFFIC, DIGITIZER_SOURCES)
+    return t["bytes_per_single"] * singles_per_step if t else None
+
+
+def event_isolated(scanners, dg, counts, tr_ms, n_sample=1_000_000):
+    """Event-isolated fraction of the transport: each phase's events of the
+    timed launches (counted by the kernel) times that event's GPU time when it
+    runs alone at full width (gpet_event_costs, on states of geometry A and B
+    with the source at the centre, averaged: the sweep is half of each), over
+    the measured transport time."""
+    costs = [scanners[g].event_costs(W.point_source((0.0, 0.0, 0.0)), dg, n_sample=n_sample, seed=2)[0]
+             for g in ("A", "B")]
+    ns = [0.5 * (a + b) for a, b in zip(*costs)]
+    events = [sum(c["phase_events"][p] for c in counts) for p in range(len(PHASES))]
+    pairs = sum(c["n_decays"] for c in counts)
+    ideal_ms = sum(events[p] * ns[p] for p in range(1, len(PHASES))) * 1e-6
+    return dict(frac=ideal_ms / tr_ms, ideal_transport_ms=ideal_ms, transport_ms=tr_ms,
+                ns_per_event={PHASES[p]: ns[p] for p in range(1, len(PHASES))},
+                events_per_pair={PHASES[p]: events[p] / pairs for p in range(1, len(PHASES))},
+                sample=f"{n_sample} histories of geometry A and of B, source at the centre")
 
 
 def _measured_hbm_gbs():
@@ -243,11 +238,14 @@ def run_reference(args):
 
 
 def run_served(G, args):
-    """The served stream: 2000 requests arriving as a Poisson process (50/s),
-    each a design drawn like the batched sweep, half point sources and half
-    the hot-rod phantom scaled 0.5-1x, 1e5-5e7 pairs; admitted under a 150 GB
-    HBM budget.  Returns latency percentiles, aggregate and offered pairs/s and
-    the pairs/s of sequential plain launches of the same requests."""
+    """The served stream: 2000 simulation requests, each a design drawn like
+    the batched sweep, half point sources and half the hot-rod phantom scaled
+    0.5-1x, 1e5-5e7 pairs, admitted under a 150 GB HBM budget.  Served twice:
+    arriving as the Poisson process of the workload (50/s, about a tenth of
+    the GPU's capacity: latency at that load), and with the same arrival times
+    compressed `served_compress` times, so that the queue never empties
+    (throughput at saturation).  Then the same requests as sequential plain
+    launches, one gpet_simulate each, back to back."""
     import threading
     reqs = W.config5(n_requests=args.served_requests)
     base = W.hot_rod_phantom()
@@ -259,59 +257,75 @@ def run_served(G, args):
             ph = dict(base, voxel=(vs, vs, vs), origin=(-30 * vs, -30 * vs, -50 * vs))
         return G.Scanner(r["scanner"], ph)
 
-    srv = G.Server(hbm_budget_bytes=150 * 10**9, workers=2, kernel=args.kernel)
-    # warm the server path once (kernels, pools)
-    w = make(reqs[0])
-    srv.wait(srv.submit(w, reqs[0]["source"], reqs[0]["digitizer"], 100_000, 1))
-    ids, scanners = [None] * len(reqs), [None] * len(reqs)
-    t0 = time.perf_counter()
+    scanners = [None] * len(reqs)
 
-    def submit_all():
-        for i, r in enumerate(reqs):
-            dt = r["arrival_s"] - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
-            scanners[i] = make(r)   # the request's design (and phantom) is built at arrival
-            ids[i] = srv.submit(scanners[i], r["source"], r["digitizer"], r["n_decays"], r["seed"])
+    def serve(compress):
+        srv = G.Server(hbm_budget_bytes=150 * 10**9, kernel=args.kernel)
+        w = scanners[0] or make(reqs[0])
+        srv.wait(srv.submit(w, reqs[0]["source"], reqs[0]["digitizer"], 100_000, 1)).free()  # warm the path
+        st0 = srv.stats()
+        ids = [None] * len(reqs)
+        t0 = time.perf_counter()
 
-    lat = []
+        def submit_all():
+            for i, r in enumerate(reqs):
+                dt = r["arrival_s"] / compress - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                if scanners[i] is None:
+                    scanners[i] = make(r)   # the request's design (and phantom) is built at arrival
+                ids[i] = srv.submit(scanners[i], r["source"], r["digitizer"], r["n_decays"], r["seed"])
 
-    def collect_all():
-        # results are taken (and their device memory released) as they complete
-        for k in range(len(reqs)):
-            while ids[k] is None:
-                time.sleep(0.001)
-            res = srv.wait(ids[k])
-            lat.append(res.counts()["latency_ms"])
-            res.free()
+        lat = []
 
-    th = threading.Thread(target=submit_all)
-    tc = threading.Thread(target=collect_all)
-    th.start()
-    tc.start()
-    th.join()
-    tc.join()
-    t_last = time.perf_counter() - t0
-    st = srv.stats()
-    srv.close()
-    pairs = sum(r["n_decays"] for r in reqs)
-    span = reqs[-1]["arrival_s"]
-    # sequential plain launches of the first requests, same designs, back to back
-    k = min(len(reqs), args.served_plain_sample)
-    sc_plain = [scanners[i] for i in range(k)]
+        def collect_all():
+            # results are taken (and their device memory released) as they complete
+            for k in range(len(reqs)):
+                while ids[k] is None:
+                    time.sleep(0.001)
+                res = srv.wait(ids[k])
+                lat.append(res.counts()["latency_ms"])
+                res.free()
+
+        th = threading.Thread(target=submit_all)
+        tc = threading.Thread(target=collect_all)
+        th.start()
+        tc.start()
+        th.join()
+        tc.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        pairs = sum(r["n_decays"] for r in reqs)
+        lat = sorted(lat)
+        return dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                    max_ms=float(lat[-1]), pairs_per_s=pairs / wall,
+                    offered_pairs_per_s=pairs / (reqs[-1]["arrival_s"] / compress), wall_s=wall,
+                    launches=st["launches"] - st0["launches"], max_jobs_per_launch=st["max_jobs_per_launch"],
+                    live_appends=st["live_appends"] - st0["live_appends"], pieces=st["pieces"] - st0["pieces"],
+                    peak_hbm_bytes=st["peak_bytes"])
+
+    poisson = serve(1.0)
+    saturated = serve(args.served_compress)
+    # the same requests as sequential plain launches, back to back
+    k = min(len(reqs), args.served_plain_sample) if args.served_plain_sample > 0 else len(reqs)
+    scanners[0].simulate(reqs[0]["source"], reqs[0]["digitizer"], 100_000, 1, kernel=args.kernel).free()
     tp = time.perf_counter()
     for i in range(k):
-        sc_plain[i].simulate(reqs[i]["source"], reqs[i]["digitizer"], reqs[i]["n_decays"], reqs[i]["seed"],
+        scanners[i].simulate(reqs[i]["source"], reqs[i]["digitizer"], reqs[i]["n_decays"], reqs[i]["seed"],
                              kernel=args.kernel).free()
     tp = time.perf_counter() - tp
     pairs_plain = sum(reqs[i]["n_decays"] for i in range(k))
-    lat = sorted(lat)
-    return dict(requests=len(reqs), p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
-                max_ms=float(lat[-1]), pairs=pairs, pairs_per_s=pairs / t_last, offered_pairs_per_s=pairs / span,
-                wall_s=t_last, launches=st["launches"], max_jobs_per_launch=st["max_jobs_per_launch"],
-                peak_hbm_bytes=st["peak_bytes"], hbm_budget_bytes=150 * 10**9,
-                sequential_plain_pairs_per_s=pairs_plain / tp, sequential_plain_sample=k,
-                arrivals="Poisson, mean 50 req/s, seed 5")
+    for sc in scanners:
+        if sc is not None:
+            sc.close()
+    pairs = sum(r["n_decays"] for r in reqs)
+    return dict(requests=len(reqs), pairs=pairs, hbm_budget_bytes=150 * 10**9,
+                arrivals="Poisson, mean 50 req/s, seed 5",
+                poisson=poisson,
+                saturated=dict(saturated, compress=args.served_compress),
+                sequential_plain_pairs_per_s=pairs_plain / tp, sequential_plain_requests=k,
+                saturated_over_sequential_plain=saturated["pairs_per_s"] / (pairs_plain / tp))
 
 
 def run_sensitivity(G, args):
@@ -466,7 +480,6 @@ def run_ours(args):
 
     dg = W.digitizer()
     scanners = {g: G.Scanner(W.config2_scanner(g)) for g in ("A", "B")}
-    n_panels = 12
     jobs = sweep_jobs(rank, pairs=args.pairs, positions=args.positions)
     pairs_per_step = sum(j["n"] for j in jobs)
     stream = torch.cuda.current_stream().cuda_stream
@@ -525,18 +538,37 @@ def run_ours(args):
     # dominant kernel: the transport kernel (per-launch CUDA events inside the library)
     tr_ms = sum(c["transport_ms"] for c in counts)
     dg_ms = sum(c["digitizer_ms"] for c in counts)
-    ops = sum(alg_ops(c, n_panels) for c in counts)
-    achieved = ops / (tr_ms / 1000.0)
-    peak = SM_COUNT_GB300 * LANES_PER_SM * SM_MAX_MHZ * 1e6
     kname = {1: "k_transport_loop", 2: "k_transport_wave"}.get(args.kernel, "k_transport_cta")
     pairs_per_launch = pairs_per_step if args.form == "batched" else pairs_per_step / max(len(jobs), 1)
+    default_kernel = args.kernel in (0, 3)
     traffic = args.traffic if args.traffic is not None else (
-        _transport_traffic(pairs_per_launch) if args.kernel in (0, 3) else None)
-    roof = dict(bound="alu", achieved=achieved, peak=peak, unit="lane-ops/s", frac=achieved / peak,
-                traffic=traffic, kernel=kname,
-                peak_note="152 SMs x 128 FP32/INT lanes x 2070 MHz (recipe unit counts and max clock)",
-                transport_share=tr_ms / (tr_ms + dg_ms),
-                issue=_transport_issue() if args.kernel in (0, 3) else None)
+        _transport_traffic(pairs_per_launch) if default_kernel else None)
+    # issue slots: warp instructions per pair (ncu, the benchmark's own launch)
+    # x pairs over the transport time of the timed launches (CUDA events),
+    # against the device's issue slots
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = _sm_max_mhz()
+    issue_peak = sm_count * SCHEDULERS_PER_SM * sm_mhz * 1e6
+    cap = _current(TRANSPORT_CAPTURE, TRANSPORT_SOURCES) if default_kernel else None
+    achieved = cap["warp_inst_per_pair"] * pairs_per_step * args.steps / (tr_ms / 1000.0) if cap else None
+    detail = _current(TRANSPORT_DETAIL, TRANSPORT_SOURCES) if default_kernel else None
+    roof = dict(bound="alu", achieved=achieved, peak=issue_peak, unit="warp-instructions/s",
+                frac=(achieved / issue_peak) if achieved else None, traffic=traffic, kernel=kname,
+                peak_note=f"{sm_count} SMs (device query) x {SCHEDULERS_PER_SM} warp schedulers x {sm_mhz:.0f} MHz "
+                          "(maximum SM clock): issue slots",
+                capture=cap["id"] if cap else None,
+                warp_inst_per_pair=cap["warp_inst_per_pair"] if cap else None,
+                issue_detail=dict(issue_active=detail["issue_active"], simt_efficiency=detail["simt_efficiency"],
+                                  capture=detail["id"]) if detail else None,
+                transport_share=tr_ms / (tr_ms + dg_ms))
+    # beside it: the transport time the launch's events would take if each ran
+    # alone at full width (per-event costs from micro-kernels on this GPU, on
+    # states of this workload), over the measured transport time
+    if default_kernel:
+        try:
+            roof["event_isolated"] = event_isolated(scanners, dg, counts, tr_ms)
+        except Exception as exc:  # noqa: BLE001
+            roof["event_isolated"] = dict(error=f"{type(exc).__name__}: {exc}")
 
     # digitizer back end (time sort + coincidences), HBM-bound: algorithmic bytes
     # per single = key build 24 + 8 radix passes x 32 (histogram read 8, scatter
@@ -698,7 +730,10 @@ def main():
     ap.add_argument("--sens-reps", type=int, default=3)
     ap.add_argument("--no-sens-plain", dest="sens_plain", action="store_false", default=True,
                     help="skip the per-window plain runs that the map is compared with")
-    ap.add_argument("--served-plain-sample", type=int, default=300)
+    ap.add_argument("--served-plain-sample", type=int, default=0,
+                    help="requests of the sequential plain comparison (0 = all)")
+    ap.add_argument("--served-compress", type=float, default=20.0,
+                    help="arrival-time compression of the saturated served run")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -235,6 +235,10 @@ typedef struct {
     uint64_t screened_flights;            /* flights decided by the axial screen (no panel test) */
     uint64_t singles_formed;              /* singles before the energy window */
     double latency_ms;      /* served requests: submission to result ready (0 otherwise) */
+    /* events run per history phase by the CTA-synchronous kernel (kernel 3; zero for the others):
+       [1] decay, [2] phantom step, [3] flight from the decay or phantom, [4] detector step,
+       [5] finish (digitizer of a history), [6] flight after a panel exit; [0] unused */
+    uint64_t phase_events[7];
 } gpet_counts;
 int gpet_result_counts(const gpet_result *r, gpet_counts *out);
 
@@ -413,8 +417,9 @@ int gpet_sort_times_noalloc(const uint64_t *d_t_in, uint64_t n, uint64_t *d_t_ou
  * choice for the transport of Sec. 2.1.
  * Time the candidate launch forms of the transport kernel -- the per-lane
  * event loop, the per-warp wavefront, the CTA-synchronous wavefront at 128,
- * 256 or 512 threads and pool depth 2 or 3 -- on a pilot run
- * (pilot_decays >= 1000, seed)
+ * 256 or 512 threads, pool depth 2 or 3 and compaction interval 1, 2 or 4
+ * (gpet_options.compact_every: detector or phantom steps a lane runs between
+ * regroupings) -- on a pilot run (pilot_decays >= 1000, seed)
  * of the caller's workload, and return the fastest in *best (its transport
  * time in *best_ms, may be NULL).  The choice is remembered for the scanner's
  * design class (panels, layers, phantom) on this device's SM count; later
@@ -424,30 +429,63 @@ int gpet_autotune(gpet_scanner *sc, const gpet_source *src, const gpet_digitizer
                   uint64_t seed, gpet_options *best, float *best_ms);
 
 /* ------------------------------------------------------------------------ */
+/* per-event costs (measurement)                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Library infrastructure with no counterpart in the paper: the cost of each
+ * event of the transport of Sec. 2.1 / 2.3 when it runs alone.  Histories
+ * 0 .. n_sample - 1 of the caller's workload (scanner, source, digitizer,
+ * seed) are run once, one GPU lane per history, keeping up to 65536 states
+ * that entered each history phase; then, per phase, a kernel in which every
+ * lane of the GPU runs that phase's event on those states is timed with CUDA
+ * events (best of three after a warm-up launch).
+ *   ns_per_event  host, 7 doubles: [p] = GPU time per event of phase p when
+ *                 the whole GPU runs only that event (phases as in
+ *                 gpet_counts.phase_events; 0 where no state of the phase
+ *                 occurred; [0] unused)
+ *   states        host, 7 uint64 or NULL: states kept per phase
+ * n_sample in [1000, 2^32].  Runs on a stream of its own and synchronises it;
+ * allocates device memory for the sample run and the state pools. */
+int gpet_event_costs(gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg, uint64_t n_sample,
+                     uint64_t seed, double *ns_per_event, uint64_t *states);
+
+/* ------------------------------------------------------------------------ */
 /* serving loop: continuous batching of simulation requests                  */
 /* ------------------------------------------------------------------------ */
 
 /* Library infrastructure with no counterpart in the paper: simulations of
- * Sec. 2.1-2.3 served as requests.
+ * Sec. 2.1-2.3 served as requests, with continuous batching.
  * A server accepts simulation requests from any host thread while earlier
- * ones run.  Worker threads (each with its own stream) repeatedly admit the
- * queued requests that fit the device-memory budget, first come first
- * served, and run them together as one batched launch; the batches of
- * different workers overlap on the GPU.  A request's device memory counts
- * against the budget from admission until its result is freed, so a client
- * that keeps results while it waits for later requests can stall admission:
- * free results once read.  A request's result equals gpet_simulate's for the
- * same inputs. */
+ * ones run.  One pipeline thread keeps a transport launch running and appends
+ * arriving requests to the work table of that launch while its kernel runs;
+ * the persistent kernel takes them up as slots free.  A request of more than
+ * piece_decays decays is split into history ranges that join successive
+ * launches (one range per request at a time, so small requests do not queue
+ * behind large ones); the kernel writes those ranges' singles and tallies into
+ * the request's own device buffers, which stay on the device until its last
+ * range has run, and its time sort and coincidence sorting then run once.  A
+ * launch takes new requests until it is max_launch_ms old or full, or until
+ * the queue is empty and its published work is all taken; its digitizer then
+ * runs, and the next launch starts.  Device memory counts against the budget
+ * per launch (a quarter of the budget at most) and per split request, until
+ * the results that view it are freed, so a client that keeps results while it
+ * waits for later requests can stall admission: free results once read.  A
+ * request's result equals gpet_simulate's for the same inputs. */
 typedef struct gpet_server gpet_server;
 typedef struct {
-    size_t hbm_budget_bytes;      /* device memory the server may hold for admitted requests */
-    int32_t workers;              /* batching threads, one stream each (0 = 2, at most 8) */
-    int32_t max_jobs_per_launch;  /* requests per batched launch (0 = 256, at most 4095) */
+    size_t hbm_budget_bytes;      /* device memory the server may hold */
+    int32_t workers;              /* 0..8, accepted for compatibility: one pipeline serves all requests */
+    int32_t max_jobs_per_launch;  /* jobs one launch takes (0 = 256, at most 4095) */
     gpet_options launch;          /* kernel options of every launch (stream, keep_hits ignored) */
+    double max_launch_ms;         /* a launch takes new requests for at most this long (0 = 20 ms) */
+    uint64_t piece_decays;        /* larger requests run in ranges of this many decays (0 = 4e6; at
+                                     most half of what one launch's singles buffer is sized for) */
 } gpet_server_config;
 typedef struct {
     uint64_t submitted, completed, rejected, launches, max_jobs_per_launch, pairs_completed;
     uint64_t bytes_in_use, peak_bytes, queued;
+    uint64_t live_appends;        /* jobs appended to a launch whose kernel was already running */
+    uint64_t pieces;              /* history ranges of split requests handed to launches */
 } gpet_server_stats;
 int gpet_server_create(const gpet_server_config *cfg, gpet_server **out);
 /* Queue one request.  The scanner (and its phantom) must stay alive until the
@@ -464,7 +502,7 @@ int gpet_server_submit(gpet_server *s, gpet_scanner *sc, const gpet_source *src,
 int gpet_server_poll(gpet_server *s, uint64_t req_id, gpet_result **out);
 int gpet_server_wait(gpet_server *s, uint64_t req_id, gpet_result **out);
 int gpet_server_stats_get(gpet_server *s, gpet_server_stats *out);
-/* Finish the queued requests, stop the workers, free untaken results. */
+/* Finish the queued requests, stop the pipeline, free untaken results. */
 void gpet_server_destroy(gpet_server *s);
 
 /* Thread-local text of the last error (never NULL). */

@@ -83,17 +83,27 @@ class Counts(C.Structure):
                 ("phantom_steps", C.c_uint64), ("status", C.c_int32), ("transport_ms", C.c_float),
                 ("digitizer_ms", C.c_float), ("h2d_bytes", C.c_uint64), ("wave_iterations", C.c_uint64),
                 ("wave_lanes", C.c_uint64), ("screened_flights", C.c_uint64), ("singles_formed", C.c_uint64),
-                ("latency_ms", C.c_double)]
+                ("latency_ms", C.c_double), ("phase_events", C.c_uint64 * 7)]
+
+
+def _counts_dict(c):
+    """gpet_counts as a dict (arrays as lists)."""
+    out = {}
+    for k, _ in Counts._fields_:
+        v = getattr(c, k)
+        out[k] = list(v) if isinstance(v, C.Array) else v
+    return out
 
 
 class ServerConfig(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("workers", C.c_int32), ("max_jobs_per_launch", C.c_int32),
-                ("launch", Options)]
+                ("launch", Options), ("max_launch_ms", C.c_double), ("piece_decays", C.c_uint64)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "rejected", "launches", "max_jobs_per_launch",
-                                          "pairs_completed", "bytes_in_use", "peak_bytes", "queued")]
+                                          "pairs_completed", "bytes_in_use", "peak_bytes", "queued",
+                                          "live_appends", "pieces")]
 
 
 # every entry point declared in include/gpet.h: name -> (restype, argtypes)
@@ -132,6 +142,8 @@ SIGNATURES = {
     "gpet_server_stats_get": (C.c_int, [_P, C.POINTER(ServerStats)]),
     "gpet_server_destroy": (None, [_P]),
     "gpet_sort_times_noalloc": (C.c_int, [_P, C.c_uint64, _P, _P, _P]),
+    "gpet_event_costs": (C.c_int, [_P, C.POINTER(Source), C.POINTER(Digitizer), C.c_uint64, C.c_uint64,
+                                   C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
     "gpet_sensitivity_map": (C.c_int, [C.c_int32, C.POINTER(_P), C.c_int32, C.POINTER(C.c_double), C.c_double,
                                        C.POINTER(Digitizer), C.c_int32, C.POINTER(C.c_double), C.c_uint64,
                                        C.c_uint64, C.POINTER(Options), _P, _P, C.POINTER(Counts)]),
@@ -248,7 +260,17 @@ class Scanner:
         ms = C.c_float()
         _check(load().gpet_autotune(self._h, C.byref(source_struct(source)), C.byref(digitizer_struct(digitizer)),
                                     int(pilot_decays), int(seed), C.byref(o), C.byref(ms)))
-        return dict(kernel=o.kernel, blocks_per_sm=o.blocks_per_sm, compact_every=o.compact_every), ms.value
+        return dict(kernel=o.kernel, blocks_per_sm=o.blocks_per_sm, compact_every=o.compact_every,
+                    pool_depth=o.pool_depth, block_size=o.block_size), ms.value
+
+    def event_costs(self, source, digitizer, n_sample=1_000_000, seed=1):
+        """GPU ns per event of each history phase when that event runs alone at
+        full width (gpet_event_costs); returns (ns list of 7, states list of 7)."""
+        ns = (C.c_double * 7)()
+        states = (C.c_uint64 * 7)()
+        _check(load().gpet_event_costs(self._h, C.byref(source_struct(source)),
+                                       C.byref(digitizer_struct(digitizer)), int(n_sample), int(seed), ns, states))
+        return list(ns), list(states)
 
     def close(self):
         if self._h:
@@ -271,7 +293,7 @@ class Result:
     def counts(self) -> dict:
         c = Counts()
         _check(load().gpet_result_counts(self._h, C.byref(c)))
-        return {k: getattr(c, k) for k, _ in Counts._fields_}
+        return _counts_dict(c)
 
     def array(self, which: int, n: int | None = None) -> np.ndarray:
         """Copy one result array to host; n = element count (derived from counts when None)."""
@@ -401,7 +423,7 @@ class Batch:
     def counts(self) -> dict:
         c = Counts()
         _check(load().gpet_batch_counts(self._h, C.byref(c)))
-        return {k: getattr(c, k) for k, _ in Counts._fields_}
+        return _counts_dict(c)
 
     def result(self, job: int) -> Result:
         out = C.c_void_p()
@@ -449,7 +471,7 @@ def sensitivity_map(scanners, positions, digitizer: dict, windows, n_decays: int
                                   C.byref(digitizer_struct(digitizer)), nw,
                                   win.ctypes.data_as(C.POINTER(C.c_double)), int(n_decays), int(seed), C.byref(o),
                                   counts.ctypes.data, sens.ctypes.data, C.byref(tot)))
-    return counts, sens, {k: getattr(tot, k) for k, _ in Counts._fields_}
+    return counts, sens, _counts_dict(tot)
 
 
 def delta_sym(s_a, s_b):
@@ -466,10 +488,11 @@ def delta_sym(s_a, s_b):
 class Server:
     """gpet_server handle: continuous batching of simulation requests."""
 
-    def __init__(self, hbm_budget_bytes=150 * 10**9, workers=2, max_jobs_per_launch=256, **launch_opts):
+    def __init__(self, hbm_budget_bytes=150 * 10**9, workers=1, max_jobs_per_launch=256, max_launch_ms=0.0,
+                 piece_decays=0, **launch_opts):
         L = load()
         cfg = ServerConfig(int(hbm_budget_bytes), int(workers), int(max_jobs_per_launch),
-                           options_struct(**launch_opts))
+                           options_struct(**launch_opts), float(max_launch_ms), int(piece_decays))
         self._h = C.c_void_p()
         _check(L.gpet_server_create(C.byref(cfg), C.byref(self._h)))
         self._keep = {}

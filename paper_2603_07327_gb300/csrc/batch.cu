@@ -38,6 +38,7 @@ int gpet_batch_build_run(Run &R, int32_t n_jobs, gpet_scanner *const *scanners, 
             it = geom_index.emplace(key, (int)R.geoms.size()).first;
             R.geoms.push_back(scanners[j]->g);
             R.geom_pose.push_back(scanners[j]->pose_dev);
+            R.geom_keys.push_back(key);
         }
         J.geom = it->second;
         R.jobs.push_back(J);

@@ -44,7 +44,10 @@ enum : uint32_t { kTagSource = 1u, kTagPhantom = 2u, kTagDetector = 3u, kTagDigi
 // the history is dropped, so no event loop can spin on it.
 // kStatusSortStall: a radix-sort tile copy did not complete within the wait
 // limit; the sort stops and its output is invalid (an internal error).
-enum : int { kStatusOk = 0, kStatusTimeout = 1, kStatusOverflow = 2, kStatusBadPhase = 4, kStatusSortStall = 8 };
+// kStatusLiveStall: a live launch found no new work and no end of the work
+// queue for the whole idle-wait limit; its CTAs stop (an internal error).
+enum : int { kStatusOk = 0, kStatusTimeout = 1, kStatusOverflow = 2, kStatusBadPhase = 4, kStatusSortStall = 8,
+             kStatusLiveStall = 16 };
 
 // ---------------------------------------------------------------------------
 // geometry descriptor (FP32, one per scanner design)
@@ -59,7 +62,10 @@ struct LayerDev {
     int32_t crystal_mat, interval_mat;  // interval_mat also fills the radial gap in front
 };
 
-struct GeomDev {
+// Descriptors start on 128-byte lines: a live launch appends descriptors while
+// its kernel runs, and no line may hold a published and an unpublished one
+// (the L1 cache could otherwise keep the unpublished bytes of a line it loaded).
+struct __align__(128) GeomDev {
     int32_t n_panels, n_layers, n_materials, modules_u, modules_v, readout_level;
     int32_t crystals_per_module, n_crystals;
     float R, W, half_u, half_v;     // inner radius, panel depth, half extents
@@ -81,7 +87,7 @@ static_assert(sizeof(GeomDev) % 16 == 0, "GeomDev is copied in words and staged 
 
 // one simulation job: a scanner design (index into the geometry table), a
 // source and its digitizer settings
-struct JobDev {
+struct __align__(128) JobDev {
     uint64_t seed, n_decays, t_span_ps;
     uint64_t h_base, n_hist;          // histories [h_base, h_base + n_hist) of the run
     int32_t geom, src_kind;
@@ -100,6 +106,12 @@ struct JobDev {
     int32_t ph_buckets, ph_pad;
     // per-crystal tallies of this job
     unsigned long long *tally_count, *tally_efx;
+    // singles of this job: NULL s_raw appends them to the launch's buffer;
+    // else to the job's own (a served request split over several launches
+    // gathers its singles there), counted in *n_singles up to s_cap
+    RawSingle *s_raw;
+    unsigned long long *n_singles;
+    unsigned long long s_cap;
 };
 
 // ---------------------------------------------------------------------------

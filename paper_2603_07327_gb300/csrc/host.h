@@ -62,7 +62,8 @@ struct RunCaps {
 struct RunHeader {
     // det_steps, flights, trials, entered, phantom_steps, hits, wavefront iterations,
     // wavefront lanes, screened flights, singles formed
-    unsigned long long counters[12];
+    // ... singles formed, then (CTA-synchronous kernel) the events run per phase in slots 10 + phase
+    unsigned long long counters[20];
     unsigned long long n_singles, n_hits, n_ovf, n_sorted, n_coinc, next_chunk;
     int status;
     int pad[3];
@@ -109,12 +110,52 @@ struct Run {
     std::vector<unsigned long long> win_counts;
     bool own_stream = false;
     std::function<void()> on_release;    // called once when the run's memory is gone
+    // Live launch (serving loop): the tables have room for `live_cap` jobs,
+    // geometries, tally crystals and posed-panel floats; the host appends jobs
+    // while the transport kernel runs (run_live_append) and closes the launch
+    // (run_live_close) before enqueuing the digitizer.
+    bool live = false;
+    struct LiveCap {
+        int jobs = 0, geoms = 0;
+        int64_t crystals = 0;
+        size_t pose_floats = 0;
+        unsigned chunk = 512;            // histories per chunk
+    } live_cap;
+    cudaStream_t upload_stream = nullptr;  // descriptor uploads and live appends (NULL: the run's stream)
+    void *stage = nullptr;               // pinned host staging of live appends (caller-owned)
+    size_t stage_bytes = 0;
+    unsigned long long *d_live = nullptr;   // [0] published chunks, [1] closed flag, [2] chunks claimed
+    uint64_t live_tail = 0;
+    int64_t live_tally_used = 0;
+    size_t live_pose_used = 0;
+    std::vector<std::string> geom_keys;  // live: descriptor bytes of each geometry (deduplication)
+    // device tables (kept for live appends)
+    JobDev *d_jobs = nullptr;
+    GeomDev *d_geoms = nullptr;
+    unsigned long long *d_chunk_start = nullptr;
+    float *d_pose = nullptr;
+    long long *d_toff = nullptr, *d_tn = nullptr;
+    // digitize-only run: its singles were appended by other launches' kernels
+    // (a served request split over several launches); no transport, and its
+    // zeroed region is cleared by the copy engine when planned
+    bool digitize_only = false;
+    const void *zeros = nullptr;         // pinned host block of zeros (caller-owned) for that clear
+    size_t zeros_bytes = 0;
     ~Run();
 };
 
 int run_plan(Run &R);                  // allocate the arena, upload jobs and geometry
 int run_enqueue(Run &R);               // memset + transport + sort + coincidences (capturable)
+int run_enqueue_transport(Run &R);     // memset + transport
+int run_enqueue_digitizer(Run &R);     // sort + coincidences + per-job statistics
 int run_collect(Run &R);               // synchronise, read the header, map device status
+// live launch: append one job (its scanner's geometry is added when new) and
+// publish it to the running kernel; GPET_ERR_BUSY when a table is full
+int run_live_append(Run &R, const JobDev &J, const gpet_scanner *sc, uint64_t window_ps);
+int run_live_close(Run &R);            // publish the end of the work queue
+int run_live_taken(Run &R, uint64_t *taken);  // chunks the kernel has claimed so far
+// results of a collected run copied into device memory of exactly their size
+std::shared_ptr<Run> run_compact(const Run &R, cudaStream_t st, int *status);
 void run_release(Run &R);
 int run_default_cfg(Run &R, const gpet_options *opt, const gpet_scanner *sc_for_tuning = nullptr);
 

@@ -97,36 +97,47 @@ int run_default_cfg(Run &R, const gpet_options *opt_in, const gpet_scanner *sc) 
 
 int run_plan(Run &R) {
     const int nj = (int)R.jobs.size();
+    // table sizes: the jobs themselves, or a live launch's capacities
+    const int njc = R.live ? std::max(nj, R.live_cap.jobs) : nj;
+    const size_t ngc = R.live ? std::max<size_t>(R.geoms.size(), (size_t)R.live_cap.geoms) : R.geoms.size();
     if (nj < 1) return gpet_fail(GPET_ERR_INVALID_ARG, "no jobs");
-    if (nj > 4095) return gpet_fail(GPET_ERR_INVALID_ARG, "at most 4095 jobs per launch");
+    if (njc > 4095) return gpet_fail(GPET_ERR_INVALID_ARG, "at most 4095 jobs per launch");
     // sort keys: the job index above the time stamps; every job's latest time
     // (its span plus the longest flight a uint32 ps offset holds) must fit below it
-    R.S.job_shift = sort_job_shift(nj);
+    R.S.job_shift = sort_job_shift(njc);
     for (int j = 0; j < nj; ++j)
         if (R.jobs[j].t_span_ps > sort_time_limit(R.S.job_shift) - 0xFFFFFFFFull)
             return gpet_fail(GPET_ERR_INVALID_ARG,
                              "job %d: acquisition of %.0f s does not fit beside %d job bits of the time key "
                              "(at most %.0f s in a launch of %d jobs): use fewer jobs per launch",
                              j, R.jobs[j].t_span_ps * 1e-12, 64 - R.S.job_shift,
-                             (sort_time_limit(R.S.job_shift) - 0xFFFFFFFFull) * 1e-12, nj);
+                             (sort_time_limit(R.S.job_shift) - 0xFFFFFFFFull) * 1e-12, njc);
     // tallies per job
     R.tally_off.resize(nj);
     int64_t tc = 0;
     for (int j = 0; j < nj; ++j) { R.tally_off[j] = tc; tc += R.job_crystals[j]; }
     R.total_crystals = tc;
-    // chunks: about 48 per resident warp, so that warps run out of work within
-    // a small fraction of the launch of one another (32..4096 histories)
+    const int64_t tcc = R.live ? std::max<int64_t>(tc, R.live_cap.crystals) : tc;
+    R.live_tally_used = tc;
     uint64_t total = 0;
     for (auto &J : R.jobs) total += J.n_hist;
-    long long warps = 0;
-    cudaError_t we = transport_resident_warps((int)R.geoms.size(), R.cfg, &warps);
-    if (we != cudaSuccess) return gpet_cuda_fail(we, "transport occupancy query");
-    uint64_t cs = total / std::max<uint64_t>((uint64_t)warps * 48, 1);
-    cs = std::max<uint64_t>(32, std::min<uint64_t>(4096, cs / 32 * 32));
+    uint64_t cs = R.live_cap.chunk;
+    if (!R.live) {
+        // chunks: about 48 per resident warp, so that warps run out of work
+        // within a small fraction of the launch of one another (32..4096)
+        long long warps = 0;
+        cudaError_t we = transport_resident_warps((int)R.geoms.size(), R.cfg, &warps);
+        if (we != cudaSuccess) return gpet_cuda_fail(we, "transport occupancy query");
+        cs = total / std::max<uint64_t>((uint64_t)warps * 48, 1);
+        cs = std::max<uint64_t>(32, std::min<uint64_t>(4096, cs / 32 * 32));
+    }
     R.chunk_size = (unsigned)cs;
-    R.chunk_start.assign(nj + 1, 0);
+    // a live launch's unpublished entries hold ~0: no chunk index reaches them
+    R.chunk_start.assign(njc + 1, ~0ull);
+    R.chunk_start[0] = 0;
     for (int j = 0; j < nj; ++j)
         R.chunk_start[j + 1] = R.chunk_start[j] + (R.jobs[j].n_hist + cs - 1) / cs;
+    R.live_tail = R.chunk_start[nj];
 
     // The first guess of the singles capacity (0.6 per history) may exceed what
     // a long run needs by far (a narrow energy window keeps few singles): it
@@ -153,27 +164,28 @@ int run_plan(Run &R) {
     // zeroed before every launch
     cv.take(R.d_hdr, 1);
     cv.take(R.S.ghist, 8 * 256);
-    cv.take(R.d_tally_count, (size_t)tc);
-    cv.take(R.d_tally_efx, (size_t)tc);
+    cv.take(R.d_tally_count, (size_t)tcc);
+    cv.take(R.d_tally_efx, (size_t)tcc);
     const size_t nwin = R.win_lo.size();
-    if (nwin) cv.take(R.d_win_counts, (size_t)nj * nwin);
+    if (nwin) cv.take(R.d_win_counts, (size_t)njc * nwin);
     R.zero_bytes = align_up(cv.off, 256);
-    JobDev *d_jobs;
-    GeomDev *d_geoms;
-    unsigned long long *d_cs;
-    cv.take(d_jobs, nj);
-    cv.take(d_geoms, R.geoms.size());
-    // posed-panel tables of the geometries in non-repetition mode
+    cv.take(R.d_live, 3);
+    cv.take(R.d_jobs, njc);
+    cv.take(R.d_geoms, ngc);
+    // posed-panel tables of the geometries in non-repetition mode, each on
+    // 128-byte lines of its own (a live launch appends them)
     std::vector<size_t> pose_off(R.geoms.size(), 0);
     size_t pose_floats = 0;
     for (size_t i = 0; i < R.geoms.size(); ++i) {
         pose_off[i] = pose_floats;
-        if (i < R.geom_pose.size()) pose_floats += R.geom_pose[i].size();
+        if (i < R.geom_pose.size()) pose_floats += align_up(R.geom_pose[i].size(), 32);
     }
-    float *d_pose = nullptr;
-    if (pose_floats) cv.take(d_pose, pose_floats);
-    cv.take(d_cs, nj + 1);
-    cv.take(R.d_window, nj);
+    R.live_pose_used = pose_floats;
+    const size_t pfc = R.live ? std::max(pose_floats, R.live_cap.pose_floats) : pose_floats;
+    R.d_pose = nullptr;
+    if (pfc) cv.take(R.d_pose, pfc);
+    cv.take(R.d_chunk_start, njc + 1);
+    cv.take(R.d_window, njc);
     // raw singles
     OutDev &O = R.O;
     cv.take(O.s_raw, cap);
@@ -202,12 +214,14 @@ int run_plan(Run &R) {
     cv.take(C.a, cap / 2 + 1); cv.take(C.b, cap / 2 + 1);
     // per-job statistics
     JobStatsDev &JS = R.JS;
-    long long *d_toff, *d_tn;
-    cv.take(JS.s_off, nj + 1); cv.take(JS.c_off, nj + 1); cv.take(JS.hits, nj);
-    cv.take(d_toff, nj); cv.take(d_tn, nj);
+    cv.take(JS.s_off, njc + 1); cv.take(JS.c_off, njc + 1); cv.take(JS.hits, njc);
+    cv.take(R.d_toff, njc); cv.take(R.d_tn, njc);
     R.arena_bytes = align_up(cv.off, 256);
 
-    cudaError_t e = cudaMallocAsync(&R.arena, R.arena_bytes, R.stream);
+    // a live launch uploads (now and while it runs) on its own stream, which
+    // the running kernel does not block
+    cudaStream_t up = R.upload_stream ? R.upload_stream : R.stream;
+    cudaError_t e = cudaMallocAsync(&R.arena, R.arena_bytes, up);
     if (e != cudaSuccess) {
         R.arena = nullptr;
         return e == cudaErrorMemoryAllocation ? gpet_fail(GPET_ERR_OOM, "device arena of %zu bytes", R.arena_bytes)
@@ -219,11 +233,12 @@ int run_plan(Run &R) {
     rebase(R.d_tally_count, base);
     rebase(R.d_tally_efx, base);
     if (nwin) rebase(R.d_win_counts, base); else R.d_win_counts = nullptr;
-    rebase(d_jobs, base); rebase(d_geoms, base); rebase(d_cs, base); rebase(R.d_window, base);
-    if (pose_floats) rebase(d_pose, base);
+    rebase(R.d_live, base);
+    rebase(R.d_jobs, base); rebase(R.d_geoms, base); rebase(R.d_chunk_start, base); rebase(R.d_window, base);
+    if (pfc) rebase(R.d_pose, base);
     for (size_t i = 0; i < R.geoms.size(); ++i)
         R.geoms[i].pose = (i < R.geom_pose.size() && !R.geom_pose[i].empty())
-                              ? reinterpret_cast<const float4 *>(d_pose + pose_off[i]) : nullptr;
+                              ? reinterpret_cast<const float4 *>(R.d_pose + pose_off[i]) : nullptr;
     rebase(O.s_raw, base);
     if (hcap) {
         rebase(O.hit_h, base); rebase(O.hit_t, base); rebase(O.hit_gstep, base); rebase(O.hit_crystal, base);
@@ -238,14 +253,16 @@ int run_plan(Run &R) {
     rebase(SD.t, base); rebase(SD.h, base); rebase(SD.unit, base); rebase(SD.panel, base); rebase(SD.job, base);
     rebase(SD.e, base); rebase(SD.eraw, base); rebase(SD.doi, base);
     rebase(C.flag, base); rebase(C.tile_cnt, base); rebase(C.a, base); rebase(C.b, base);
-    rebase(JS.s_off, base); rebase(JS.c_off, base); rebase(JS.hits, base); rebase(d_toff, base); rebase(d_tn, base);
+    rebase(JS.s_off, base); rebase(JS.c_off, base); rebase(JS.hits, base); rebase(R.d_toff, base);
+    rebase(R.d_tn, base);
     JS.n_jobs = nj;
     JS.tally_count = R.d_tally_count;
-    JS.tally_off = d_toff;
-    JS.tally_n = d_tn;
+    JS.tally_off = R.d_toff;
+    JS.tally_n = R.d_tn;
 
     // wire the structs
     for (int j = 0; j < nj; ++j) {
+        if (R.jobs[j].s_raw) continue;  // a job with its own singles buffer brings its own tallies
         R.jobs[j].tally_count = R.d_tally_count + R.tally_off[j];
         R.jobs[j].tally_efx = R.d_tally_efx + R.tally_off[j];
     }
@@ -259,14 +276,17 @@ int run_plan(Run &R) {
     O.counters = H->counters;
     O.status = &H->status;
     WorkDev &W = R.W;
-    W.jobs = d_jobs;
-    W.n_jobs = nj;
-    W.geoms = d_geoms;
+    W.jobs = R.d_jobs;
+    W.n_jobs = njc;
+    W.geoms = R.d_geoms;
     W.n_geoms = (int)R.geoms.size();
-    W.chunk_start = d_cs;
-    W.total_chunks = R.chunk_start[nj];
+    W.chunk_start = R.d_chunk_start;
+    W.total_chunks = R.live ? 0 : R.chunk_start[nj];
     W.next_chunk = &H->next_chunk;
     W.chunk_size = R.chunk_size;
+    W.live_tail = R.live ? R.d_live : nullptr;
+    W.live_closed = R.live ? reinterpret_cast<const int *>(R.d_live + 1) : nullptr;
+    W.live_taken = R.live ? R.d_live + 2 : nullptr;
     int st = gpet_xs_table(&W.gtab, &W.ln_emin, &W.inv_h);
     if (st != GPET_OK) return st;
     S.max_tiles = tiles;
@@ -279,49 +299,85 @@ int run_plan(Run &R) {
     C.window_ps = R.d_window;
 
     // upload descriptors (small; stream-ordered after the allocation)
-    e = cudaMemcpyAsync(d_jobs, R.jobs.data(), sizeof(JobDev) * nj, cudaMemcpyHostToDevice, R.stream);
+    e = cudaMemcpyAsync(R.d_jobs, R.jobs.data(), sizeof(JobDev) * nj, cudaMemcpyHostToDevice, up);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_geoms, R.geoms.data(), sizeof(GeomDev) * R.geoms.size(), cudaMemcpyHostToDevice,
-                            R.stream);
+        e = cudaMemcpyAsync(R.d_geoms, R.geoms.data(), sizeof(GeomDev) * R.geoms.size(), cudaMemcpyHostToDevice, up);
     for (size_t i = 0; i < R.geoms.size() && e == cudaSuccess; ++i)
         if (i < R.geom_pose.size() && !R.geom_pose[i].empty())
-            e = cudaMemcpyAsync(d_pose + pose_off[i], R.geom_pose[i].data(), sizeof(float) * R.geom_pose[i].size(),
-                                cudaMemcpyHostToDevice, R.stream);
+            e = cudaMemcpyAsync(R.d_pose + pose_off[i], R.geom_pose[i].data(), sizeof(float) * R.geom_pose[i].size(),
+                                cudaMemcpyHostToDevice, up);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_cs, R.chunk_start.data(), sizeof(unsigned long long) * (nj + 1),
-                            cudaMemcpyHostToDevice, R.stream);
+        e = cudaMemcpyAsync(R.d_chunk_start, R.chunk_start.data(), sizeof(unsigned long long) * (njc + 1),
+                            cudaMemcpyHostToDevice, up);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(R.d_window, R.windows.data(), sizeof(uint64_t) * nj, cudaMemcpyHostToDevice, R.stream);
+        e = cudaMemcpyAsync(R.d_window, R.windows.data(), sizeof(uint64_t) * nj, cudaMemcpyHostToDevice, up);
     std::vector<long long> toff(R.tally_off.begin(), R.tally_off.end()), tn(R.job_crystals.begin(), R.job_crystals.end());
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_toff, toff.data(), sizeof(long long) * nj, cudaMemcpyHostToDevice, R.stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tn, tn.data(), sizeof(long long) * nj, cudaMemcpyHostToDevice, R.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(R.stream);  // host vectors may change after return
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.d_toff, toff.data(), sizeof(long long) * nj, cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.d_tn, tn.data(), sizeof(long long) * nj, cudaMemcpyHostToDevice, up);
+    const unsigned long long live0[3] = {R.live_tail, 0ull, 0ull};  // published chunks, closed, claimed
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.d_live, live0, sizeof(live0), cudaMemcpyHostToDevice, up);
+    // a digitize-only run's singles and tallies are written by other launches'
+    // kernels, possibly running now: the copy engine clears its zeroed region
+    for (size_t off = 0; R.digitize_only && off < R.zero_bytes && e == cudaSuccess; off += R.zeros_bytes) {
+        if (!R.zeros || !R.zeros_bytes) return gpet_fail(GPET_ERR_INVALID_ARG, "digitize-only run without zeros");
+        e = cudaMemcpyAsync(base + off, R.zeros, std::min(R.zeros_bytes, R.zero_bytes - off), cudaMemcpyHostToDevice,
+                            up);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(up);  // host vectors may change after return
     R.h2d_bytes = sizeof(JobDev) * nj + sizeof(GeomDev) * R.geoms.size() + sizeof(float) * pose_floats +
-                  sizeof(unsigned long long) * (nj + 1) +
+                  sizeof(unsigned long long) * (njc + 1) +
                   sizeof(uint64_t) * nj + 2 * sizeof(long long) * nj;
     if (e != cudaSuccess) return gpet_cuda_fail(e, "upload of the job descriptors");
+    if (R.live) R.geom_keys.resize(R.geoms.size());
     return GPET_OK;
 }
 
-int run_enqueue(Run &R) {
+static int stage_events(Run &R, unsigned *rec_flags) {
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 3 && e == cudaSuccess; ++i)
         if (!R.ev[i]) e = cudaEventCreate(&R.ev[i]);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaEventCreate");
-    e = cudaMemsetAsync(R.arena, 0, R.zero_bytes, R.stream);
-    if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaMemsetAsync");
     // under stream capture the stage events must be external records, which
     // the replayed graph really records (a plain record there only orders
     // work); outside capture the external flag is refused, so record plainly
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     e = cudaStreamIsCapturing(R.stream, &cap);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaStreamIsCapturing");
-    const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    *rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    return GPET_OK;
+}
+
+int run_enqueue_transport(Run &R) {
+    unsigned rec_flags = 0;
+    int st = stage_events(R, &rec_flags);
+    if (st != GPET_OK) return st;
+    cudaError_t e = cudaMemsetAsync(R.arena, 0, R.zero_bytes, R.stream);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaMemsetAsync");
     e = cudaEventRecordWithFlags(R.ev[0], R.stream, rec_flags);
     if (e == cudaSuccess) e = launch_transport(R.W, R.O, R.cfg, R.stream);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "transport launch");
     e = cudaEventRecordWithFlags(R.ev[1], R.stream, rec_flags);
-    if (e == cudaSuccess) e = launch_sort_coinc(R.S, R.SD, R.C, R.cfg.sm_count, R.stream);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaEventRecord");
+    return GPET_OK;
+}
+
+int run_enqueue(Run &R) {
+    int st = run_enqueue_transport(R);
+    return st == GPET_OK ? run_enqueue_digitizer(R) : st;
+}
+
+int run_enqueue_digitizer(Run &R) {
+    unsigned rec_flags = 0;
+    int st = stage_events(R, &rec_flags);
+    if (st != GPET_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (R.digitize_only) {  // no transport: both transport marks here
+        e = cudaEventRecordWithFlags(R.ev[0], R.stream, rec_flags);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(R.ev[1], R.stream, rec_flags);
+        if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaEventRecord");
+    }
+    R.JS.n_jobs = (int)R.jobs.size();
+    e = launch_sort_coinc(R.S, R.SD, R.C, R.cfg.sm_count, R.stream);
     if (e == cudaSuccess) e = launch_job_stats(R.SD, R.C, R.JS, R.stream);
     if (e == cudaSuccess && R.d_win_counts) {
         WinDev win{};
@@ -339,18 +395,22 @@ int run_collect(Run &R) {
     R.s_off.resize(nj + 1);
     R.c_off.resize(nj + 1);
     R.job_hits.resize(nj);
-    cudaError_t e = cudaMemcpyAsync(&R.h_hdr, R.d_hdr, sizeof(RunHeader), cudaMemcpyDeviceToHost, R.stream);
+    // A run with an upload stream (the serving loop's) is read back on that
+    // stream, once the caller has seen its work complete: its own stream may
+    // already hold the next launch.
+    cudaStream_t rs = R.upload_stream ? R.upload_stream : R.stream;
+    cudaError_t e = cudaMemcpyAsync(&R.h_hdr, R.d_hdr, sizeof(RunHeader), cudaMemcpyDeviceToHost, rs);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(R.s_off.data(), R.JS.s_off, 8 * (nj + 1), cudaMemcpyDeviceToHost, R.stream);
+        e = cudaMemcpyAsync(R.s_off.data(), R.JS.s_off, 8 * (nj + 1), cudaMemcpyDeviceToHost, rs);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(R.c_off.data(), R.JS.c_off, 8 * (nj + 1), cudaMemcpyDeviceToHost, R.stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(R.job_hits.data(), R.JS.hits, 8 * nj, cudaMemcpyDeviceToHost, R.stream);
+        e = cudaMemcpyAsync(R.c_off.data(), R.JS.c_off, 8 * (nj + 1), cudaMemcpyDeviceToHost, rs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.job_hits.data(), R.JS.hits, 8 * nj, cudaMemcpyDeviceToHost, rs);
     if (e == cudaSuccess && R.d_win_counts) {
         R.win_counts.resize(nj * R.win_lo.size());
         e = cudaMemcpyAsync(R.win_counts.data(), R.d_win_counts, 8 * R.win_counts.size(), cudaMemcpyDeviceToHost,
-                            R.stream);
+                            rs);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(R.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(rs);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "run read-back");
     if (R.ev[0] && cudaEventElapsedTime(&R.transport_ms, R.ev[0], R.ev[1]) != cudaSuccess) {
         R.transport_ms = -1.f;
@@ -368,6 +428,8 @@ int run_collect(Run &R) {
                          H.n_singles, R.O.s_cap, H.n_hits, R.O.hit_cap, H.n_ovf, R.O.ovf_cap);
     if (H.status & kStatusBadPhase)
         return gpet_fail(GPET_ERR_CUDA, "internal error: a history reached a phase no event handles");
+    if (H.status & kStatusLiveStall)
+        return gpet_fail(GPET_ERR_CUDA, "internal error: a live launch waited too long for work or its end");
     if (H.status & kStatusSortStall)
         return gpet_fail(GPET_ERR_CUDA, "internal error: a time-sort tile copy did not complete");
     if (H.status & kStatusOverflow)
@@ -459,6 +521,179 @@ void fill_counts(const Run &R, int job, uint64_t n_decays, int64_t n_crystals, g
     c->wave_lanes = H.counters[7];
     c->screened_flights = H.counters[8];
     c->singles_formed = H.counters[9];
+    for (int p = 0; p < 7; ++p) c->phase_events[p] = H.counters[10 + p];
+}
+
+// ---------------------------------------------------------------------------
+// live launch: jobs appended while the transport kernel runs
+// ---------------------------------------------------------------------------
+
+// Staged host bytes of one append, copied in this order on the upload stream:
+// the table entries first, the published chunk count last.
+struct LiveStage {
+    JobDev job;
+    GeomDev geom;
+    unsigned long long chunk_end, window, tail;
+    long long toff, tn;
+};
+
+int run_live_append(Run &R, const JobDev &J_in, const gpet_scanner *sc, uint64_t window_ps) {
+    if (!R.live || !R.arena || !sc) return gpet_fail(GPET_ERR_INVALID_ARG, "not a live launch");
+    const size_t pose_need = sc->pose_dev.empty() ? 0 : align_up(sc->pose_dev.size(), 32);
+    if (!R.stage || R.stage_bytes < sizeof(LiveStage) + sizeof(float) * pose_need)
+        return gpet_fail(GPET_ERR_INVALID_ARG, "live launch without a large enough staging buffer");
+    const int j = (int)R.jobs.size();
+    if (j >= R.live_cap.jobs) return gpet_fail(GPET_ERR_BUSY, "live launch: job table full");
+    if (J_in.t_span_ps > sort_time_limit(R.S.job_shift) - 0xFFFFFFFFull)
+        return gpet_fail(GPET_ERR_BUSY, "live launch: acquisition too long for its time key");
+    const std::string key = gpet_geometry_key(sc);
+    int gi = -1;
+    for (size_t i = 0; i < R.geom_keys.size(); ++i)
+        if (R.geom_keys[i] == key) { gi = (int)i; break; }
+    const bool new_geom = gi < 0;
+    if (new_geom && ((int)R.geoms.size() >= R.live_cap.geoms ||
+                     R.live_pose_used + pose_need > std::max(R.live_cap.pose_floats, R.live_pose_used)))
+        return gpet_fail(GPET_ERR_BUSY, "live launch: geometry table full");
+    // a job with its own singles buffer brings its own tallies
+    const int64_t crystals = J_in.s_raw ? 0 : sc->n_crystals;
+    if (R.live_tally_used + crystals > R.live_cap.crystals)
+        return gpet_fail(GPET_ERR_BUSY, "live launch: tally space full");
+    LiveStage *S = static_cast<LiveStage *>(R.stage);
+    float *pose_stage = reinterpret_cast<float *>(S + 1);
+    if (new_geom) {
+        gi = (int)R.geoms.size();
+        S->geom = sc->g;
+        S->geom.pose = pose_need ? reinterpret_cast<const float4 *>(R.d_pose + R.live_pose_used) : nullptr;
+        if (pose_need) std::memcpy(pose_stage, sc->pose_dev.data(), sizeof(float) * sc->pose_dev.size());
+    }
+    S->job = J_in;
+    S->job.geom = gi;
+    if (!J_in.s_raw) {
+        S->job.tally_count = R.d_tally_count + R.live_tally_used;
+        S->job.tally_efx = R.d_tally_efx + R.live_tally_used;
+    }
+    const uint64_t chunks = (J_in.n_hist + R.chunk_size - 1) / R.chunk_size;
+    S->chunk_end = R.live_tail + chunks;
+    S->window = window_ps;
+    S->tail = S->chunk_end;
+    S->toff = R.live_tally_used;
+    S->tn = crystals;
+    cudaStream_t up = R.upload_stream;
+    cudaError_t e = cudaSuccess;
+    if (new_geom) {
+        e = cudaMemcpyAsync(R.d_geoms + gi, &S->geom, sizeof(GeomDev), cudaMemcpyHostToDevice, up);
+        if (e == cudaSuccess && pose_need)
+            e = cudaMemcpyAsync(R.d_pose + R.live_pose_used, pose_stage, sizeof(float) * sc->pose_dev.size(),
+                                cudaMemcpyHostToDevice, up);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.d_jobs + j, &S->job, sizeof(JobDev), cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.d_window + j, &S->window, 8, cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.d_toff + j, &S->toff, 8, cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.d_tn + j, &S->tn, 8, cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.d_chunk_start + j + 1, &S->chunk_end, 8, cudaMemcpyHostToDevice, up);
+    // copies of one stream complete in order: the tail lands after the entries
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.d_live, &S->tail, 8, cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(up);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "live launch append");
+    if (new_geom) {
+        R.geoms.push_back(S->geom);
+        R.geom_pose.push_back(sc->pose_dev);
+        R.geom_keys.push_back(key);
+        R.live_pose_used += pose_need;
+        R.h2d_bytes += sizeof(GeomDev) + sizeof(float) * sc->pose_dev.size();
+    }
+    R.jobs.push_back(S->job);
+    R.job_crystals.push_back(crystals);
+    R.windows.push_back(window_ps);
+    R.tally_off.push_back(R.live_tally_used);
+    R.live_tally_used += crystals;
+    R.total_crystals = R.live_tally_used;
+    R.chunk_start[j + 1] = S->chunk_end;
+    R.live_tail = S->chunk_end;
+    R.h2d_bytes += sizeof(JobDev) + 5 * 8;
+    return GPET_OK;
+}
+
+int run_live_close(Run &R) {
+    if (!R.live || !R.arena || !R.stage) return gpet_fail(GPET_ERR_INVALID_ARG, "not a live launch");
+    unsigned long long *one = static_cast<unsigned long long *>(R.stage);
+    *one = 1ull;  // the closed flag is the low int of its word (little-endian)
+    cudaError_t e = cudaMemcpyAsync(R.d_live + 1, one, 8, cudaMemcpyHostToDevice, R.upload_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(R.upload_stream);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "live launch close");
+    return GPET_OK;
+}
+
+// A copy of a collected run's results -- time-ordered singles, coincidences,
+// tallies and the per-job segments -- in device memory of exactly their size,
+// made by the copy engine on `st`.  The serving loop hands out views of the
+// copy, so that results a client keeps do not hold a launch's buffers.
+std::shared_ptr<Run> run_compact(const Run &R, cudaStream_t st, int *status) {
+    auto C = std::make_shared<Run>();
+    const size_t nj = R.jobs.size();
+    if (R.s_off.size() != nj + 1 || R.c_off.size() != nj + 1) {
+        *status = gpet_fail(GPET_ERR_INVALID_ARG, "compact copy of a run without collected results");
+        return nullptr;
+    }
+    const uint64_t ns = R.s_off[nj], nc = R.c_off[nj];
+    const size_t tc = (size_t)R.total_crystals;
+    Carver cv;
+    SinglesDev &SD = C->SD;
+    cv.take(SD.t, ns); cv.take(SD.h, ns); cv.take(SD.unit, ns); cv.take(SD.panel, ns); cv.take(SD.job, ns);
+    cv.take(SD.e, ns); cv.take(SD.eraw, ns); cv.take(SD.doi, ns);
+    cv.take(C->C.a, nc); cv.take(C->C.b, nc);
+    cv.take(C->d_tally_count, tc); cv.take(C->d_tally_efx, tc);
+    C->arena_bytes = align_up(cv.off, 256);
+    cudaError_t e = cudaMallocAsync(&C->arena, C->arena_bytes, st);
+    if (e != cudaSuccess) {
+        C->arena = nullptr;
+        *status = e == cudaErrorMemoryAllocation ? gpet_fail(GPET_ERR_OOM, "compact copy of %zu bytes", C->arena_bytes)
+                                                 : gpet_cuda_fail(e, "cudaMallocAsync");
+        return nullptr;
+    }
+    char *base = static_cast<char *>(C->arena);
+    rebase(SD.t, base); rebase(SD.h, base); rebase(SD.unit, base); rebase(SD.panel, base); rebase(SD.job, base);
+    rebase(SD.e, base); rebase(SD.eraw, base); rebase(SD.doi, base);
+    rebase(C->C.a, base); rebase(C->C.b, base);
+    rebase(C->d_tally_count, base); rebase(C->d_tally_efx, base);
+    struct Part { void *dst; const void *src; size_t bytes; };
+    const Part parts[] = {{SD.t, R.SD.t, 8 * ns}, {SD.h, R.SD.h, 8 * ns}, {SD.unit, R.SD.unit, 4 * ns},
+                          {SD.panel, R.SD.panel, 4 * ns}, {SD.job, R.SD.job, 4 * ns}, {SD.e, R.SD.e, 4 * ns},
+                          {SD.eraw, R.SD.eraw, 4 * ns}, {SD.doi, R.SD.doi, 4 * ns}, {C->C.a, R.C.a, 4 * nc},
+                          {C->C.b, R.C.b, 4 * nc}, {C->d_tally_count, R.d_tally_count, 8 * tc},
+                          {C->d_tally_efx, R.d_tally_efx, 8 * tc}};
+    for (const Part &p : parts)
+        if (e == cudaSuccess && p.bytes) e = cudaMemcpyAsync(p.dst, p.src, p.bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        *status = gpet_cuda_fail(e, "compact copy of a run's results");
+        return nullptr;
+    }
+    C->device = R.device;
+    C->jobs = R.jobs;
+    C->job_crystals = R.job_crystals;
+    C->tally_off = R.tally_off;
+    C->total_crystals = R.total_crystals;
+    C->s_off = R.s_off;
+    C->c_off = R.c_off;
+    C->job_hits = R.job_hits;
+    C->h_hdr = R.h_hdr;
+    C->transport_ms = R.transport_ms;
+    C->digitizer_ms = R.digitizer_ms;
+    C->h2d_bytes = R.h2d_bytes;
+    C->keep_hits = false;
+    *status = GPET_OK;
+    return C;
+}
+
+int run_live_taken(Run &R, uint64_t *taken) {
+    if (!R.live || !R.arena || !R.stage) return gpet_fail(GPET_ERR_INVALID_ARG, "not a live launch");
+    unsigned long long *v = static_cast<unsigned long long *>(R.stage);
+    cudaError_t e = cudaMemcpyAsync(v, R.d_live + 2, 8, cudaMemcpyDeviceToHost, R.upload_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(R.upload_stream);
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "live launch progress read");
+    *taken = *v;
+    return GPET_OK;
 }
 
 }  // namespace gpet

@@ -1,29 +1,38 @@
-// server.cu -- serving loop with continuous batching.
+// server.cu -- serving loop with continuous batching into live launches.
 //
 // Requests (scanner design + source + digitizer + decay count + seed) arrive
-// through gpet_server_submit from any host thread.  Worker threads, each with
-// its own CUDA stream, repeatedly take the queued requests that fit the HBM
-// budget (first come, first served), run them together as one batched launch
-// (one persistent transport kernel over all their histories, one segmented
-// time sort, one coincidence pass) and publish one result per request.  While
-// one worker's batch is on the GPU the other admits the requests that arrived
-// meanwhile and launches them, so their work overlaps on the device.  A
-// request's device memory counts against the budget from admission until its
-// result is freed.  Because every random number is addressed by (seed,
-// history), a request's result is the same alone and in any mix.
+// through gpet_server_submit from any host thread.  One pipeline thread keeps
+// a transport launch open on the GPU and appends the requests that arrive to
+// its work table while its kernel runs (a live launch: the persistent warps
+// take the new jobs' chunks as they are published, see WorkDev).  A request of
+// more than piece_decays histories is split into history ranges that join
+// successive launches, one range per request and pass so that small requests
+// are not queued behind large ones; the kernel writes the singles and tallies
+// of those pieces straight into the request's own device buffers, so the
+// request's state stays on the device between pieces, and its time sort and
+// coincidence sorting run once, after its last piece.  A launch takes new work
+// until it is max_launch_ms old or a table is full, or until the queue is empty
+// and every published chunk has been claimed; it is then closed, its time sort,
+// coincidence sorting and per-job statistics are enqueued behind its transport
+// on the same stream, and the next launch opens behind those.  Device memory
+// counts against the budget per launch arena and per split request, from
+// allocation until the results that view it are freed.  Every random number is
+// addressed by (seed, history), so a request's result is the same alone and in
+// any mix, whole or in pieces.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 
 #include "host.h"
 
 using namespace gpet;
-
 
 namespace {
 
@@ -32,11 +41,15 @@ using Clock = std::chrono::steady_clock;
 struct Req {
     uint64_t id = 0;
     gpet_scanner *sc = nullptr;
-    gpet_source src{};
-    gpet_digitizer dg{};
-    uint64_t n = 0, seed = 0;
+    uint64_t n = 0;
     size_t est = 0;
-    uint64_t span_ps = 0;             // acquisition span (decay times lie in [0, span_ps))
+    JobDev J{};                       // the whole request as one job (validated at submission)
+    uint64_t window_ps = 0;
+    uint64_t next_h = 0;              // first history not yet handed to a launch
+    bool split = false;               // runs in pieces through its own buffers
+    std::shared_ptr<Run> own;         // split request: singles buffer, tallies and digitizer
+    int piece_status = GPET_OK;       // error of a launch that carried one of its pieces
+    std::string piece_error;
     bool done = false;
     int status = GPET_OK;
     std::string error;
@@ -47,10 +60,38 @@ struct Req {
 // budget accounting shared with the release callbacks of the runs
 struct Core {
     std::mutex mu;
-    std::condition_variable cv;       // queue changes and memory releases
+    std::condition_variable cv;       // submissions, memory releases, stop
     std::condition_variable done_cv;  // request completions
     size_t budget = 0, in_use = 0, peak = 0;
 };
+
+// one live launch
+struct Launch {
+    std::shared_ptr<Run> R;
+    std::vector<std::pair<Req *, int>> whole;   // requests run whole here: (request, job)
+    std::vector<Req *> pieces;                  // split requests with a piece here
+    std::vector<Req *> finishing;               // split requests whose last piece is here
+    Clock::time_point t_open;
+    uint64_t singles_guess = 0;                 // expected singles of the whole requests
+    bool full = false;
+    cudaEvent_t done = nullptr;
+    ~Launch() {
+        if (done) cudaEventDestroy(done);
+    }
+};
+
+// the pipeline's streams and pinned host blocks
+struct Pipe {
+    cudaStream_t gpu = nullptr;       // transport launches and every digitizer, in order
+    cudaStream_t up = nullptr;        // uploads, appends and read-backs (never blocked by a kernel)
+    cudaStream_t fb = nullptr;        // whole-request re-runs after an overflow
+    void *stage = nullptr;
+    size_t stage_bytes = 64 << 10;
+    void *zeros = nullptr;
+    size_t zeros_bytes = 8 << 20;
+};
+
+constexpr double kGuessPerDecay = 0.6;   // first guess of singles per history (as the plain runs)
 
 }  // namespace
 
@@ -58,120 +99,449 @@ struct gpet_server {
     std::shared_ptr<Core> core;
     gpet_options opt{};
     int max_jobs = 256;
-    std::deque<Req *> queue;
+    double max_launch_ms = 20.0;
+    uint64_t piece = 4000000;
+    uint64_t launch_singles = 0;      // singles one launch's buffer holds
+    int64_t launch_crystals = 0;      // tally crystals one launch holds
+    std::deque<Req *> queue;         // requests with histories not yet handed to a launch
     std::map<uint64_t, Req *> reqs;
     uint64_t next_id = 1;
     bool stop = false;
-    std::vector<std::thread> workers;
+    std::thread pipeline;
     gpet_server_stats stats{};
     int device = 0;
 };
 
-static void worker_main(gpet_server *S, int widx) {
-    cudaSetDevice(S->device);
-    cudaStream_t stream = nullptr;
-    cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+namespace {
+
+// charge `bytes` of the budget to run R until its memory is released
+void charge(gpet_server *S, Run &R, size_t bytes) {
     Core &C = *S->core;
+    {
+        std::lock_guard<std::mutex> lk(C.mu);
+        C.in_use += bytes;
+        C.peak = std::max(C.peak, C.in_use);
+    }
+    std::weak_ptr<Core> wc = S->core;
+    R.on_release = [wc, bytes]() {
+        if (auto c = wc.lock()) {
+            std::lock_guard<std::mutex> l2(c->mu);
+            c->in_use -= bytes;
+            c->cv.notify_all();
+        }
+    };
+}
+
+bool budget_allows(gpet_server *S, size_t bytes) {
+    Core &C = *S->core;
+    std::lock_guard<std::mutex> lk(C.mu);
+    return C.in_use + bytes <= C.budget || C.in_use == 0;
+}
+
+// hand a finished request its result (or error); caller does not hold the lock
+void publish(gpet_server *S, Req *r, int st, const std::string &err, std::shared_ptr<Run> run, int job) {
+    Core &C = *S->core;
+    // the request's own run is let go outside the lock: its release callback takes it
+    std::shared_ptr<Run> drop = std::move(r->own);
+    gpet_result *res = nullptr;
+    if (st == GPET_OK) {
+        res = new (std::nothrow) gpet_result();
+        if (res) {
+            res->run = std::move(run);
+            res->job = job;
+            fill_counts(*res->run, job, r->n, r->sc->n_crystals, &res->counts);
+            res->counts.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
+        }
+    }
+    std::lock_guard<std::mutex> lk(C.mu);
+    r->status = st;
+    if (st == GPET_OK && !res) {
+        r->status = GPET_ERR_OOM;
+        r->error = "host allocation of a result failed";
+    } else if (st != GPET_OK) {
+        r->error = err;
+    }
+    r->result = res;
+    r->done = true;
+    S->stats.completed++;
+    S->stats.pairs_completed += r->n;
+    C.done_cv.notify_all();
+}
+
+// the whole request in a fixed launch of its own (after an overflow of a live one)
+int run_whole(gpet_server *S, Pipe &P, Req *r, std::shared_ptr<Run> &out) {
+    auto R = std::make_shared<Run>();
+    gpet_options o = S->opt;
+    o.stream = P.fb;
+    int st = run_default_cfg(*R, &o, r->sc);
+    if (st != GPET_OK) return st;
+    R->jobs = {r->J};
+    R->geoms = {r->sc->g};
+    R->geom_pose = {r->sc->pose_dev};
+    R->job_crystals = {r->sc->n_crystals};
+    R->windows = {r->window_ps};
+    R->caps.singles = std::max<uint64_t>(65536, (uint64_t)(r->n * kGuessPerDecay));
+    R->caps.ovf = std::max<uint64_t>(4096, r->n / 256);
+    st = run_with_retry(*R);
+    if (st != GPET_OK) return st;
+    charge(S, *R, R->arena_bytes);
+    out = R;
+    return GPET_OK;
+}
+
+// a split request's own run: singles buffer and tallies that its pieces fill
+int make_own(gpet_server *S, Pipe &P, Req *r) {
+    auto M = std::make_shared<Run>();
+    gpet_options o = S->opt;
+    o.stream = P.gpu;
+    int st = run_default_cfg(*M, &o, r->sc);
+    if (st != GPET_OK) return st;
+    M->jobs = {r->J};
+    M->geoms = {r->sc->g};
+    M->geom_pose = {r->sc->pose_dev};
+    M->job_crystals = {r->sc->n_crystals};
+    M->windows = {r->window_ps};
+    M->caps.singles = std::max<uint64_t>(65536, (uint64_t)(r->n * kGuessPerDecay));
+    M->caps.ovf = 1;
+    M->digitize_only = true;
+    M->upload_stream = P.up;
+    M->zeros = P.zeros;
+    M->zeros_bytes = P.zeros_bytes;
+    st = run_plan(*M);
+    if (st != GPET_OK) return st;
+    charge(S, *M, M->arena_bytes);
+    r->own = M;
+    return GPET_OK;
+}
+
+// arena bytes of one live launch of this server
+size_t launch_bytes(gpet_server *S) {
+    return run_footprint((uint64_t)(S->launch_singles / kGuessPerDecay), S->launch_crystals, S->max_jobs, 64, false);
+}
+
+// Start a live launch with `J` as its first job; returns null on an error
+// (reported to the request by the caller).
+std::unique_ptr<Launch> open_launch(gpet_server *S, Pipe &P, const JobDev &J, const gpet_scanner *sc,
+                                    uint64_t window_ps, int64_t crystals, int &st) {
+    auto L = std::make_unique<Launch>();
+    L->R = std::make_shared<Run>();
+    Run &R = *L->R;
+    gpet_options o = S->opt;
+    o.stream = P.gpu;
+    st = run_default_cfg(R, &o, sc);
+    if (st != GPET_OK) return nullptr;
+    R.live = true;
+    R.live_cap.jobs = S->max_jobs;
+    R.live_cap.geoms = 64;
+    R.live_cap.crystals = S->launch_crystals;
+    R.live_cap.pose_floats = 64 * 16 * kMaxPanels;
+    R.upload_stream = P.up;
+    R.stage = P.stage;
+    R.stage_bytes = P.stage_bytes;
+    R.jobs = {J};
+    R.geoms = {sc->g};
+    R.geom_pose = {sc->pose_dev};
+    R.geom_keys = {gpet_geometry_key(sc)};
+    R.job_crystals = {crystals};
+    R.windows = {window_ps};
+    R.caps.singles = S->launch_singles;
+    R.caps.guess = false;
+    R.caps.ovf = std::max<uint64_t>(4096, S->launch_singles / 64);
+    st = run_plan(R);
+    if (st == GPET_OK) st = run_enqueue_transport(R);
+    if (st != GPET_OK) return nullptr;
+    charge(S, R, R.arena_bytes);
+    L->t_open = Clock::now();
+    return L;
+}
+
+// Hand one pass of queued work to the open launch (opening one when none is):
+// a whole request, or the next piece of a split one.  Returns false when the
+// request must wait (budget, a full launch).
+bool admit(gpet_server *S, Pipe &P, std::unique_ptr<Launch> &L, Req *r, bool pieces_ok) {
+    JobDev J = r->J;
+    int64_t crystals = r->sc->n_crystals;
+    uint64_t guess = 0;
+    if (!r->split) {
+        guess = std::max<uint64_t>(64, (uint64_t)(r->n * kGuessPerDecay));
+        if (L && L->singles_guess + guess > S->launch_singles) {
+            L->full = true;
+            return false;
+        }
+    } else {
+        if (!pieces_ok) return false;
+        if (!r->own) {
+            const size_t need = run_footprint(r->n, r->sc->n_crystals, 1, 1, false);
+            if (!budget_allows(S, need)) return false;
+            const int st = make_own(S, P, r);
+            if (st != GPET_OK) {
+                std::lock_guard<std::mutex> lk(S->core->mu);
+                r->next_h = r->n;  // nothing more of it runs
+                r->piece_status = st;
+                r->piece_error = gpet_last_error();
+                return true;
+            }
+        }
+        const uint64_t h1 = std::min(r->n, r->next_h + S->piece);
+        J.h_base = r->next_h;
+        J.n_hist = h1 - r->next_h;
+        Run &M = *r->own;
+        J.s_raw = M.O.s_raw;
+        J.n_singles = &M.d_hdr->n_singles;
+        J.s_cap = M.O.s_cap;
+        J.tally_count = M.d_tally_count;
+        J.tally_efx = M.d_tally_efx;
+        crystals = 0;
+    }
+    int job = 0;
+    if (!L) {
+        if (!budget_allows(S, launch_bytes(S))) return false;
+        int st = GPET_OK;
+        L = open_launch(S, P, J, r->sc, r->window_ps, crystals, st);
+        if (!L) {
+            std::lock_guard<std::mutex> lk(S->core->mu);
+            r->piece_status = st;
+            r->piece_error = gpet_last_error();
+            r->next_h = r->n;
+            return true;
+        }
+    } else {
+        const int st = run_live_append(*L->R, J, r->sc, r->window_ps);
+        if (st == GPET_ERR_BUSY) {
+            L->full = true;
+            return false;
+        }
+        if (st != GPET_OK) {
+            std::lock_guard<std::mutex> lk(S->core->mu);
+            r->piece_status = st;
+            r->piece_error = gpet_last_error();
+            r->next_h = r->n;
+            return true;
+        }
+        job = (int)L->R->jobs.size() - 1;
+        std::lock_guard<std::mutex> lk(S->core->mu);
+        S->stats.live_appends++;
+    }
+    if (!r->split) {
+        L->whole.push_back({r, job});
+        L->singles_guess += guess;
+        r->next_h = r->n;
+    } else {
+        r->next_h += J.n_hist;
+        L->pieces.push_back(r);
+        if (r->next_h == r->n) L->finishing.push_back(r);
+        std::lock_guard<std::mutex> lk(S->core->mu);
+        S->stats.pieces++;
+    }
+    return true;
+}
+
+// no more appends: digitizers of the launch and of the split requests it
+// finishes go behind its transport, then an event marks the end
+int close_launch(gpet_server *S, Launch &L) {
+    Run &R = *L.R;
+    int st = run_live_close(R);
+    if (st == GPET_OK) st = run_enqueue_digitizer(R);
+    for (Req *r : L.finishing)
+        if (r->own && r->piece_status == GPET_OK && run_enqueue_digitizer(*r->own) != GPET_OK) {
+            r->piece_status = GPET_ERR_CUDA;
+            r->piece_error = gpet_last_error();
+        }
+    cudaError_t e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(L.done, R.stream);
+    if (e != cudaSuccess) {
+        // no end marker: wait for the launch here, so that its results are not read early
+        if (L.done) { cudaEventDestroy(L.done); L.done = nullptr; }
+        cudaStreamSynchronize(R.stream);
+        if (st == GPET_OK) st = gpet_cuda_fail(e, "launch end event");
+    }
+    std::lock_guard<std::mutex> lk(S->core->mu);
+    S->stats.launches++;
+    S->stats.max_jobs_per_launch = std::max<uint64_t>(S->stats.max_jobs_per_launch, R.jobs.size());
+    return st;
+}
+
+// Results of a launch whose work (and that of the digitizers behind it) is
+// done.  Requests that met a full buffer go to `rerun`: they run again, whole
+// and with exact sizes, once no launch is on the GPU.
+void finish_launch(gpet_server *S, Launch &L, int close_status, const std::string &close_error,
+                   std::vector<Req *> &rerun, cudaStream_t up) {
+    int st = close_status;
+    std::string err = close_error;
+    if (st == GPET_OK) {
+        st = run_collect(*L.R);
+        if (st != GPET_OK) err = gpet_last_error();
+    }
+    // the results move to memory of their own size, and the launch's buffers
+    // go back at once (results a client keeps then hold only what they are)
+    std::shared_ptr<Run> views = L.R;
+    if (st == GPET_OK && !L.whole.empty()) {
+        int cst = GPET_OK;
+        std::shared_ptr<Run> compact = run_compact(*L.R, up, &cst);
+        if (compact) {
+            charge(S, *compact, compact->arena_bytes);
+            views = compact;
+        }
+    }
+    // only the launch's own singles buffer was too small: pieces (which write
+    // to their requests' buffers) are complete
+    const RunHeader &H = L.R->h_hdr;
+    const bool shared_only = st == GPET_ERR_OVERFLOW && H.n_ovf <= L.R->O.ovf_cap && !(H.status & kStatusOverflow);
+    for (auto &w : L.whole) {
+        Req *r = w.first;
+        if (st == GPET_OK) publish(S, r, GPET_OK, "", views, w.second);
+        else if (st == GPET_ERR_OVERFLOW) rerun.push_back(r);
+        else publish(S, r, st, err, nullptr, 0);
+    }
+    if (st != GPET_OK && !shared_only)
+        for (Req *r : L.pieces)
+            if (r->piece_status == GPET_OK) {
+                r->piece_status = st;
+                r->piece_error = err;
+            }
+    for (Req *r : L.finishing) {
+        int s2 = r->piece_status;
+        std::string e2 = r->piece_error;
+        if (s2 == GPET_OK && r->own) {
+            s2 = run_collect(*r->own);
+            if (s2 != GPET_OK) e2 = gpet_last_error();
+        }
+        if (s2 == GPET_OK) {
+            int cst = GPET_OK;
+            std::shared_ptr<Run> own = run_compact(*r->own, up, &cst);
+            if (own) charge(S, *own, own->arena_bytes);
+            else own = r->own;
+            publish(S, r, GPET_OK, "", own, 0);
+        } else if (s2 == GPET_ERR_OVERFLOW) {
+            r->own.reset();
+            rerun.push_back(r);
+        } else {
+            publish(S, r, s2, e2, nullptr, 0);
+        }
+    }
+    views.reset();
+    L.R.reset();  // views of the launch itself (no compact copy) keep its memory; the pipeline does not
+}
+
+void pipeline_main(gpet_server *S) {
+    cudaSetDevice(S->device);
+    Pipe P;
+    cudaStreamCreateWithFlags(&P.gpu, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&P.up, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&P.fb, cudaStreamNonBlocking);
+    if (cudaMallocHost(&P.stage, P.stage_bytes) != cudaSuccess) P.stage = nullptr;
+    if (cudaMallocHost(&P.zeros, P.zeros_bytes) != cudaSuccess) P.zeros = nullptr;
+    if (P.zeros) std::memset(P.zeros, 0, P.zeros_bytes);
+    Core &C = *S->core;
+    std::unique_ptr<Launch> open;
+    std::deque<std::pair<std::unique_ptr<Launch>, std::pair<int, std::string>>> inflight;
+    // histories published to the open launch and not yet claimed by its kernel
+    const uint64_t backlog_target = 4 * S->piece;
+    std::vector<Req *> rerun;
     for (;;) {
-        std::vector<Req *> batch;
-        size_t taken = 0;
-        uint64_t max_span = 0;
+        // 1. launches whose work is done, in order
+        while (!inflight.empty() && cudaEventQuery(inflight.front().first->done) != cudaErrorNotReady) {
+            cudaGetLastError();
+            finish_launch(S, *inflight.front().first, inflight.front().second.first, inflight.front().second.second,
+                          rerun, P.up);
+            inflight.pop_front();
+        }
+        // requests that met a full buffer run again alone, with exact sizes, on
+        // an idle GPU (a live launch would hold every SM while they wait)
+        if (!rerun.empty()) {
+            if (open) {
+                const int st = close_launch(S, *open);
+                std::string err = st == GPET_OK ? std::string() : std::string(gpet_last_error());
+                inflight.emplace_back(std::move(open), std::make_pair(st, std::move(err)));
+                open.reset();
+            }
+            if (inflight.empty()) {
+                for (Req *r : rerun) {
+                    std::shared_ptr<Run> R;
+                    const int s2 = run_whole(S, P, r, R);
+                    publish(S, r, s2, s2 == GPET_OK ? "" : std::string(gpet_last_error()), R, 0);
+                }
+                rerun.clear();
+            } else {
+                std::unique_lock<std::mutex> lk(C.mu);
+                C.cv.wait_for(lk, std::chrono::microseconds(100));
+            }
+            continue;
+        }
+        std::vector<Req *> work;
         {
             std::unique_lock<std::mutex> lk(C.mu);
-            for (;;) {
-                if (S->stop && S->queue.empty()) break;
-                // first come, first served: take from the front while the budget allows
-                while (!S->queue.empty() && (int)batch.size() < S->max_jobs) {
-                    Req *r = S->queue.front();
-                    if (C.in_use + r->est > C.budget && !(batch.empty() && C.in_use == 0)) break;
-                    // the time stamps of every job must fit beside the job bits of the sort key
-                    const uint64_t span = std::max(max_span, r->span_ps);
-                    if (!batch.empty() &&
-                        span > sort_time_limit(sort_job_shift((int)batch.size() + 1)) - 0xFFFFFFFFull)
-                        break;
-                    max_span = span;
-                    S->queue.pop_front();
-                    C.in_use += r->est;
-                    taken += r->est;
-                    batch.push_back(r);
-                }
-                C.peak = std::max(C.peak, C.in_use);
-                if (!batch.empty()) break;
+            if (S->stop && S->queue.empty() && !open && inflight.empty()) break;
+            if (S->queue.empty() && !open && inflight.empty()) {
                 C.cv.wait(lk);
+                continue;
             }
-            if (batch.empty()) break;  // stopping and drained
+            work.assign(S->queue.begin(), S->queue.end());
+            S->queue.clear();
         }
-        // one batched launch over the admitted requests
-        std::vector<gpet_scanner *> scs;
-        std::vector<gpet_source> srcs;
-        std::vector<gpet_digitizer> dgs;
-        std::vector<uint64_t> ns, seeds;
-        for (Req *r : batch) {
-            scs.push_back(r->sc);
-            srcs.push_back(r->src);
-            dgs.push_back(r->dg);
-            ns.push_back(r->n);
-            seeds.push_back(r->seed);
+        // 2. one pass over the queue: whole requests, and one piece of each split one
+        bool pieces_ok = true;
+        if (open && std::any_of(work.begin(), work.end(), [](Req *r) { return r->split; })) {
+            uint64_t taken = 0;
+            if (run_live_taken(*open->R, &taken) == GPET_OK)
+                pieces_ok = (open->R->live_tail - std::min(taken, open->R->live_tail)) * open->R->chunk_size <
+                            backlog_target;
         }
-        auto R = std::make_shared<Run>();
-        gpet_options o = S->opt;
-        o.stream = stream;
-        int st = gpet_batch_build_run(*R, (int32_t)batch.size(), scs.data(), srcs.data(), dgs.data(), ns.data(),
-                                      seeds.data(), &o);
-        if (st == GPET_OK) st = run_with_retry(*R);
-        const std::string err = st == GPET_OK ? std::string() : std::string(gpet_last_error());
-        const auto t_done = Clock::now();
+        std::vector<Req *> keep;
+        for (Req *r : work) {
+            if (!P.stage || !P.zeros) {
+                std::lock_guard<std::mutex> lk(C.mu);
+                r->piece_status = GPET_ERR_OOM;
+                r->piece_error = "pinned host staging of the serving loop could not be allocated";
+                r->next_h = r->n;
+            } else if (!(open && open->full)) {
+                admit(S, P, open, r, pieces_ok);
+            }
+            if (r->next_h < r->n) {
+                keep.push_back(r);
+            } else if (r->piece_status != GPET_OK) {
+                // A failed request is answered once every launch holding a
+                // piece of it has finished (kernels may still write its
+                // buffers): with the latest launch, as launches end in order.
+                if (r->split && r->own && open) open->finishing.push_back(r);
+                else if (r->split && r->own && !inflight.empty()) inflight.back().first->finishing.push_back(r);
+                else publish(S, r, r->piece_status, r->piece_error, nullptr, 0);
+            }
+        }
         {
             std::lock_guard<std::mutex> lk(C.mu);
-            C.in_use -= taken;
-            if (st == GPET_OK) {
-                // the run's real arena stays charged until its last result is freed
-                const size_t bytes = R->arena_bytes;
-                C.in_use += bytes;
-                C.peak = std::max(C.peak, C.in_use);
-                std::weak_ptr<Core> wc = S->core;
-                R->on_release = [wc, bytes]() {
-                    if (auto c = wc.lock()) {
-                        std::lock_guard<std::mutex> l2(c->mu);
-                        c->in_use -= bytes;
-                        c->cv.notify_all();
-                    }
-                };
-                S->stats.launches++;
-                S->stats.max_jobs_per_launch = std::max<uint64_t>(S->stats.max_jobs_per_launch, batch.size());
-            }
-            for (size_t j = 0; j < batch.size(); ++j) {
-                Req *r = batch[j];
-                r->status = st;
-                if (st == GPET_OK) {
-                    gpet_result *res = new (std::nothrow) gpet_result();
-                    if (res) {
-                        res->run = R;
-                        res->job = (int)j;
-                        fill_counts(*R, (int)j, r->n, r->sc->n_crystals, &res->counts);
-                        res->counts.latency_ms =
-                            std::chrono::duration<double, std::milli>(t_done - r->t_submit).count();
-                        r->result = res;
-                    } else {
-                        r->status = GPET_ERR_OOM;
-                        r->error = "host allocation of a result failed";
-                    }
-                } else {
-                    r->error = err;
-                }
-                r->done = true;
-                S->stats.completed++;
-                S->stats.pairs_completed += r->n;
-            }
-            C.cv.notify_all();
-            C.done_cv.notify_all();
+            S->queue.insert(S->queue.begin(), keep.begin(), keep.end());  // ahead of later arrivals
         }
-        R.reset();  // views keep the run alive; the worker does not
+        // 3. close the open launch: old enough, full, or out of published work
+        if (open) {
+            bool close = open->full ||
+                         std::chrono::duration<double, std::milli>(Clock::now() - open->t_open).count() >=
+                             S->max_launch_ms;
+            if (!close && keep.empty()) {
+                uint64_t taken = 0;
+                close = run_live_taken(*open->R, &taken) != GPET_OK || taken >= open->R->live_tail;
+            }
+            if (close) {
+                const int st = close_launch(S, *open);
+                std::string err = st == GPET_OK ? std::string() : std::string(gpet_last_error());
+                inflight.emplace_back(std::move(open), std::make_pair(st, std::move(err)));
+                open.reset();
+            }
+        }
+        // 4. a short wait: arrivals wake it; launch progress and ends are polled
+        std::unique_lock<std::mutex> lk(C.mu);
+        C.cv.wait_for(lk, std::chrono::microseconds(100));
     }
-    cudaStreamSynchronize(stream);
-    cudaStreamDestroy(stream);
-    (void)widx;
+    cudaStreamSynchronize(P.gpu);
+    cudaStreamSynchronize(P.fb);
+    cudaStreamDestroy(P.gpu);
+    cudaStreamDestroy(P.up);
+    cudaStreamDestroy(P.fb);
+    if (P.stage) cudaFreeHost(P.stage);
+    if (P.zeros) cudaFreeHost(P.zeros);
 }
+
+}  // namespace
 
 extern "C" int gpet_server_create(const gpet_server_config *cfg, gpet_server **out) {
     if (!cfg || !out) return gpet_fail(GPET_ERR_INVALID_ARG, "NULL argument");
@@ -179,6 +549,8 @@ extern "C" int gpet_server_create(const gpet_server_config *cfg, gpet_server **o
     if (cfg->workers < 0 || cfg->workers > 8) return gpet_fail(GPET_ERR_INVALID_ARG, "workers must be in [0, 8]");
     if (cfg->max_jobs_per_launch < 0 || cfg->max_jobs_per_launch > 4095)
         return gpet_fail(GPET_ERR_INVALID_ARG, "max_jobs_per_launch must be in [0, 4095]");
+    if (!(cfg->max_launch_ms >= 0.0) || !(cfg->max_launch_ms <= 1.0e4))
+        return gpet_fail(GPET_ERR_INVALID_ARG, "max_launch_ms must be in [0, 1e4]");
     gpet_server *S = new (std::nothrow) gpet_server();
     if (!S) return gpet_fail(GPET_ERR_OOM, "host allocation of the server failed");
     S->core = std::make_shared<Core>();
@@ -186,11 +558,23 @@ extern "C" int gpet_server_create(const gpet_server_config *cfg, gpet_server **o
     S->opt = cfg->launch;
     S->opt.stream = nullptr;
     S->opt.keep_hits = 0;
+    S->opt.h_begin = S->opt.h_end = 0;
     S->max_jobs = cfg->max_jobs_per_launch > 0 ? cfg->max_jobs_per_launch : 256;
+    S->max_launch_ms = cfg->max_launch_ms > 0.0 ? cfg->max_launch_ms : 20.0;
+    // One launch's arena takes at most a quarter of the budget (the open launch,
+    // the one finishing and split requests' buffers share it), and at most
+    // 2^26 singles (7.9 GB); a piece's first guess of singles fits half of it.
+    const size_t per_single = sizeof(RawSingle) + 2 * 8 + 2 * 4 + 8 + 8 + 6 * 4 + 1 + 4;
+    S->launch_crystals = (int64_t)std::min<size_t>(1 << 22, std::max<size_t>(1 << 18, cfg->hbm_budget_bytes / 400));
+    const size_t fixed = run_footprint(0, S->launch_crystals, S->max_jobs, 64, false);
+    const size_t quarter = cfg->hbm_budget_bytes / 4;
+    S->launch_singles = std::min<uint64_t>(1ull << 26, quarter > fixed ? (quarter - fixed) / per_single : 0);
+    S->launch_singles = std::max<uint64_t>(S->launch_singles, 65536);
+    const uint64_t piece_cap = std::max<uint64_t>(1024, (uint64_t)(S->launch_singles / kGuessPerDecay / 2));
+    S->piece = std::min<uint64_t>(cfg->piece_decays > 0 ? cfg->piece_decays : 4000000, piece_cap);
     cudaError_t e = cudaGetDevice(&S->device);
     if (e != cudaSuccess) { delete S; return gpet_cuda_fail(e, "cudaGetDevice"); }
-    const int nw = cfg->workers > 0 ? cfg->workers : 2;
-    for (int w = 0; w < nw; ++w) S->workers.emplace_back(worker_main, S, w);
+    S->pipeline = std::thread(pipeline_main, S);
     *out = S;
     return GPET_OK;
 }
@@ -199,17 +583,16 @@ extern "C" int gpet_server_submit(gpet_server *S, gpet_scanner *sc, const gpet_s
                                   uint64_t n_decays, uint64_t seed, int32_t block, uint64_t *req_id) {
     if (!S || !sc || !src || !dg || !req_id) return gpet_fail(GPET_ERR_INVALID_ARG, "NULL argument");
     JobDev J;
-    int st = gpet_make_job(sc, src, dg, n_decays, seed, J);  // validate now, not in the worker
+    int st = gpet_make_job(sc, src, dg, n_decays, seed, J);  // validate now, not in the pipeline
     if (st != GPET_OK) return st;
     Req *r = new (std::nothrow) Req();
     if (!r) return gpet_fail(GPET_ERR_OOM, "host allocation of a request failed");
     r->sc = sc;
-    r->src = *src;
-    r->dg = *dg;
     r->n = n_decays;
-    r->seed = seed;
+    r->J = J;
+    r->window_ps = (uint64_t)std::llround(dg->coinc_window_ns * 1000.0);
+    r->split = n_decays > S->piece;
     r->est = run_footprint(n_decays, sc->n_crystals, 1, 1, false);
-    r->span_ps = J.t_span_ps;
     Core &C = *S->core;
     std::unique_lock<std::mutex> lk(C.mu);
     if (r->est > C.budget) {
@@ -295,7 +678,7 @@ extern "C" void gpet_server_destroy(gpet_server *S) {
         S->stop = true;
         S->core->cv.notify_all();
     }
-    for (auto &t : S->workers) t.join();
+    if (S->pipeline.joinable()) S->pipeline.join();
     for (auto &kv : S->reqs) {
         if (kv.second->result) gpet_result_free(kv.second->result);
         delete kv.second;

@@ -25,52 +25,6 @@ __device__ __forceinline__ void flush_counters(const OutDev &O, const Counters &
     }
 }
 
-// job owning global chunk c (chunk_start is an (n_jobs + 1)-entry prefix sum)
-__device__ __forceinline__ int chunk_job(const WorkDev &W, unsigned long long c) {
-    int lo = 0, hi = W.n_jobs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (W.chunk_start[mid] <= c) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Warp-wide refill: lanes in `need` receive consecutive history ids from the
-// warp's current chunk, fetching new chunks (one atomic each) as needed.
-__device__ __forceinline__ void warp_refill(const WorkDev &W, uint32_t need, uint64_t &pool_next, uint64_t &pool_end,
-                                            int &pool_job, bool &exhausted, bool &got, uint64_t &h, int &job) {
-    const int lane = threadIdx.x & 31;
-    got = false;
-    while (need && !exhausted) {
-        const uint64_t avail = pool_end - pool_next;
-        if (avail == 0) {
-            unsigned long long c = 0;
-            if (lane == 0) c = atomicAdd(W.next_chunk, 1ull);
-            c = __shfl_sync(kFullMask, c, 0);
-            if (c >= W.total_chunks) {
-                exhausted = true;
-                break;
-            }
-            pool_job = chunk_job(W, c);
-            const uint64_t h0 = (uint64_t)(c - W.chunk_start[pool_job]) * W.chunk_size;
-            const uint64_t base = W.jobs[pool_job].h_base;
-            pool_next = base + h0;
-            pool_end = base + min(h0 + (uint64_t)W.chunk_size, W.jobs[pool_job].n_hist);
-            continue;
-        }
-        const uint32_t cnt = (uint32_t)__popc(need);
-        const uint32_t take = avail < cnt ? (uint32_t)avail : cnt;
-        const uint32_t rank = (uint32_t)__popc(need & lanemask_lt());
-        if (((need >> lane) & 1u) && rank < take) {
-            got = true;
-            h = pool_next + rank;
-            job = pool_job;
-        }
-        pool_next += take;
-        need &= ~__ballot_sync(kFullMask, ((need >> lane) & 1u) && rank < take);  // drop the served lanes
-    }
-}
-
 template <int S>
 __global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int ng_smem) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -88,10 +42,10 @@ __global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int
     s.phase = kPhIdle;
     s.job = 0;
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint64_t pool_next = 0, pool_end = 0;
-    int pool_job = 0;
-    bool exhausted = false;
+    Refill rf;
+    refill_init(rf);
     int status = kStatusOk;
+    uint32_t idle_polls = 0;
 
     for (;;) {
         const uint32_t need = __ballot_sync(kFullMask, s.phase == kPhIdle);
@@ -99,14 +53,19 @@ __global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int
             bool got;
             uint64_t h = 0;
             int job = 0;
-            warp_refill(W, need, pool_next, pool_end, pool_job, exhausted, got, h, job);
+            warp_refill(W, need, rf, got, h, job);
             if (got) {
                 s.h = h;
                 s.job = job;
                 s.phase = kPhSource;
             }
         }
-        if (__all_sync(kFullMask, s.phase == kPhIdle)) break;  // only when the queue is exhausted
+        if (__all_sync(kFullMask, s.phase == kPhIdle)) {
+            // the queue is exhausted, or a live launch has nothing published yet
+            if (!rf.waiting || live_idle_wait(idle_polls, status)) break;
+            continue;
+        }
+        idle_polls = 0;
 
         const JobDev &J = W.jobs[s.job];
         const GeomDev &g = J.geom < ng_smem ? sgeom[J.geom] : W.geoms[J.geom];

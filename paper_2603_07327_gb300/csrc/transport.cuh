@@ -64,12 +64,130 @@ struct WorkDev {
     unsigned int chunk_size;
     const float *gtab;                      // Compton ratio table, kXsIntervals + 1 nodes
     float ln_emin, inv_h;
+    // A live launch (the serving loop's) takes jobs that the host appends while
+    // the kernel runs.  The host writes, with the copy engine and in this order,
+    // the new jobs, their geometry and chunk_start entries, then *live_tail
+    // (chunks published so far); *live_closed = 1 once it appends no more, after
+    // the last tail.  chunk_start then spans n_jobs = the table's capacity, its
+    // unpublished entries ~0.  NULL live_tail: a fixed launch of total_chunks.
+    const unsigned long long *live_tail;
+    const int *live_closed;
+    unsigned long long *live_taken;         // chunks claimed so far (a progress hint for the host)
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+constexpr unsigned long long kNoChunk = ~0ull;
+// idle waits of a live launch: a sleep that doubles up to 16 us, at most this
+// many in a row (about 4 s) before the kernel gives up with kStatusLiveStall
+constexpr uint32_t kLiveIdlePolls = 1u << 18;
+
+// Where a warp takes its next histories from: the current chunk [next, end) of
+// job `job`, a chunk index claimed but not yet published (pend), and whether
+// the queue is exhausted.
+struct Refill {
+    uint64_t next, end;
+    unsigned long long pend;
+    int job;
+    bool exhausted, waiting;
+};
+
+__device__ __forceinline__ void refill_init(Refill &r) {
+    r.next = r.end = 0;
+    r.pend = kNoChunk;
+    r.job = 0;
+    r.exhausted = r.waiting = false;
+}
+
+// Claim of the next chunk by a warp (lanes converged).  Lane 0 takes the next
+// index of the work counter, or re-checks the one it took before while that
+// chunk was not yet published.  Returns 1 (chunk c ready), 0 (a live launch
+// has not published it yet) or -1 (no more work).
+__device__ __forceinline__ int claim_chunk(const WorkDev &W, unsigned long long &pend, unsigned long long &c) {
+    int r = 0;
+    unsigned long long cc = 0;
+    if ((threadIdx.x & 31) == 0) {
+        if (pend == kNoChunk) pend = atomicAdd(W.next_chunk, 1ull);
+        cc = pend;
+        if (!W.live_tail) {
+            r = cc < W.total_chunks ? 1 : -1;
+        } else {
+            // closed first: once it reads 1, the tail read after it is final
+            const int closed = *reinterpret_cast<const volatile int *>(W.live_closed);
+            __threadfence();
+            const unsigned long long tail = *reinterpret_cast<const volatile unsigned long long *>(W.live_tail);
+            r = cc < tail ? 1 : (closed ? -1 : 0);
+            if (r == 1) atomicMax(W.live_taken, cc + 1);
+        }
+        if (r != 0) pend = kNoChunk;
+    }
+    r = __shfl_sync(kFullMask, r, 0);
+    c = __shfl_sync(kFullMask, cc, 0);
+    if (r == 1 && W.live_tail) __threadfence();  // the chunk's table entries were written before its tail
+    return r;
+}
+
+// Warp-wide refill: lanes in `need` receive consecutive history ids from the
+// warp's current chunk, fetching new chunks (one atomic each) as needed.
+// Table reads go to L2 (ld.cg): a live launch appends to these tables.
+__device__ __forceinline__ void warp_refill(const WorkDev &W, uint32_t need, Refill &R, bool &got, uint64_t &h,
+                                            int &job) {
+    const int lane = threadIdx.x & 31;
+    got = false;
+    R.waiting = false;
+    while (need && !R.exhausted) {
+        const uint64_t avail = R.end - R.next;
+        if (avail == 0) {
+            unsigned long long c = 0;
+            const int cl = claim_chunk(W, R.pend, c);
+            if (cl < 0) {
+                R.exhausted = true;
+                break;
+            }
+            if (cl == 0) {
+                R.waiting = true;  // try again at the next refill
+                break;
+            }
+            int lo = 0, hi = W.n_jobs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldcg(W.chunk_start + mid) <= c) lo = mid; else hi = mid - 1;
+            }
+            R.job = lo;
+            const uint64_t h0 = (uint64_t)(c - __ldcg(W.chunk_start + lo)) * W.chunk_size;
+            const uint64_t base = __ldcg(reinterpret_cast<const unsigned long long *>(&W.jobs[lo].h_base));
+            R.next = base + h0;
+            R.end = base + min(h0 + (uint64_t)W.chunk_size,
+                               (uint64_t)__ldcg(reinterpret_cast<const unsigned long long *>(&W.jobs[lo].n_hist)));
+            continue;
+        }
+        const uint32_t cnt = (uint32_t)__popc(need);
+        const uint32_t take = avail < cnt ? (uint32_t)avail : cnt;
+        const uint32_t rank = (uint32_t)__popc(need & lanemask_lt());
+        if (((need >> lane) & 1u) && rank < take) {
+            got = true;
+            h = R.next + rank;
+            job = R.job;
+        }
+        R.next += take;
+        need &= ~__ballot_sync(kFullMask, ((need >> lane) & 1u) && rank < take);  // drop the served lanes
+    }
+}
+
+// One idle wait of a live launch whose slots are all idle while work may still
+// be published: sleeps (doubling up to 16 us) and returns false, or returns
+// true with kStatusLiveStall once kLiveIdlePolls waits ran in a row.
+__device__ __forceinline__ bool live_idle_wait(uint32_t &polls, int &status) {
+    if (++polls > kLiveIdlePolls) {
+        status |= kStatusLiveStall;
+        return true;
+    }
+    __nanosleep(polls < 14u ? (1u << polls) : 16384u);
+    return false;
 }
 
 // copy the first ng geometry descriptors into shared memory
@@ -462,20 +580,40 @@ __device__ __forceinline__ void ev_finish(const JobDev *__restrict__ jobs, const
         }
         const uint32_t b = __ballot_sync(mask, keep);
         if (!b) continue;
-        unsigned long long base = 0;
-        const int leader = __ffs(b) - 1;
-        if (lane == leader) base = atomicAdd(O.n_singles, (unsigned long long)__popc(b));
-        base = __shfl_sync(mask, base, leader);
+        // destination: the launch's singles buffer, or the job's own
+        RawSingle *dst = O.s_raw;
+        unsigned long long *dst_n = O.n_singles, dst_cap = O.s_cap;
+        if (keep && J->s_raw) {
+            dst = J->s_raw;
+            dst_n = J->n_singles;
+            dst_cap = J->s_cap;
+        }
+        unsigned long long slot = 0;
+        if (__all_sync(mask, dst_n == O.n_singles)) {
+            // one counter for the warp (every fixed launch)
+            unsigned long long base = 0;
+            const int leader = __ffs(b) - 1;
+            if (lane == leader) base = atomicAdd(O.n_singles, (unsigned long long)__popc(b));
+            base = __shfl_sync(mask, base, leader);
+            slot = base + __popc(b & lanemask_lt());
+        } else if (keep) {
+            // lanes grouped by destination, one atomic per group
+            const uint32_t grp = __match_any_sync(b, reinterpret_cast<unsigned long long>(dst_n));
+            const int leader = __ffs(grp) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(dst_n, (unsigned long long)__popc(grp));
+            base = __shfl_sync(grp, base, leader);
+            slot = base + __popc(grp & lanemask_lt());
+        }
         if (keep) {
-            const unsigned long long slot = base + __popc(b & lanemask_lt());
-            if (slot < O.s_cap) {
+            if (slot < dst_cap) {
                 const GeomDev &g = geoms[J->geom];
                 int panel;
                 if (g.readout_level == 0) panel = (int)unit;
                 else if (g.readout_level == 1) panel = (int)(unit / (uint32_t)(g.modules_u * g.modules_v));
                 else panel = (int)(unit / (uint32_t)(g.crystals_per_module * g.modules_u * g.modules_v));
                 const uint64_t t = s.t0 + dt;
-                uint4 *r = reinterpret_cast<uint4 *>(O.s_raw + slot);
+                uint4 *r = reinterpret_cast<uint4 *>(dst + slot);
                 r[0] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)s.h, (uint32_t)(s.h >> 32));
                 r[1] = make_uint4(unit, (uint32_t)panel, (uint32_t)s.job, __float_as_uint(eb));
                 r[2] = make_uint4(__float_as_uint(e), __float_as_uint(db), 0u, 0u);

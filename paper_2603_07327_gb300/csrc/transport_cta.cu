@@ -99,51 +99,12 @@ __device__ __forceinline__ void cstore(Pool &P, int q, const PState &s, bool all
     P.st[kCsteps][q] = (s.sph & 0xFFFFu) | (s.sdet << 16);
 }
 
-// warp-wide refill of the idle slots of one group of 32 (see transport.cu)
-__device__ void cta_refill(const WorkDev &W, uint32_t need, uint64_t &pool_next, uint64_t &pool_end, int &pool_job,
-                           bool &exhausted, bool &got, uint64_t &h, int &job) {
-    const int lane = threadIdx.x & 31;
-    got = false;
-    while (need && !exhausted) {
-        const uint64_t avail = pool_end - pool_next;
-        if (avail == 0) {
-            unsigned long long c = 0;
-            if (lane == 0) c = atomicAdd(W.next_chunk, 1ull);
-            c = __shfl_sync(kFullMask, c, 0);
-            if (c >= W.total_chunks) {
-                exhausted = true;
-                break;
-            }
-            int lo = 0, hi = W.n_jobs - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (W.chunk_start[mid] <= c) lo = mid; else hi = mid - 1;
-            }
-            pool_job = lo;
-            const uint64_t h0 = (uint64_t)(c - W.chunk_start[lo]) * W.chunk_size;
-            const uint64_t base = W.jobs[lo].h_base;
-            pool_next = base + h0;
-            pool_end = base + min(h0 + (uint64_t)W.chunk_size, W.jobs[lo].n_hist);
-            continue;
-        }
-        const uint32_t cnt = (uint32_t)__popc(need);
-        const uint32_t take = avail < cnt ? (uint32_t)avail : cnt;
-        const uint32_t rank = (uint32_t)__popc(need & lanemask_lt());
-        if (((need >> lane) & 1u) && rank < take) {
-            got = true;
-            h = pool_next + rank;
-            job = pool_job;
-        }
-        pool_next += take;
-        need &= ~__ballot_sync(kFullMask, ((need >> lane) & 1u) && rank < take);  // drop the served lanes
-    }
-}
-
 }  // namespace
 
 // at most 128 registers a thread: 16 warps of the kernel stay resident per SM
 template <int SPL, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1)) k_transport_cta(WorkDev W, OutDev O, int ng_smem) {
+__global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1)) k_transport_cta(WorkDev W, OutDev O, int ng_smem,
+                                                                                                 int repeat) {
     using Pool = CtaPool<SPL>;
     constexpr int kPool = Pool::kPool;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -154,6 +115,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
     // i - 1 is cleared after the barrier of iteration i, which every read of
     // it precedes and every add of iteration i + 2 follows.
     __shared__ int census[3][8];
+    __shared__ unsigned long long phase_events[kNumPh];  // lanes that ran an event, per phase
     __shared__ uint8_t assign[WARPS][32];  // slot of each lane in the chosen phase
     stage_geometry(W, sgeom, ng_smem);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -161,38 +123,42 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
 #pragma unroll
     for (int g = 0; g < SPL; ++g) P.st[kCpack][g * 32 + lane] = 0;
     if (threadIdx.x < 24) (&census[0][0])[threadIdx.x] = 0;
+    if (threadIdx.x < kNumPh) phase_events[threadIdx.x] = 0;
     __syncthreads();
 
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint64_t pool_next = 0, pool_end = 0;
-    int pool_job = 0;
-    bool exhausted = false;
+    Refill rf;
+    refill_init(rf);
     int status = kStatusOk;
+    uint32_t idle_polls = 0;
     unsigned long long iters = 0, lanes_used = 0;
     int buf = 0;
-    bool may_idle = true;  // slots turn idle only in the finish event (or on an error)
+    // slots turn idle only in the finish event (or on an error); a warp whose
+    // next chunk a live launch has not published yet retries every iteration
+    bool may_idle = true;
 
     for (;;) {
         // 1. refill the warp's idle slots
 #pragma unroll
         for (int g = 0; g < SPL; ++g) {
-            if (!may_idle || exhausted) break;
+            if (!may_idle || rf.exhausted) break;
             const int q = g * 32 + lane;
             const uint32_t need = __ballot_sync(kFullMask, cphase(P, q) == kPhIdle);
             if (need) {
                 bool got;
                 uint64_t h = 0;
                 int job = 0;
-                cta_refill(W, need, pool_next, pool_end, pool_job, exhausted, got, h, job);
+                warp_refill(W, need, rf, got, h, job);
                 if (got) {
                     P.st[kCh0][q] = (uint32_t)h;
                     P.st[kCh1][q] = (uint32_t)(h >> 32);
                     P.st[kCjob][q] = (uint32_t)job;
                     P.st[kCpack][q] = (uint32_t)kPhSource << 16;
                 }
+                if (rf.waiting) break;
             }
         }
-        may_idle = false;
+        may_idle = rf.waiting && !rf.exhausted;
         __syncwarp();
         // 2. the warp's census: lane p adds the warp's count of phase p
         uint32_t ph[SPL];
@@ -211,7 +177,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
             if (lane == p) my_n = n;
         }
         if (my_n) atomicAdd(&census[buf][lane], my_n);
-        __syncthreads();
+        const int any_waiting = __syncthreads_or(rf.waiting && !rf.exhausted);
         // 3. every warp reads the same totals: the most populated phase wins
         //    (ties to the later phase, which finishes histories sooner)
         const uint32_t key = (lane >= 1 && lane < kNumPh) ? ((uint32_t)census[buf][lane] << 3) | (uint32_t)lane : 0u;
@@ -219,7 +185,13 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
         if (threadIdx.x < 8) census[buf == 0 ? 2 : buf - 1][threadIdx.x] = 0;
         buf = buf == 2 ? 0 : buf + 1;
         const int best_p = (int)(best & 7u);
-        if ((best >> 3) == 0) break;  // every slot of every warp idle after refills: done
+        if ((best >> 3) == 0) {
+            // every slot of every warp idle after refills: done, unless a warp
+            // of a live launch waits for a chunk the host has not published yet
+            if (!any_waiting || live_idle_wait(idle_polls, status)) break;
+            continue;
+        }
+        idle_polls = 0;
         // 4. lanes onto this warp's slots of the chosen phase: the slot of
         //    rank r (in slot order) goes to lane r
         int mine = 0;
@@ -238,6 +210,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
         if (mine == 0) continue;  // nothing of this phase here: wait for the next choice
         ++iters;
         lanes_used += (unsigned long long)min(mine, 32);
+        if (lane == 0) atomicAdd(&phase_events[best_p], (unsigned long long)min(mine, 32));
         PState s;
         s.phase = kPhIdle;
         s.job = 0;
@@ -251,23 +224,34 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
             __syncwarp();
             continue;
         }
+        int n_ev = 0;
         if (active) {
             cload(P, q, s);
             const JobDev &J = W.jobs[s.job];
             const GeomDev &g = J.geom < ng_smem ? sgeom[J.geom] : W.geoms[J.geom];
             int st = kStatusOk;
-            switch (best_p) {
-                case kPhSource: ev_source(J, g, s, cnt); break;
-                case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
-                case kPhFlight: case kPhFlightOut: ev_flight(J, g, s, cnt); break;
-                case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, kCtaS, cnt); break;
-                default: st = kStatusBadPhase; break;
-            }
+            // the chosen event, then again while the slot stays in its phase, up
+            // to `repeat` events in all: the compaction interval (events between
+            // regroupings; only steps of the phantom and of the detector repeat)
+            do {
+                ++n_ev;
+                switch (best_p) {
+                    case kPhSource: ev_source(J, g, s, cnt); break;
+                    case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
+                    case kPhFlight: case kPhFlightOut: ev_flight(J, g, s, cnt); break;
+                    case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, kCtaS, cnt); break;
+                    default: st = kStatusBadPhase; break;
+                }
+            } while (st == kStatusOk && n_ev < repeat && s.phase == (uint32_t)best_p);
             if (st != kStatusOk) {
                 status |= st;
                 s.phase = kPhIdle;
             }
             cstore(P, q, s, best_p == kPhSource);
+        }
+        if (repeat > 1) {  // the repeated events, beyond the one per lane counted above
+            const int extra = __reduce_add_sync(kFullMask, n_ev > 1 ? n_ev - 1 : 0);
+            if (lane == 0 && extra) atomicAdd(&phase_events[best_p], (unsigned long long)extra);
         }
         may_idle = may_idle || __any_sync(kFullMask, active && s.phase == kPhIdle);
         __syncwarp();
@@ -285,6 +269,9 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
         atomicAdd(O.counters + 7, lanes_used);
     }
     if (status) atomicOr(O.status, status);
+    __syncthreads();  // every warp's event counts are in
+    if (threadIdx.x >= 1 && threadIdx.x < kNumPh && phase_events[threadIdx.x])
+        atomicAdd(O.counters + 10 + threadIdx.x, phase_events[threadIdx.x]);
 }
 
 // dynamic shared memory and resident CTAs of one instantiation
@@ -305,7 +292,7 @@ static cudaError_t launch_cta(const WorkDev &W, const OutDev &O, const LaunchCfg
     int ctas = 0, ng = 0;
     cudaError_t e = cta_shape<SPL, WARPS>(W.n_geoms, cfg, &smem, &ctas, &ng);
     if (e != cudaSuccess) return e;
-    k_transport_cta<SPL, WARPS><<<ctas, WARPS * 32, smem, st>>>(W, O, ng);
+    k_transport_cta<SPL, WARPS><<<ctas, WARPS * 32, smem, st>>>(W, O, ng, max(1, cfg.compact_every));
     return cudaGetLastError();
 }
 

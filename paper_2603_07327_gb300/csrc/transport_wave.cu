@@ -104,46 +104,6 @@ __device__ __forceinline__ void pool_store(Pool &P, int q, const PState &s, bool
     P.st[kWsteps][q] = (s.sph & 0xFFFFu) | (s.sdet << 16);
 }
 
-// warp-wide refill of the idle slots of one half of the pool (see transport.cu)
-__device__ void warp_refill_wave(const WorkDev &W, uint32_t need, uint64_t &pool_next, uint64_t &pool_end,
-                                 int &pool_job, bool &exhausted, bool &got, uint64_t &h, int &job) {
-    const int lane = threadIdx.x & 31;
-    got = false;
-    while (need && !exhausted) {
-        const uint64_t avail = pool_end - pool_next;
-        if (avail == 0) {
-            unsigned long long c = 0;
-            if (lane == 0) c = atomicAdd(W.next_chunk, 1ull);
-            c = __shfl_sync(kFullMask, c, 0);
-            if (c >= W.total_chunks) {
-                exhausted = true;
-                break;
-            }
-            int lo = 0, hi = W.n_jobs - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (W.chunk_start[mid] <= c) lo = mid; else hi = mid - 1;
-            }
-            pool_job = lo;
-            const uint64_t h0 = (uint64_t)(c - W.chunk_start[lo]) * W.chunk_size;
-            const uint64_t base = W.jobs[lo].h_base;
-            pool_next = base + h0;
-            pool_end = base + min(h0 + (uint64_t)W.chunk_size, W.jobs[lo].n_hist);
-            continue;
-        }
-        const uint32_t cnt = (uint32_t)__popc(need);
-        const uint32_t take = avail < cnt ? (uint32_t)avail : cnt;
-        const uint32_t rank = (uint32_t)__popc(need & lanemask_lt());
-        if (((need >> lane) & 1u) && rank < take) {
-            got = true;
-            h = pool_next + rank;
-            job = pool_job;
-        }
-        pool_next += take;
-        need &= ~__ballot_sync(kFullMask, ((need >> lane) & 1u) && rank < take);  // drop the served lanes
-    }
-}
-
 template <int SPL>
 __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, OutDev O, int ng_smem, int repeat) {
     using Pool = WarpPool<SPL>;
@@ -159,10 +119,10 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
     __syncthreads();
 
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint64_t pool_next = 0, pool_end = 0;
-    int pool_job = 0;
-    bool exhausted = false;
+    Refill rf;
+    refill_init(rf);
     int status = kStatusOk;
+    uint32_t idle_polls = 0;
     unsigned long long iters = 0, lanes_used = 0;   // wavefront fill diagnostics
 
     for (;;) {
@@ -171,11 +131,11 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
         for (int g = 0; g < SPL; ++g) {
             const int q = g * 32 + lane;
             const uint32_t need = __ballot_sync(kFullMask, pool_phase(P, q) == kPhIdle);
-            if (need && !exhausted) {
+            if (need && !rf.exhausted) {
                 bool got;
                 uint64_t h = 0;
                 int job = 0;
-                warp_refill_wave(W, need, pool_next, pool_end, pool_job, exhausted, got, h, job);
+                warp_refill(W, need, rf, got, h, job);
                 if (got) {
                     P.st[kWh0][q] = (uint32_t)h;
                     P.st[kWh1][q] = (uint32_t)(h >> 32);
@@ -207,7 +167,13 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
                 for (int g = 0; g < SPL; ++g) best_b[g] = b[g];
             }
         }
-        if (best_n == 0) break;  // every slot idle after a refill: the queue is exhausted
+        if (best_n == 0) {
+            // every slot idle after a refill: the queue is exhausted, or a live
+            // launch has nothing published yet
+            if (!rf.waiting || live_idle_wait(idle_polls, status)) break;
+            continue;
+        }
+        idle_polls = 0;
         // 3. lane i takes the i-th slot of that phase
         const bool active = lane < best_n;
         int q = 0;

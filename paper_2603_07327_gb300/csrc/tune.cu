@@ -2,7 +2,8 @@
 // launch forms on a pilot run of the caller's own workload (same scanner,
 // source and digitizer): the per-lane event loop at 2 CTAs per SM, the per-warp
 // wavefront, and the CTA-synchronous wavefront at 128, 256 and 512 threads
-// (slot pool depth 2) and at 256 threads with depth 3.  The fastest form is
+// (slot pool depth 2), at 256 threads with depth 3, and at 256 threads with a
+// compaction interval of 2 and 4 events.  The fastest form is
 // returned and remembered per design class (panels, layers, phantom) and SM
 // count; launches that leave gpet_options.kernel at 0 use it.
 #include <algorithm>
@@ -44,8 +45,11 @@ extern "C" int gpet_autotune(gpet_scanner *sc, const gpet_source *src, const gpe
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "device query");
     struct Cand { int kernel, bps, compact, depth, block; };
-    const Cand cands[] = {{kKernelLoop, 2, 1, 0, 0}, {kKernelWave, 0, 1, 2, 0}, {kKernelCta, 0, 1, 2, 128},
-                          {kKernelCta, 0, 1, 2, 256}, {kKernelCta, 0, 1, 2, 512}, {kKernelCta, 0, 1, 3, 256}};
+    // the CTA-synchronous kernel also at compaction intervals of 2 and 4 events
+    // (a detector or phantom step repeated on its lane before the next regrouping)
+    const Cand cands[] = {{kKernelLoop, 2, 1, 0, 0},   {kKernelWave, 0, 1, 2, 0},   {kKernelCta, 0, 1, 2, 128},
+                          {kKernelCta, 0, 1, 2, 256},  {kKernelCta, 0, 1, 2, 512},  {kKernelCta, 0, 1, 3, 256},
+                          {kKernelCta, 0, 2, 2, 256},  {kKernelCta, 0, 4, 2, 256}};
     float best_t = 1e30f;
     gpet_options bo;
     std::memset(&bo, 0, sizeof(bo));

@@ -66,11 +66,11 @@ def test_captures_are_keyed_to_the_captured_sources(bench, tmp_path, monkeypatch
         with open(os.path.join(csrc, name)) as f:
             (fake / name).write_text(f.read())
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "TRANSPORT_TRAFFIC", dict(bench.TRANSPORT_TRAFFIC,
+    monkeypatch.setattr(bench, "TRANSPORT_CAPTURE", dict(bench.TRANSPORT_CAPTURE, dram_bytes_per_pair=8.4,
                                                          sha1=bench._sources_sha1(bench.TRANSPORT_SOURCES)))
     monkeypatch.setattr(bench, "DIGITIZER_TRAFFIC", dict(bench.DIGITIZER_TRAFFIC,
                                                          sha1=bench._sources_sha1(bench.DIGITIZER_SOURCES)))
-    assert bench._transport_traffic(1.22e9) == pytest.approx(bench.TRANSPORT_TRAFFIC["bytes_per_pair"] * 1.22e9)
+    assert bench._transport_traffic(1.22e9) == pytest.approx(8.4 * 1.22e9)
     assert bench._digitizer_traffic(1000) == pytest.approx(bench.DIGITIZER_TRAFFIC["bytes_per_single"] * 1000)
     sort_cu = fake / "sort.cu"
     sort_cu.write_text(sort_cu.read_text() + "\n// a comment\n\n/* another */\n")

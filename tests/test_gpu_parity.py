@@ -112,7 +112,7 @@ def test_parity_small(G, oracle, name, kernel):
     check_parity(G, oracle, res, orc, n, dg)
 
 
-@pytest.mark.parametrize("compact_every", [1, 4])
+@pytest.mark.parametrize("compact_every", [1, 2, 4])
 def test_kernels_agree_bit_for_bit(G, compact_every):
     """The per-lane loop and the regrouping wavefront run the same events, so
     hits, singles, coincidences and tallies are identical (as sets)."""

@@ -78,6 +78,60 @@ def test_served_results_equal_alone(G, oracle):
         res.free()
 
 
+@pytest.mark.parametrize("kernel", [3, 1, 2])
+def test_split_requests_equal_alone(G, oracle, kernel):
+    """Requests above the piece size run as history ranges in successive live
+    launches, their singles and tallies gathered in their own device buffers
+    and sorted once at the end; each equals its plain run bit for bit, mixed
+    with whole requests that arrive meanwhile, on every transport kernel."""
+    reqs = W.config5(n_requests=10, pairs_lo=2e4, pairs_hi=3e5, seed=55)
+    base = W.hot_rod_phantom()
+    made = [_request_scanner(G, r, base) for r in reqs]
+    srv = G.Server(hbm_budget_bytes=8 * 10**9, piece_decays=40_000, kernel=kernel)
+    ids = [srv.submit(made[i][0], r["source"], r["digitizer"], r["n_decays"], r["seed"]) for i, r in enumerate(reqs)]
+    served = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    n_split = sum(r["n_decays"] > 40_000 for r in reqs)
+    assert n_split >= 4 and st["pieces"] > n_split and st["completed"] == len(reqs)
+    for i, r in enumerate(reqs):
+        alone = made[i][0].simulate(r["source"], r["digitizer"], r["n_decays"], r["seed"], kernel=kernel)
+        assert_same(canon(alone), canon(served[i]))
+        alone.free()
+    srv.close()
+    # one split phantom request against the oracle as well
+    i = next(k for k, r in enumerate(reqs) if r["n_decays"] > 40_000 and r["phantom"] is not None)
+    r = reqs[i]
+    res = made[i][0].simulate(r["source"], r["digitizer"], r["n_decays"], r["seed"], keep_hits=True)
+    assert_same(canon(res), canon(served[i]))
+    orc = oracle.simulate(r["scanner"], r["source"], r["digitizer"], r["n_decays"], r["seed"],
+                          phantom=made[i][1], threads=8)
+    check_parity(G, oracle, res, orc, r["n_decays"], r["digitizer"])
+
+
+def test_requests_join_a_running_launch(G):
+    """A launch stays open while requests keep arriving (max_launch_ms), and
+    its kernel takes the appended jobs as they come: requests submitted while
+    a large one runs are appended to its launch, and every result equals its
+    plain run."""
+    sc = G.Scanner(W.config2_scanner("B"))
+    dg = W.digitizer()
+    srv = G.Server(hbm_budget_bytes=16 * 10**9, max_launch_ms=500.0, piece_decays=30_000_000)
+    jobs = [((0.0, 0.0, -3.0), 20_000_000, 71)] + [((0.0, 0.0, 1.0 * k), 200_000, 80 + k) for k in range(12)]
+    ids = []
+    for pos, n, seed in jobs:
+        ids.append(srv.submit(sc, W.point_source(pos), dg, n, seed))
+        time.sleep(0.0005)
+    served = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    assert st["live_appends"] >= 1 and st["max_jobs_per_launch"] >= 2, st
+    for (pos, n, seed), s in zip(jobs, served):
+        alone = sc.simulate(W.point_source(pos), dg, n, seed)
+        assert_same(canon(alone), canon(s))
+        alone.free()
+    srv.close()
+    sc.close()
+
+
 def test_admission_by_footprint(G):
     sc = G.Scanner(W.config2_scanner("A"))
     srv = G.Server(hbm_budget_bytes=200 * 10**6, workers=1)
