@@ -488,6 +488,8 @@ void pipeline_main(gpet_server *S) {
                             backlog_target;
         }
         std::vector<Req *> keep;
+        const Launch *opened_before = open.get();
+        const size_t jobs_before = open ? open->R->jobs.size() : 0;
         for (Req *r : work) {
             if (!P.stage || !P.zeros) {
                 std::lock_guard<std::mutex> lk(C.mu);
@@ -513,11 +515,14 @@ void pipeline_main(gpet_server *S) {
             S->queue.insert(S->queue.begin(), keep.begin(), keep.end());  // ahead of later arrivals
         }
         // 3. close the open launch: old enough, full, or out of published work
+        //    with nothing more to take now (an empty queue, or requests that
+        //    wait for memory)
+        const bool appended = open && (open.get() != opened_before || open->R->jobs.size() > jobs_before);
         if (open) {
             bool close = open->full ||
                          std::chrono::duration<double, std::milli>(Clock::now() - open->t_open).count() >=
                              S->max_launch_ms;
-            if (!close && keep.empty()) {
+            if (!close && (keep.empty() || !appended)) {
                 uint64_t taken = 0;
                 close = run_live_taken(*open->R, &taken) != GPET_OK || taken >= open->R->live_tail;
             }

@@ -12,7 +12,8 @@ import workloads as W
 from tests.test_gpu_batch import assert_same, canon
 from tests.test_gpu_parity import check_parity
 
-pytestmark = pytest.mark.gpu
+# a serving-loop test that waits on a request which never completes ends here
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(240)]
 
 
 @pytest.fixture(scope="module")
