@@ -429,7 +429,11 @@ int run_collect(Run &R) {
     if (H.status & kStatusBadPhase)
         return gpet_fail(GPET_ERR_CUDA, "internal error: a history reached a phase no event handles");
     if (H.status & kStatusLiveStall)
-        return gpet_fail(GPET_ERR_CUDA, "internal error: a live launch waited too long for work or its end");
+        return gpet_fail(GPET_ERR_CUDA,
+                         "internal error: a live launch waited %.3f s for work or its end (it last saw %llu "
+                         "chunks published, closed flag %llu; the host had published %llu)",
+                         H.counters[17] * 1e-9, H.counters[18], H.counters[19],
+                         (unsigned long long)R.live_tail);
     if (H.status & kStatusSortStall)
         return gpet_fail(GPET_ERR_CUDA, "internal error: a time-sort tile copy did not complete");
     if (H.status & kStatusOverflow)

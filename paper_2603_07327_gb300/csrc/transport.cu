@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int
     Refill rf;
     refill_init(rf);
     int status = kStatusOk;
-    uint32_t idle_polls = 0;
+    LiveIdle idle;
+    live_idle_reset(idle);
 
     for (;;) {
         const uint32_t need = __ballot_sync(kFullMask, s.phase == kPhIdle);
@@ -62,10 +63,10 @@ __global__ void __launch_bounds__(256) k_transport_loop(WorkDev W, OutDev O, int
         }
         if (__all_sync(kFullMask, s.phase == kPhIdle)) {
             // the queue is exhausted, or a live launch has nothing published yet
-            if (!rf.waiting || live_idle_wait(idle_polls, status)) break;
+            if (!rf.waiting || __any_sync(kFullMask, live_idle_wait(idle, status, W, O))) break;
             continue;
         }
-        idle_polls = 0;
+        live_idle_reset(idle);
 
         const JobDev &J = W.jobs[s.job];
         const GeomDev &g = J.geom < ng_smem ? sgeom[J.geom] : W.geoms[J.geom];

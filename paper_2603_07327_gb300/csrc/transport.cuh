@@ -82,9 +82,16 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 constexpr unsigned long long kNoChunk = ~0ull;
-// idle waits of a live launch: a sleep that doubles up to 16 us, at most this
-// many in a row (about 4 s) before the kernel gives up with kStatusLiveStall
-constexpr uint32_t kLiveIdlePolls = 1u << 18;
+// idle waits of a live launch: sleeps that double up to 16 us, for at most
+// this long in a row by the GPU's global timer before the kernel gives up with
+// kStatusLiveStall (a sleep's length is only approximate, the timer is not)
+constexpr unsigned long long kLiveIdleNs = 10ull * 1000 * 1000 * 1000;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Where a warp takes its next histories from: the current chunk [next, end) of
 // job `job`, a chunk index claimed but not yet published (pend), and whether
@@ -178,15 +185,37 @@ __device__ __forceinline__ void warp_refill(const WorkDev &W, uint32_t need, Ref
     }
 }
 
+// Idle state of a live launch's warp or CTA: when its idle stretch began (by
+// the global timer, 0 = not idle) and how many sleeps it took.
+struct LiveIdle {
+    unsigned long long t0;
+    uint32_t polls;
+};
+
+__device__ __forceinline__ void live_idle_reset(LiveIdle &w) {
+    w.t0 = 0;
+    w.polls = 0;
+}
+
 // One idle wait of a live launch whose slots are all idle while work may still
-// be published: sleeps (doubling up to 16 us) and returns false, or returns
-// true with kStatusLiveStall once kLiveIdlePolls waits ran in a row.
-__device__ __forceinline__ bool live_idle_wait(uint32_t &polls, int &status) {
-    if (++polls > kLiveIdlePolls) {
+// be published: sleeps (doubling up to 16 us) and returns false, or, once the
+// idle stretch has lasted kLiveIdleNs, records it (counters 17..19: the
+// stretch in ns, the published chunk count and the closed flag it last saw),
+// sets kStatusLiveStall and returns true.
+__device__ __forceinline__ bool live_idle_wait(LiveIdle &w, int &status, const WorkDev &W, const OutDev &O) {
+    const unsigned long long now = global_ns();
+    if (w.t0 == 0) w.t0 = now;
+    if (now - w.t0 > kLiveIdleNs) {
         status |= kStatusLiveStall;
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(O.counters + 17, now - w.t0);
+            atomicMax(O.counters + 18, *reinterpret_cast<const volatile unsigned long long *>(W.live_tail));
+            atomicMax(O.counters + 19, (unsigned long long)*reinterpret_cast<const volatile int *>(W.live_closed));
+        }
         return true;
     }
-    __nanosleep(polls < 14u ? (1u << polls) : 16384u);
+    ++w.polls;
+    __nanosleep(w.polls < 14u ? (1u << w.polls) : 16384u);
     return false;
 }
 

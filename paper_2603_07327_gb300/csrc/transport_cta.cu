@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
     Refill rf;
     refill_init(rf);
     int status = kStatusOk;
-    uint32_t idle_polls = 0;
+    LiveIdle idle;
+    live_idle_reset(idle);
     unsigned long long iters = 0, lanes_used = 0;
     int buf = 0;
     // slots turn idle only in the finish event (or on an error); a warp whose
@@ -188,10 +189,15 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
         if ((best >> 3) == 0) {
             // every slot of every warp idle after refills: done, unless a warp
             // of a live launch waits for a chunk the host has not published yet
-            if (!any_waiting || live_idle_wait(idle_polls, status)) break;
+            if (!any_waiting) break;
+            // one decision for the whole CTA: its threads leave the loop together
+            if (__syncthreads_or(live_idle_wait(idle, status, W, O))) {
+                status |= kStatusLiveStall;
+                break;
+            }
             continue;
         }
-        idle_polls = 0;
+        live_idle_reset(idle);
         // 4. lanes onto this warp's slots of the chosen phase: the slot of
         //    rank r (in slot order) goes to lane r
         int mine = 0;

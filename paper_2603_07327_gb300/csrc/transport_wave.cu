@@ -122,7 +122,8 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
     Refill rf;
     refill_init(rf);
     int status = kStatusOk;
-    uint32_t idle_polls = 0;
+    LiveIdle idle;
+    live_idle_reset(idle);
     unsigned long long iters = 0, lanes_used = 0;   // wavefront fill diagnostics
 
     for (;;) {
@@ -170,10 +171,10 @@ __global__ void __launch_bounds__(kWaveWarps * 32) k_transport_wave(WorkDev W, O
         if (best_n == 0) {
             // every slot idle after a refill: the queue is exhausted, or a live
             // launch has nothing published yet
-            if (!rf.waiting || live_idle_wait(idle_polls, status)) break;
+            if (!rf.waiting || __any_sync(kFullMask, live_idle_wait(idle, status, W, O))) break;
             continue;
         }
-        idle_polls = 0;
+        live_idle_reset(idle);
         // 3. lane i takes the i-th slot of that phase
         const bool active = lane < best_n;
         int q = 0;

@@ -48,8 +48,33 @@ def allreduce_tallies(counts, efx, group=None):
 
 
 def gather_singles(singles, group=None):
-    """All ranks' singles, merged and time-ordered, on every rank."""
+    """All ranks' singles, merged and time-ordered, on every rank.
+
+    Tensor collectives, no pickling: the ranks first exchange their singles
+    counts (one all-gather of an int64), then every field is all-gathered as a
+    tensor padded to the largest count (64-bit unsigned fields travel as their
+    int64 bit patterns), and each rank trims the padding before the merge."""
+    import torch
     import torch.distributed as dist
-    parts = [None] * dist.get_world_size(group)
-    dist.all_gather_object(parts, {f: np.asarray(v) for f, v in singles.items()}, group=group)
+    world = dist.get_world_size(group)
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    fields = [f for f in SINGLE_FIELDS if f in singles]
+    n = len(np.asarray(singles[fields[0]])) if fields else 0
+    counts = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(world)]
+    dist.all_gather(counts, torch.tensor([n], dtype=torch.int64, device=dev), group=group)
+    counts = [int(c.item()) for c in counts]
+    cap = max(counts + [1])
+    parts = [dict() for _ in range(world)]
+    for f in fields:
+        a = np.asarray(singles[f])
+        dt = a.dtype
+        wire = a.view(np.int64) if dt == np.uint64 else a
+        buf = np.zeros(cap, dtype=wire.dtype)
+        buf[:n] = wire
+        t = torch.from_numpy(buf).to(dev)
+        out = [torch.empty_like(t) for _ in range(world)]
+        dist.all_gather(out, t, group=group)
+        for r in range(world):
+            v = out[r].cpu().numpy()[:counts[r]]
+            parts[r][f] = v.view(np.uint64) if dt == np.uint64 else v
     return merge_singles(parts)
