@@ -6,8 +6,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "gpet.h"
@@ -37,6 +39,50 @@ int gpet_cuda_fail(cudaError_t e, const char *where) {
 
 extern "C" const char *gpet_last_error(void) { return t_err.c_str(); }
 extern "C" const char *gpet_version(void) { return "gpet-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// kernel loading and shared-memory limits (see internal.h)
+// ---------------------------------------------------------------------------
+namespace gpet {
+
+static std::mutex g_attr_mutex;
+static std::map<std::pair<int, const void *>, size_t> g_smem_limit;  // (device, kernel) -> limit set
+
+cudaError_t ensure_dynamic_smem(const void *fn, size_t bytes) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    // the limit covers the kernel's static shared memory as well
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    const size_t cap = optin > (int)fa.sharedSizeBytes ? (size_t)(optin - (int)fa.sharedSizeBytes) : 0;
+    bytes = std::min(bytes, cap);
+    std::lock_guard<std::mutex> lk(g_attr_mutex);
+    size_t &have = g_smem_limit[std::make_pair(dev, fn)];
+    if (bytes <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
+
+cudaError_t preload_kernels() {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return cudaSuccess;
+    e = preload_transport_kernels();
+    if (e == cudaSuccess) e = preload_sort_kernels();
+    if (e == cudaSuccess) e = preload_window_kernels();
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
+}  // namespace gpet
 
 // ---------------------------------------------------------------------------
 // Klein-Nishina ratio table g(E) = sigma_KN(E) / sigma_KN(511 keV), built in

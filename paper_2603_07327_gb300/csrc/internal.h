@@ -72,17 +72,37 @@ struct JobStatsDev {
     const long long *tally_off, *tally_n; // [n_jobs]
 };
 
+// most geometry descriptors a transport CTA stages in shared memory
+constexpr int kMaxStagedGeoms = 16;
+
+// Raise kernel fn's dynamic shared-memory limit on the current device to at
+// least `bytes` (capped at the device's opt-in maximum).  The attribute is set
+// only when it grows, so a launch never changes it while a live launch of the
+// same kernel may be running (a change can wait for running launches).
+cudaError_t ensure_dynamic_smem(const void *fn, size_t bytes);
+
+// Load every kernel the transport and digitizer can launch (and set their
+// shared-memory limits), once per device.  CUDA loads kernels lazily, and a
+// load can wait for running kernels: a live launch's kernel waits on the host,
+// so nothing may be loaded while it runs.
+cudaError_t preload_kernels();
+cudaError_t preload_transport_kernels();
+cudaError_t preload_wave_kernels();
+cudaError_t preload_cta_kernels();
+cudaError_t preload_sort_kernels();
+cudaError_t preload_window_kernels();
+
 // Geometry descriptors a transport launch stages in shared memory: as many of
 // the first min(n_geoms, max_geoms) as fit without fewer resident CTAs than a
-// launch that stages none (the rest are read through L1).  Sets the kernel's
-// dynamic shared-memory limit to the chosen size.
+// launch that stages none (the rest are read through L1).  The kernel's
+// dynamic shared-memory limit covers the largest staging.
 template <class Kernel>
 cudaError_t staged_geometry(Kernel k, int block, size_t pool_smem, int n_geoms, int max_geoms, int *ng_out,
                             size_t *smem_out, int *occ_out) {
     int ng = n_geoms < max_geoms ? n_geoms : max_geoms;
     if (ng < 0) ng = 0;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(pool_smem + (size_t)ng * sizeof(GeomDev)));
+    cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void *>(k),
+                                        pool_smem + (size_t)(max_geoms > 0 ? max_geoms : 0) * sizeof(GeomDev));
     if (e != cudaSuccess) return e;
     int occ0 = 0, occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k, block, pool_smem);
@@ -95,7 +115,7 @@ cudaError_t staged_geometry(Kernel k, int block, size_t pool_smem, int n_geoms, 
     *ng_out = ng;
     *smem_out = pool_smem + (size_t)ng * sizeof(GeomDev);
     *occ_out = occ;
-    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem_out);
+    return cudaSuccess;
 }
 
 cudaError_t launch_job_stats(const SinglesDev &s, const CoincDev &C, const JobStatsDev &J, cudaStream_t st);

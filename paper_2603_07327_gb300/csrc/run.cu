@@ -69,6 +69,8 @@ int run_default_cfg(Run &R, const gpet_options *opt_in, const gpet_scanner *sc) 
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaGetDevice");
     R.device = dev;
     keep_pool_memory(dev);
+    e = preload_kernels();  // all of them, once per device: no lazy load while a live launch runs
+    if (e != cudaSuccess) return gpet_cuda_fail(e, "kernel preload");
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaDeviceGetAttribute");
@@ -89,7 +91,7 @@ int run_default_cfg(Run &R, const gpet_options *opt_in, const gpet_scanner *sc) 
     R.cfg.pool_depth = (opt && opt->pool_depth > 0) ? opt->pool_depth : 2;
     if (R.cfg.pool_depth > 4) return gpet_fail(GPET_ERR_INVALID_ARG, "pool_depth must be in [1, 4]");
     if (R.cfg.compact_every > 64) return gpet_fail(GPET_ERR_INVALID_ARG, "compact_every must be <= 64");
-    R.cfg.max_smem_geoms = 16;
+    R.cfg.max_smem_geoms = kMaxStagedGeoms;
     R.keep_hits = opt && opt->keep_hits;
     R.stream = opt ? reinterpret_cast<cudaStream_t>(opt->stream) : nullptr;
     return GPET_OK;
@@ -122,7 +124,7 @@ int run_plan(Run &R) {
     uint64_t total = 0;
     for (auto &J : R.jobs) total += J.n_hist;
     uint64_t cs = R.live_cap.chunk;
-    if (!R.live) {
+    if (!R.live && !R.digitize_only) {
         // chunks: about 48 per resident warp, so that warps run out of work
         // within a small fraction of the launch of one another (32..4096)
         long long warps = 0;

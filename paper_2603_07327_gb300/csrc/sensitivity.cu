@@ -89,6 +89,12 @@ cudaError_t launch_coinc_windows(const SinglesDev &s, const CoincDev &C, const W
     return cudaGetLastError();
 }
 
+// load the window-count kernel (internal.h)
+cudaError_t preload_window_kernels() {
+    cudaFuncAttributes fa;
+    return cudaFuncGetAttributes(&fa, k_coinc_windows);
+}
+
 }  // namespace gpet
 
 using namespace gpet;

@@ -578,7 +578,10 @@ extern "C" int gpet_server_create(const gpet_server_config *cfg, gpet_server **o
     const uint64_t piece_cap = std::max<uint64_t>(1024, (uint64_t)(S->launch_singles / kGuessPerDecay / 2));
     S->piece = std::min<uint64_t>(cfg->piece_decays > 0 ? cfg->piece_decays : 4000000, piece_cap);
     cudaError_t e = cudaGetDevice(&S->device);
-    if (e != cudaSuccess) { delete S; return gpet_cuda_fail(e, "cudaGetDevice"); }
+    // every kernel a launch may run is loaded now: loading one later could wait
+    // for a live launch, whose kernel waits for the pipeline
+    if (e == cudaSuccess) e = preload_kernels();
+    if (e != cudaSuccess) { delete S; return gpet_cuda_fail(e, "server set-up"); }
     S->pipeline = std::thread(pipeline_main, S);
     *out = S;
     return GPET_OK;

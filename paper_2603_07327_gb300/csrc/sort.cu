@@ -354,11 +354,9 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_scatter(SortDev S, int p) {
 }
 
 static cudaError_t scatter_smem_attr() {
-    cudaError_t e = cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kScatterSmem);
+    cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void *>(k_scatter<false>), kScatterSmem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kScatterSmemStaged);
+    return ensure_dynamic_smem(reinterpret_cast<const void *>(k_scatter<true>), kScatterSmemStaged);
 }
 
 // singles into time order
@@ -553,6 +551,21 @@ cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const Coi
     k_coinc_scan<<<1, 1024, 0, st>>>(out, C);
     k_coinc_write<<<cg, 1024, 0, st>>>(out, C);
     return cudaGetLastError();
+}
+
+// load the digitizer's kernels and set their shared-memory limits (internal.h)
+cudaError_t preload_sort_kernels() {
+    const void *fns[] = {reinterpret_cast<const void *>(k_make_keys), reinterpret_cast<const void *>(k_plan),
+                         reinterpret_cast<const void *>(k_tile_hist), reinterpret_cast<const void *>(k_digit_scan),
+                         reinterpret_cast<const void *>(k_gather), reinterpret_cast<const void *>(k_coinc_flags),
+                         reinterpret_cast<const void *>(k_coinc_count), reinterpret_cast<const void *>(k_coinc_scan),
+                         reinterpret_cast<const void *>(k_coinc_write), reinterpret_cast<const void *>(k_job_stats)};
+    cudaFuncAttributes fa;
+    for (const void *f : fns) {
+        const cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return e;
+    }
+    return scatter_smem_attr();
 }
 
 }  // namespace gpet

@@ -192,4 +192,16 @@ cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg 
     return cudaGetLastError();
 }
 
+// load the transport kernels and set their shared-memory limits (internal.h)
+cudaError_t preload_transport_kernels() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_transport_redo);
+    if (e == cudaSuccess)
+        e = ensure_dynamic_smem(reinterpret_cast<const void *>(k_transport_loop<8>),
+                                loop_smem(kMaxStagedGeoms, 256, 8));
+    if (e == cudaSuccess) e = preload_wave_kernels();
+    if (e == cudaSuccess) e = preload_cta_kernels();
+    return e;
+}
+
 }  // namespace gpet

@@ -343,4 +343,21 @@ cudaError_t launch_transport_cta(const WorkDev &W, const OutDev &O, const Launch
     }
 }
 
+template <int SPL, int WARPS>
+static cudaError_t preload_cta() {
+    return ensure_dynamic_smem(reinterpret_cast<const void *>(k_transport_cta<SPL, WARPS>),
+                               sizeof(CtaPool<SPL>) * WARPS + (size_t)kMaxStagedGeoms * sizeof(GeomDev));
+}
+
+// load every instantiation and set its shared-memory limit (internal.h)
+cudaError_t preload_cta_kernels() {
+    cudaError_t e = preload_cta<2, 4>();
+    if (e == cudaSuccess) e = preload_cta<2, 8>();
+    if (e == cudaSuccess) e = preload_cta<2, 16>();
+    if (e == cudaSuccess) e = preload_cta<3, 4>();
+    if (e == cudaSuccess) e = preload_cta<3, 8>();
+    if (e == cudaSuccess) e = preload_cta<3, 16>();
+    return e;
+}
+
 }  // namespace gpet

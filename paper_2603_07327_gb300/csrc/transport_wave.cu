@@ -285,4 +285,18 @@ cudaError_t wave_resident_warps(int n_geoms, const LaunchCfg &cfg, long long *wa
     return e;
 }
 
+template <int SPL>
+static cudaError_t preload_wave() {
+    return ensure_dynamic_smem(reinterpret_cast<const void *>(k_transport_wave<SPL>),
+                               sizeof(WarpPool<SPL>) * kWaveWarps + (size_t)kMaxStagedGeoms * sizeof(GeomDev));
+}
+
+// load every instantiation and set its shared-memory limit (internal.h)
+cudaError_t preload_wave_kernels() {
+    cudaError_t e = preload_wave<2>();
+    if (e == cudaSuccess) e = preload_wave<3>();
+    if (e == cudaSuccess) e = preload_wave<4>();
+    return e;
+}
+
 }  // namespace gpet
