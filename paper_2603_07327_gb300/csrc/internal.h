@@ -119,7 +119,11 @@ cudaError_t staged_geometry(Kernel k, int block, size_t pool_smem, int n_geoms, 
 }
 
 cudaError_t launch_job_stats(const SinglesDev &s, const CoincDev &C, const JobStatsDev &J, cudaStream_t st);
-cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
+// the transport kernel cfg selects, then (with_redo) the re-simulation of
+// histories whose singles list overflowed
+cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st,
+                             bool with_redo = true);
+cudaError_t launch_transport_redo(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
 cudaError_t launch_transport_wave(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
 cudaError_t launch_transport_cta(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st);
 // warps resident at once in the transport launch that cfg selects (sizes the work chunks)

@@ -356,10 +356,14 @@ int run_enqueue_transport(Run &R) {
     cudaError_t e = cudaMemsetAsync(R.arena, 0, R.zero_bytes, R.stream);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaMemsetAsync");
     e = cudaEventRecordWithFlags(R.ev[0], R.stream, rec_flags);
-    if (e == cudaSuccess) e = launch_transport(R.W, R.O, R.cfg, R.stream);
+    // A live launch's kernel waits on the host: nothing else is launched while
+    // it runs (the re-simulation of overflowed histories follows at its close).
+    if (e == cudaSuccess) e = launch_transport(R.W, R.O, R.cfg, R.stream, !R.live);
     if (e != cudaSuccess) return gpet_cuda_fail(e, "transport launch");
-    e = cudaEventRecordWithFlags(R.ev[1], R.stream, rec_flags);
-    if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaEventRecord");
+    if (!R.live) {
+        e = cudaEventRecordWithFlags(R.ev[1], R.stream, rec_flags);
+        if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaEventRecord");
+    }
     return GPET_OK;
 }
 
@@ -377,6 +381,10 @@ int run_enqueue_digitizer(Run &R) {
         e = cudaEventRecordWithFlags(R.ev[0], R.stream, rec_flags);
         if (e == cudaSuccess) e = cudaEventRecordWithFlags(R.ev[1], R.stream, rec_flags);
         if (e != cudaSuccess) return gpet_cuda_fail(e, "cudaEventRecord");
+    } else if (R.live) {    // closed: the re-simulation of overflowed histories, then the transport's end
+        e = launch_transport_redo(R.W, R.O, R.cfg, R.stream);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(R.ev[1], R.stream, rec_flags);
+        if (e != cudaSuccess) return gpet_cuda_fail(e, "re-simulation launch");
     }
     R.JS.n_jobs = (int)R.jobs.size();
     e = launch_sort_coinc(R.S, R.SD, R.C, R.cfg.sm_count, R.stream);

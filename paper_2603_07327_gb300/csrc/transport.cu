@@ -171,7 +171,13 @@ cudaError_t transport_resident_warps(int n_geoms, const LaunchCfg &cfg, long lon
     return e;
 }
 
-cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
+cudaError_t launch_transport_redo(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st) {
+    k_transport_redo<<<cfg.sm_count, 128, 0, st>>>(W, O);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg &cfg, cudaStream_t st,
+                             bool with_redo) {
     constexpr int S = 8;
     if (cfg.kernel == kKernelWave) {
         cudaError_t e = launch_transport_wave(W, O, cfg, st);
@@ -188,14 +194,19 @@ cudaError_t launch_transport(const WorkDev &W, const OutDev &O, const LaunchCfg 
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    k_transport_redo<<<cfg.sm_count, 128, 0, st>>>(W, O);
-    return cudaGetLastError();
+    return with_redo ? launch_transport_redo(W, O, cfg, st) : cudaSuccess;
 }
 
-// load the transport kernels and set their shared-memory limits (internal.h)
+// Load the transport kernels and set their shared-memory limits (internal.h).
+// The re-simulation kernel keeps its long singles list in local memory: the
+// per-thread stack limit is raised to hold it now, since growing the device's
+// local-memory reservation at a later launch waits for every running kernel.
 cudaError_t preload_transport_kernels() {
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, k_transport_redo);
+    size_t stack = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetLimit(&stack, cudaLimitStackSize);
+    if (e == cudaSuccess && stack < fa.localSizeBytes) e = cudaDeviceSetLimit(cudaLimitStackSize, fa.localSizeBytes);
     if (e == cudaSuccess)
         e = ensure_dynamic_smem(reinterpret_cast<const void *>(k_transport_loop<8>),
                                 loop_smem(kMaxStagedGeoms, 256, 8));
