@@ -14,7 +14,9 @@
 // until it is max_launch_ms old or a table is full, or until the queue is empty
 // and every published chunk has been claimed; it is then closed, its time sort,
 // coincidence sorting and per-job statistics are enqueued behind its transport
-// on the same stream, and the next launch opens behind those.  Device memory
+// on the same stream, and the next launch opens once those have run and the
+// results have been collected (while a live kernel holds every SM, the loop
+// makes no device-to-device copy: such a copy may need the SMs).  Device memory
 // counts against the budget per launch arena and per split request, from
 // allocation until the results that view it are freed.  Every random number is
 // addressed by (seed, history), so a request's result is the same alone and in
@@ -363,9 +365,10 @@ int close_launch(gpet_server *S, Launch &L) {
 
 // Results of a launch whose work (and that of the digitizers behind it) is
 // done.  Requests that met a full buffer go to `rerun`: they run again, whole
-// and with exact sizes, once no launch is on the GPU.
+// and with exact sizes, once no launch is on the GPU.  The compact copies of
+// the results go on st_copy, called with no live launch on the GPU.
 void finish_launch(gpet_server *S, Launch &L, int close_status, const std::string &close_error,
-                   std::vector<Req *> &rerun, cudaStream_t up) {
+                   std::vector<Req *> &rerun, cudaStream_t st_copy) {
     int st = close_status;
     std::string err = close_error;
     if (st == GPET_OK) {
@@ -377,7 +380,7 @@ void finish_launch(gpet_server *S, Launch &L, int close_status, const std::strin
     std::shared_ptr<Run> views = L.R;
     if (st == GPET_OK && !L.whole.empty()) {
         int cst = GPET_OK;
-        std::shared_ptr<Run> compact = run_compact(*L.R, up, &cst);
+        std::shared_ptr<Run> compact = run_compact(*L.R, st_copy, &cst);
         if (compact) {
             charge(S, *compact, compact->arena_bytes);
             views = compact;
@@ -408,7 +411,7 @@ void finish_launch(gpet_server *S, Launch &L, int close_status, const std::strin
         }
         if (s2 == GPET_OK) {
             int cst = GPET_OK;
-            std::shared_ptr<Run> own = run_compact(*r->own, up, &cst);
+            std::shared_ptr<Run> own = run_compact(*r->own, st_copy, &cst);
             if (own) charge(S, *own, own->arena_bytes);
             else own = r->own;
             publish(S, r, GPET_OK, "", own, 0);
@@ -443,7 +446,7 @@ void pipeline_main(gpet_server *S) {
         while (!inflight.empty() && cudaEventQuery(inflight.front().first->done) != cudaErrorNotReady) {
             cudaGetLastError();
             finish_launch(S, *inflight.front().first, inflight.front().second.first, inflight.front().second.second,
-                          rerun, P.up);
+                          rerun, P.gpu);
             inflight.pop_front();
         }
         // requests that met a full buffer run again alone, with exact sizes, on
@@ -474,6 +477,15 @@ void pipeline_main(gpet_server *S) {
             if (S->stop && S->queue.empty() && !open && inflight.empty()) break;
             if (S->queue.empty() && !open && inflight.empty()) {
                 C.cv.wait(lk);
+                continue;
+            }
+            if (!S->queue.empty() && !open && !inflight.empty()) {
+                // The next live launch opens only once the last one has been
+                // collected: its results are compacted by device-to-device
+                // copies, which may run on the SMs, and a live kernel holds
+                // every SM while it waits on this thread.
+                lk.unlock();
+                cudaEventSynchronize(inflight.front().first->done);
                 continue;
             }
             work.assign(S->queue.begin(), S->queue.end());
