@@ -108,7 +108,8 @@ struct __align__(128) JobDev {
     unsigned long long *tally_count, *tally_efx;
     // singles of this job: NULL s_raw appends them to the launch's buffer;
     // else to the job's own (a served request split over several launches
-    // gathers its singles there), counted in *n_singles up to s_cap
+    // gathers its singles there), counted in *n_singles up to s_cap and
+    // recorded as job 0 (the one job of the run that owns that buffer)
     RawSingle *s_raw;
     unsigned long long *n_singles;
     unsigned long long s_cap;

@@ -644,7 +644,8 @@ __device__ __forceinline__ void ev_finish(const JobDev *__restrict__ jobs, const
                 const uint64_t t = s.t0 + dt;
                 uint4 *r = reinterpret_cast<uint4 *>(dst + slot);
                 r[0] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)s.h, (uint32_t)(s.h >> 32));
-                r[1] = make_uint4(unit, (uint32_t)panel, (uint32_t)s.job, __float_as_uint(eb));
+                // a job with its own buffer is job 0 of the run that buffer belongs to
+                r[1] = make_uint4(unit, (uint32_t)panel, J->s_raw ? 0u : (uint32_t)s.job, __float_as_uint(eb));
                 r[2] = make_uint4(__float_as_uint(e), __float_as_uint(db), 0u, 0u);
             }
         }
