@@ -617,11 +617,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_t0 = time.perf_counter()
     sim_s = 0.0
+    copy_ms = []
     h2d = d2h = 0
     for k in range(args.steps):
         t0 = time.perf_counter()
         res = e2e_simulate()
-        sim_s += time.perf_counter() - t0
+        t1 = time.perf_counter()
+        sim_s += t1 - t0
         h2d = d2h = 0
         for r in views_of(res):
             h2d += r.counts()["h2d_bytes"]
@@ -633,11 +635,25 @@ def run_ours(args):
                 d2h += nb
         for cs in copy_streams.values():
             cs.synchronize()
+        copy_ms.append(1000 * (time.perf_counter() - t1))
         for r in res:
             r.free()
     torch.cuda.synchronize()
     e2e_dt = (time.perf_counter() - e2e_t0) / args.steps
     e2e_sim_s = sim_s / args.steps
+    # the copy leg against a plain pinned copy of 1 GiB from device memory,
+    # measured here in the same process (best of 3 after one untimed copy)
+    blk = torch.ones(1 << 30, dtype=torch.uint8, device="cuda")
+    hb = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+    plain_gbs = 0.0
+    for k in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hb.copy_(blk, non_blocking=True)
+        torch.cuda.synchronize()
+        if k:
+            plain_gbs = max(plain_gbs, (1 << 30) / (time.perf_counter() - t0) / 1e9)
+    del blk, hb
     if dist:
         t = torch.tensor([e2e_dt], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -656,7 +672,9 @@ def run_ours(args):
                 wall_s=wall, gpu_launches=None, roofline=roof, roofline_digitizer=roof_dig, clocks=clk,
                 e2e=dict(value=pairs_per_step * world / e2e_dt, unit="pairs/s", h2d_bytes_per_step=h2d,
                          d2h_bytes_per_step=d2h, ms_per_step=1000 * e2e_dt, simulate_ms_per_step=1000 * e2e_sim_s,
-                         copy_ms_per_step=1000 * (e2e_dt - e2e_sim_s), host_buffers="pinned, caller-owned, reused",
+                         copy_ms_per_step=1000 * (e2e_dt - e2e_sim_s), copy_ms_steps=[round(c, 2) for c in copy_ms],
+                         d2h_gbs=d2h / (1e-3 * min(copy_ms)) / 1e9 if copy_ms and min(copy_ms) > 0 else None,
+                         plain_pinned_d2h_gbs=plain_gbs, host_buffers="pinned, caller-owned, reused",
                          copies="one async copy per array of the whole launch, arrays on concurrent streams"),
                 stages=dict(transport_ms_per_step=tr_ms / args.steps, digitizer_ms_per_step=dg_ms / args.steps),
                 per_step_counts=dict(hits=sum(c["hits"] for c in counts) // args.steps,
