@@ -303,7 +303,11 @@ def run_served(G, args):
                     offered_pairs_per_s=pairs / (reqs[-1]["arrival_s"] / compress), wall_s=wall,
                     launches=st["launches"] - st0["launches"], max_jobs_per_launch=st["max_jobs_per_launch"],
                     live_appends=st["live_appends"] - st0["live_appends"], pieces=st["pieces"] - st0["pieces"],
-                    peak_hbm_bytes=st["peak_bytes"])
+                    peak_hbm_bytes=st["peak_bytes"],
+                    # GPU time of the launches' stages (CUDA events): the live kernels
+                    # from open to close, and every time sort / coincidence pass
+                    transport_gpu_s=(st["transport_ms"] - st0["transport_ms"]) / 1000.0,
+                    digitizer_gpu_s=(st["digitizer_ms"] - st0["digitizer_ms"]) / 1000.0)
 
     poisson = serve(1.0)
     saturated = serve(args.served_compress)
@@ -311,9 +315,14 @@ def run_served(G, args):
     k = min(len(reqs), args.served_plain_sample) if args.served_plain_sample > 0 else len(reqs)
     scanners[0].simulate(reqs[0]["source"], reqs[0]["digitizer"], 100_000, 1, kernel=args.kernel).free()
     tp = time.perf_counter()
+    plain_tr = plain_dg = 0.0
     for i in range(k):
-        scanners[i].simulate(reqs[i]["source"], reqs[i]["digitizer"], reqs[i]["n_decays"], reqs[i]["seed"],
-                             kernel=args.kernel).free()
+        res = scanners[i].simulate(reqs[i]["source"], reqs[i]["digitizer"], reqs[i]["n_decays"], reqs[i]["seed"],
+                                   kernel=args.kernel)
+        c = res.counts()
+        plain_tr += c["transport_ms"] / 1000.0
+        plain_dg += c["digitizer_ms"] / 1000.0
+        res.free()
     tp = time.perf_counter() - tp
     pairs_plain = sum(reqs[i]["n_decays"] for i in range(k))
     for sc in scanners:
@@ -325,6 +334,8 @@ def run_served(G, args):
                 poisson=poisson,
                 saturated=dict(saturated, compress=args.served_compress),
                 sequential_plain_pairs_per_s=pairs_plain / tp, sequential_plain_requests=k,
+                sequential_plain_transport_gpu_s=plain_tr, sequential_plain_digitizer_gpu_s=plain_dg,
+                sequential_plain_wall_s=tp,
                 saturated_over_sequential_plain=saturated["pairs_per_s"] / (pairs_plain / tp))
 
 

@@ -486,6 +486,10 @@ typedef struct {
     uint64_t bytes_in_use, peak_bytes, queued;
     uint64_t live_appends;        /* jobs appended to a launch whose kernel was already running */
     uint64_t pieces;              /* history ranges of split requests handed to launches */
+    double transport_ms;          /* GPU time of the launches' transport kernels, open to close (a live
+                                   * kernel's waits for appended work included) */
+    double digitizer_ms;          /* GPU time of the launches' and split requests' time sorts and
+                                   * coincidence sorting */
 } gpet_server_stats;
 int gpet_server_create(const gpet_server_config *cfg, gpet_server **out);
 /* Queue one request.  The scanner (and its phantom) must stay alive until the

@@ -103,7 +103,8 @@ class ServerConfig(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "rejected", "launches", "max_jobs_per_launch",
                                           "pairs_completed", "bytes_in_use", "peak_bytes", "queued",
-                                          "live_appends", "pieces")]
+                                          "live_appends", "pieces")] + \
+              [("transport_ms", C.c_double), ("digitizer_ms", C.c_double)]
 
 
 # every entry point declared in include/gpet.h: name -> (restype, argtypes)

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kCostThreads) k_event_alone(WorkDev W, OutDev 
         else if (PH == kPhPhantom) ev_phantom(J, g, W, s, cnt);
         else if (PH == kPhFlight || PH == kPhFlightOut) ev_flight(J, g, s, cnt);
         else if (PH == kPhPanel) ev_panel<true>(J, g, W, O, s, SL, kListS, cnt);
-        else if (PH == kPhFinish) ev_finish(W.jobs, W.geoms, O, s, true, SL, kFullMask, cnt);
+        else if (PH == kPhFinish) ev_finish<false>(W.jobs, W.geoms, O, s, true, SL, kFullMask, cnt);
         acc ^= __float_as_uint(s.x) ^ __float_as_uint(s.E) ^ s.phase ^ cnt.singles ^ cnt.hits;
     }
     if (acc == 0x9E3779B9u) *sink = acc;  // never true in practice; keeps the work

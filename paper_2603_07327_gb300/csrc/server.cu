@@ -375,6 +375,11 @@ void finish_launch(gpet_server *S, Launch &L, int close_status, const std::strin
         st = run_collect(*L.R);
         if (st != GPET_OK) err = gpet_last_error();
     }
+    {
+        std::lock_guard<std::mutex> lk(S->core->mu);
+        S->stats.transport_ms += std::max(0.f, L.R->transport_ms);
+        S->stats.digitizer_ms += std::max(0.f, L.R->digitizer_ms);
+    }
     // the results move to memory of their own size, and the launch's buffers
     // go back at once (results a client keeps then hold only what they are)
     std::shared_ptr<Run> views = L.R;
@@ -408,6 +413,8 @@ void finish_launch(gpet_server *S, Launch &L, int close_status, const std::strin
         if (s2 == GPET_OK && r->own) {
             s2 = run_collect(*r->own);
             if (s2 != GPET_OK) e2 = gpet_last_error();
+            std::lock_guard<std::mutex> lk(S->core->mu);
+            S->stats.digitizer_ms += std::max(0.f, r->own->digitizer_ms);
         }
         if (s2 == GPET_OK) {
             int cst = GPET_OK;

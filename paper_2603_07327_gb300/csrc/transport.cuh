@@ -94,11 +94,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Where a warp takes its next histories from: the current chunk [next, end) of
-// job `job`, a chunk index claimed but not yet published (pend), and whether
-// the queue is exhausted.
+// job `job`, whose chunks are [jc0, jend) and histories h_base + [0, nh); a
+// chunk index claimed while a live launch had not yet published it (pend,
+// lane 0 only); and whether the queue is exhausted.
 struct Refill {
     uint64_t next, end;
     unsigned long long pend;
+    unsigned long long jc0, jend;
+    uint64_t base, nh;
     int job;
     bool exhausted, waiting;
 };
@@ -106,6 +109,8 @@ struct Refill {
 __device__ __forceinline__ void refill_init(Refill &r) {
     r.next = r.end = 0;
     r.pend = kNoChunk;
+    r.jc0 = r.jend = 0;
+    r.base = r.nh = 0;
     r.job = 0;
     r.exhausted = r.waiting = false;
 }
@@ -113,14 +118,16 @@ __device__ __forceinline__ void refill_init(Refill &r) {
 // Claim of the next chunk by a warp (lanes converged).  Lane 0 takes the next
 // index of the work counter, or re-checks the one it took before while that
 // chunk was not yet published.  Returns 1 (chunk c ready), 0 (a live launch
-// has not published it yet) or -1 (no more work).
+// has not published it yet) or -1 (no more work).  kLive = false: the caller
+// runs fixed launches only (live_tail is NULL), and the live branch is left out.
+template <bool kLive>
 __device__ __forceinline__ int claim_chunk(const WorkDev &W, unsigned long long &pend, unsigned long long &c) {
     int r = 0;
     unsigned long long cc = 0;
     if ((threadIdx.x & 31) == 0) {
         if (pend == kNoChunk) pend = atomicAdd(W.next_chunk, 1ull);
         cc = pend;
-        if (!W.live_tail) {
+        if (!kLive || !W.live_tail) {
             r = cc < W.total_chunks ? 1 : -1;
         } else {
             // closed first: once it reads 1, the tail read after it is final
@@ -134,13 +141,22 @@ __device__ __forceinline__ int claim_chunk(const WorkDev &W, unsigned long long 
     }
     r = __shfl_sync(kFullMask, r, 0);
     c = __shfl_sync(kFullMask, cc, 0);
-    if (r == 1 && W.live_tail) __threadfence();  // the chunk's table entries were written before its tail
+    if (kLive && r == 1 && W.live_tail) __threadfence();  // the chunk's table entries were written before its tail
     return r;
+}
+
+// a work-table entry: through L2 where a live launch may append to the table,
+// else through the read-only cache
+template <bool kLive, class T>
+__device__ __forceinline__ T table_load(const T *p) {
+    return kLive ? __ldcg(p) : __ldg(p);
 }
 
 // Warp-wide refill: lanes in `need` receive consecutive history ids from the
 // warp's current chunk, fetching new chunks (one atomic each) as needed.
-// Table reads go to L2 (ld.cg): a live launch appends to these tables.
+// kLive: table reads go to L2 (ld.cg), since a live launch appends to these
+// tables.
+template <bool kLive = true>
 __device__ __forceinline__ void warp_refill(const WorkDev &W, uint32_t need, Refill &R, bool &got, uint64_t &h,
                                             int &job) {
     const int lane = threadIdx.x & 31;
@@ -150,7 +166,7 @@ __device__ __forceinline__ void warp_refill(const WorkDev &W, uint32_t need, Ref
         const uint64_t avail = R.end - R.next;
         if (avail == 0) {
             unsigned long long c = 0;
-            const int cl = claim_chunk(W, R.pend, c);
+            const int cl = claim_chunk<kLive>(W, R.pend, c);
             if (cl < 0) {
                 R.exhausted = true;
                 break;
@@ -159,17 +175,35 @@ __device__ __forceinline__ void warp_refill(const WorkDev &W, uint32_t need, Ref
                 R.waiting = true;  // try again at the next refill
                 break;
             }
-            int lo = 0, hi = W.n_jobs - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldcg(W.chunk_start + mid) <= c) lo = mid; else hi = mid - 1;
+            if (c >= R.jend) {
+                // Another job: the last chunk_start entry <= c.  A warp's
+                // claims increase, so the search starts at its current job
+                // (chunk_start[job] <= c), gallops forward, then bisects.
+                int lo = R.job, hi = W.n_jobs - 1, step = 1;
+                while (lo < hi) {
+                    const int probe = min(lo + step, hi);
+                    if (table_load<kLive>(W.chunk_start + probe) <= c) {
+                        lo = probe;
+                        step <<= 1;
+                    } else {
+                        hi = probe - 1;
+                        break;
+                    }
+                }
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (table_load<kLive>(W.chunk_start + mid) <= c) lo = mid; else hi = mid - 1;
+                }
+                // a published job's entries are final (its end is written with it)
+                R.job = lo;
+                R.jc0 = table_load<kLive>(W.chunk_start + lo);
+                R.jend = table_load<kLive>(W.chunk_start + lo + 1);
+                R.base = table_load<kLive>(reinterpret_cast<const unsigned long long *>(&W.jobs[lo].h_base));
+                R.nh = table_load<kLive>(reinterpret_cast<const unsigned long long *>(&W.jobs[lo].n_hist));
             }
-            R.job = lo;
-            const uint64_t h0 = (uint64_t)(c - __ldcg(W.chunk_start + lo)) * W.chunk_size;
-            const uint64_t base = __ldcg(reinterpret_cast<const unsigned long long *>(&W.jobs[lo].h_base));
-            R.next = base + h0;
-            R.end = base + min(h0 + (uint64_t)W.chunk_size,
-                               (uint64_t)__ldcg(reinterpret_cast<const unsigned long long *>(&W.jobs[lo].n_hist)));
+            const uint64_t h0 = (uint64_t)(c - R.jc0) * W.chunk_size;
+            R.next = R.base + h0;
+            R.end = R.base + min(h0 + (uint64_t)W.chunk_size, R.nh);
             continue;
         }
         const uint32_t cnt = (uint32_t)__popc(need);
@@ -562,7 +596,10 @@ __device__ __forceinline__ int ev_panel(const JobDev &J, const GeomDev &g, const
 }
 
 // digitizer for one finished history: blur, window, warp-aggregated append
-// (call with the lanes of `mask` converged; `active` lanes own a history)
+// (call with the lanes of `mask` converged; `active` lanes own a history).
+// kJobDest = false: no job of the launch has a singles buffer of its own
+// (every fixed launch), and the singles go to the launch's buffer alone.
+template <bool kJobDest = true>
 __device__ __forceinline__ void ev_finish(const JobDev *__restrict__ jobs, const GeomDev *__restrict__ geoms,
                                           const OutDev &O, const PState &s, bool active, const SinglesList &SL,
                                           uint32_t mask, Counters &cnt) {
@@ -612,13 +649,13 @@ __device__ __forceinline__ void ev_finish(const JobDev *__restrict__ jobs, const
         // destination: the launch's singles buffer, or the job's own
         RawSingle *dst = O.s_raw;
         unsigned long long *dst_n = O.n_singles, dst_cap = O.s_cap;
-        if (keep && J->s_raw) {
+        if (kJobDest && keep && J->s_raw) {
             dst = J->s_raw;
             dst_n = J->n_singles;
             dst_cap = J->s_cap;
         }
         unsigned long long slot = 0;
-        if (__all_sync(mask, dst_n == O.n_singles)) {
+        if (!kJobDest || __all_sync(mask, dst_n == O.n_singles)) {
             // one counter for the warp (every fixed launch)
             unsigned long long base = 0;
             const int leader = __ffs(b) - 1;
@@ -645,7 +682,8 @@ __device__ __forceinline__ void ev_finish(const JobDev *__restrict__ jobs, const
                 uint4 *r = reinterpret_cast<uint4 *>(dst + slot);
                 r[0] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)s.h, (uint32_t)(s.h >> 32));
                 // a job with its own buffer is job 0 of the run that buffer belongs to
-                r[1] = make_uint4(unit, (uint32_t)panel, J->s_raw ? 0u : (uint32_t)s.job, __float_as_uint(eb));
+                r[1] = make_uint4(unit, (uint32_t)panel, kJobDest && J->s_raw ? 0u : (uint32_t)s.job,
+                                  __float_as_uint(eb));
                 r[2] = make_uint4(__float_as_uint(e), __float_as_uint(db), 0u, 0u);
             }
         }

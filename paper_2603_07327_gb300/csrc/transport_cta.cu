@@ -99,12 +99,37 @@ __device__ __forceinline__ void cstore(Pool &P, int q, const PState &s, bool all
     P.st[kCsteps][q] = (s.sph & 0xFFFFu) | (s.sdet << 16);
 }
 
+// one event of phase p for a lane's history
+__device__ __forceinline__ int run_event(int p, const JobDev &J, const GeomDev &g, const WorkDev &W, const OutDev &O,
+                                         PState &s, const SinglesList &SL, Counters &cnt) {
+    int st = kStatusOk;
+    switch (p) {
+        case kPhSource: ev_source(J, g, s, cnt); break;
+        case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
+        case kPhFlight: case kPhFlightOut: ev_flight(J, g, s, cnt); break;
+        case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, kCtaS, cnt); break;
+        default: st = kStatusBadPhase; break;
+    }
+    return st;
+}
+
+// Launch modes, one instantiation each, so that a fixed launch carries none
+// of the other modes' instructions:
+//   kModeFixed  : a fixed work table, one event per slot and phase choice;
+//   kModeRepeat : the compaction interval -- a slot repeats its event up to
+//                 `repeat` times while it stays in the chosen phase (steps of
+//                 the phantom and of the detector repeat);
+//   kModeLive   : a live launch (chunks the host appends while the kernel
+//                 runs, bounded idle waits, per-job singles buffers).
+enum : int { kModeFixed = 0, kModeRepeat = 1, kModeLive = 2 };
+
 }  // namespace
 
 // at most 128 registers a thread: 16 warps of the kernel stay resident per SM
-template <int SPL, int WARPS>
+template <int SPL, int WARPS, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1)) k_transport_cta(WorkDev W, OutDev O, int ng_smem,
                                                                                                  int repeat) {
+    constexpr bool kLive = MODE == kModeLive;
     using Pool = CtaPool<SPL>;
     constexpr int kPool = Pool::kPool;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -115,7 +140,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
     // i - 1 is cleared after the barrier of iteration i, which every read of
     // it precedes and every add of iteration i + 2 follows.
     __shared__ int census[3][8];
-    __shared__ unsigned long long phase_events[kNumPh];  // lanes that ran an event, per phase
+    __shared__ unsigned long long phase_events[WARPS][kNumPh];  // lanes that ran an event, per warp and phase
     __shared__ uint8_t assign[WARPS][32];  // slot of each lane in the chosen phase
     stage_geometry(W, sgeom, ng_smem);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -123,7 +148,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
 #pragma unroll
     for (int g = 0; g < SPL; ++g) P.st[kCpack][g * 32 + lane] = 0;
     if (threadIdx.x < 24) (&census[0][0])[threadIdx.x] = 0;
-    if (threadIdx.x < kNumPh) phase_events[threadIdx.x] = 0;
+    if (threadIdx.x < WARPS * kNumPh) (&phase_events[0][0])[threadIdx.x] = 0;
     __syncthreads();
 
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -149,17 +174,17 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
                 bool got;
                 uint64_t h = 0;
                 int job = 0;
-                warp_refill(W, need, rf, got, h, job);
+                warp_refill<kLive>(W, need, rf, got, h, job);
                 if (got) {
                     P.st[kCh0][q] = (uint32_t)h;
                     P.st[kCh1][q] = (uint32_t)(h >> 32);
                     P.st[kCjob][q] = (uint32_t)job;
                     P.st[kCpack][q] = (uint32_t)kPhSource << 16;
                 }
-                if (rf.waiting) break;
+                if (kLive && rf.waiting) break;
             }
         }
-        may_idle = rf.waiting && !rf.exhausted;
+        may_idle = kLive && rf.waiting && !rf.exhausted;
         __syncwarp();
         // 2. the warp's census: lane p adds the warp's count of phase p
         uint32_t ph[SPL];
@@ -178,7 +203,9 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
             if (lane == p) my_n = n;
         }
         if (my_n) atomicAdd(&census[buf][lane], my_n);
-        const int any_waiting = __syncthreads_or(rf.waiting && !rf.exhausted);
+        int any_waiting = 0;
+        if constexpr (kLive) any_waiting = __syncthreads_or(rf.waiting && !rf.exhausted);
+        else __syncthreads();
         // 3. every warp reads the same totals: the most populated phase wins
         //    (ties to the later phase, which finishes histories sooner)
         const uint32_t key = (lane >= 1 && lane < kNumPh) ? ((uint32_t)census[buf][lane] << 3) | (uint32_t)lane : 0u;
@@ -189,7 +216,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
         if ((best >> 3) == 0) {
             // every slot of every warp idle after refills: done, unless a warp
             // of a live launch waits for a chunk the host has not published yet
-            if (!any_waiting) break;
+            if (!kLive || !any_waiting) break;
             // one decision for the whole CTA: its threads leave the loop together
             if (__syncthreads_or(live_idle_wait(idle, status, W, O))) {
                 status |= kStatusLiveStall;
@@ -197,7 +224,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
             }
             continue;
         }
-        live_idle_reset(idle);
+        if (kLive) live_idle_reset(idle);
         // 4. lanes onto this warp's slots of the chosen phase: the slot of
         //    rank r (in slot order) goes to lane r
         int mine = 0;
@@ -216,7 +243,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
         if (mine == 0) continue;  // nothing of this phase here: wait for the next choice
         ++iters;
         lanes_used += (unsigned long long)min(mine, 32);
-        if (lane == 0) atomicAdd(&phase_events[best_p], (unsigned long long)min(mine, 32));
+        if (lane == 0) phase_events[wid][best_p] += (unsigned long long)min(mine, 32);  // this warp's row only
         PState s;
         s.phase = kPhIdle;
         s.job = 0;
@@ -224,7 +251,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
         if (best_p == kPhFinish) {
             if (active) cload(P, q, s);
             __syncwarp();
-            ev_finish(W.jobs, W.geoms, O, s, active, SL, kFullMask, cnt);
+            ev_finish<kLive>(W.jobs, W.geoms, O, s, active, SL, kFullMask, cnt);
             if (active) P.st[kCpack][q] = 0;
             may_idle = true;
             __syncwarp();
@@ -236,28 +263,25 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
             const JobDev &J = W.jobs[s.job];
             const GeomDev &g = J.geom < ng_smem ? sgeom[J.geom] : W.geoms[J.geom];
             int st = kStatusOk;
-            // the chosen event, then again while the slot stays in its phase, up
-            // to `repeat` events in all: the compaction interval (events between
-            // regroupings; only steps of the phantom and of the detector repeat)
-            do {
-                ++n_ev;
-                switch (best_p) {
-                    case kPhSource: ev_source(J, g, s, cnt); break;
-                    case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
-                    case kPhFlight: case kPhFlightOut: ev_flight(J, g, s, cnt); break;
-                    case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, kCtaS, cnt); break;
-                    default: st = kStatusBadPhase; break;
-                }
-            } while (st == kStatusOk && n_ev < repeat && s.phase == (uint32_t)best_p);
+            if constexpr (MODE == kModeRepeat) {
+                // the chosen event, then again while the slot stays in its
+                // phase, up to `repeat` events in all
+                do {
+                    ++n_ev;
+                    st = run_event(best_p, J, g, W, O, s, SL, cnt);
+                } while (st == kStatusOk && n_ev < repeat && s.phase == (uint32_t)best_p);
+            } else {
+                st = run_event(best_p, J, g, W, O, s, SL, cnt);
+            }
             if (st != kStatusOk) {
                 status |= st;
                 s.phase = kPhIdle;
             }
             cstore(P, q, s, best_p == kPhSource);
         }
-        if (repeat > 1) {  // the repeated events, beyond the one per lane counted above
+        if constexpr (MODE == kModeRepeat) {  // the repeated events, beyond the one per lane counted above
             const int extra = __reduce_add_sync(kFullMask, n_ev > 1 ? n_ev - 1 : 0);
-            if (lane == 0 && extra) atomicAdd(&phase_events[best_p], (unsigned long long)extra);
+            if (lane == 0) phase_events[wid][best_p] += (unsigned long long)extra;
         }
         may_idle = may_idle || __any_sync(kFullMask, active && s.phase == kPhIdle);
         __syncwarp();
@@ -276,16 +300,21 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
     }
     if (status) atomicOr(O.status, status);
     __syncthreads();  // every warp's event counts are in
-    if (threadIdx.x >= 1 && threadIdx.x < kNumPh && phase_events[threadIdx.x])
-        atomicAdd(O.counters + 10 + threadIdx.x, phase_events[threadIdx.x]);
+    if (threadIdx.x >= 1 && threadIdx.x < kNumPh) {
+        unsigned long long n = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) n += phase_events[w][threadIdx.x];
+        if (n) atomicAdd(O.counters + 10 + threadIdx.x, n);
+    }
 }
 
-// dynamic shared memory and resident CTAs of one instantiation
+// dynamic shared memory and resident CTAs of one shape (the same in every
+// mode: the launch bounds cap each mode's registers alike)
 template <int SPL, int WARPS>
 static cudaError_t cta_shape(int n_geoms, const LaunchCfg &cfg, size_t *smem, int *ctas, int *ng) {
     int occ = 0;
-    cudaError_t e = staged_geometry(k_transport_cta<SPL, WARPS>, WARPS * 32, sizeof(CtaPool<SPL>) * WARPS, n_geoms,
-                                    cfg.max_smem_geoms, ng, smem, &occ);
+    cudaError_t e = staged_geometry(k_transport_cta<SPL, WARPS, kModeFixed>, WARPS * 32, sizeof(CtaPool<SPL>) * WARPS,
+                                    n_geoms, cfg.max_smem_geoms, ng, smem, &occ);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     *ctas = cfg.sm_count * occ;
@@ -298,7 +327,11 @@ static cudaError_t launch_cta(const WorkDev &W, const OutDev &O, const LaunchCfg
     int ctas = 0, ng = 0;
     cudaError_t e = cta_shape<SPL, WARPS>(W.n_geoms, cfg, &smem, &ctas, &ng);
     if (e != cudaSuccess) return e;
-    k_transport_cta<SPL, WARPS><<<ctas, WARPS * 32, smem, st>>>(W, O, ng, max(1, cfg.compact_every));
+    // a live launch runs one event per choice (its compaction interval is 1)
+    const int repeat = max(1, cfg.compact_every);
+    if (W.live_tail) k_transport_cta<SPL, WARPS, kModeLive><<<ctas, WARPS * 32, smem, st>>>(W, O, ng, 1);
+    else if (repeat > 1) k_transport_cta<SPL, WARPS, kModeRepeat><<<ctas, WARPS * 32, smem, st>>>(W, O, ng, repeat);
+    else k_transport_cta<SPL, WARPS, kModeFixed><<<ctas, WARPS * 32, smem, st>>>(W, O, ng, 1);
     return cudaGetLastError();
 }
 
@@ -345,8 +378,13 @@ cudaError_t launch_transport_cta(const WorkDev &W, const OutDev &O, const Launch
 
 template <int SPL, int WARPS>
 static cudaError_t preload_cta() {
-    return ensure_dynamic_smem(reinterpret_cast<const void *>(k_transport_cta<SPL, WARPS>),
-                               sizeof(CtaPool<SPL>) * WARPS + (size_t)kMaxStagedGeoms * sizeof(GeomDev));
+    const size_t bytes = sizeof(CtaPool<SPL>) * WARPS + (size_t)kMaxStagedGeoms * sizeof(GeomDev);
+    cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void *>(k_transport_cta<SPL, WARPS, kModeFixed>), bytes);
+    if (e == cudaSuccess)
+        e = ensure_dynamic_smem(reinterpret_cast<const void *>(k_transport_cta<SPL, WARPS, kModeRepeat>), bytes);
+    if (e == cudaSuccess)
+        e = ensure_dynamic_smem(reinterpret_cast<const void *>(k_transport_cta<SPL, WARPS, kModeLive>), bytes);
+    return e;
 }
 
 // load every instantiation and set its shared-memory limit (internal.h)
