@@ -127,8 +127,8 @@ TRANSPORT_DETAIL = dict(id="k_transport_cta_sweep_position_2e6", sha1=None, issu
                         simt_efficiency=None)
 # DRAM bytes of the digitizer back end (make_keys .. job_stats of one step), per single.
 DIGITIZER_SOURCES = ("device.cuh", "sort.cu")
-DIGITIZER_TRAFFIC = dict(id="traffic_sensitivity_sweep_122x1e7", sha1="e89c00f723ab94c4c2a9e21ce83ac296c1ea3af2",
-                         bytes_per_single=528.7)
+DIGITIZER_TRAFFIC = dict(id="traffic_digitizer_sweep_8x1e7", sha1="b915a3a10ffec48e46a9c2565b39c68faaa2da0e",
+                         bytes_per_single=463.0)
 
 
 def _current(entry, sources):

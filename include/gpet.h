@@ -495,7 +495,9 @@ int gpet_server_create(const gpet_server_config *cfg, gpet_server **out);
 /* Queue one request.  The scanner (and its phantom) must stay alive until the
  * request's result has been taken.  block = 0: GPET_ERR_BUSY when the budget
  * cannot take it now; block = 1: it waits in the queue.  GPET_ERR_OOM when it
- * alone exceeds the budget.  *req_id identifies it for poll / wait. */
+ * alone exceeds the budget, or when a request above piece_decays does not fit
+ * beside one launch arena (its own buffers and the launch that runs its pieces
+ * are held together).  *req_id identifies it for poll / wait. */
 int gpet_server_submit(gpet_server *s, gpet_scanner *sc, const gpet_source *src, const gpet_digitizer *dg,
                        uint64_t n_decays, uint64_t seed, int32_t block, uint64_t *req_id);
 /* *out = NULL while the request runs; its result (ownership passes to the

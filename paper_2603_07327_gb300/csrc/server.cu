@@ -273,8 +273,13 @@ bool admit(gpet_server *S, Pipe &P, std::unique_ptr<Launch> &L, Req *r, bool pie
     } else {
         if (!pieces_ok) return false;
         if (!r->own) {
+            // Its own buffers leave room for one launch arena (charged already
+            // when a launch is open): pieces progress only through launches,
+            // so buffers that took the whole budget would wait forever.
             const size_t need = run_footprint(r->n, r->sc->n_crystals, 1, 1, false);
-            if (!budget_allows(S, need)) return false;
+            const size_t arena = launch_bytes(S);
+            const size_t open_arena = L ? std::min(L->R->arena_bytes, arena) : 0;
+            if (!budget_allows(S, need + arena - open_arena)) return false;
             const int st = make_own(S, P, r);
             if (st != GPET_OK) {
                 std::lock_guard<std::mutex> lk(S->core->mu);
@@ -498,7 +503,11 @@ void pipeline_main(gpet_server *S) {
             work.assign(S->queue.begin(), S->queue.end());
             S->queue.clear();
         }
-        // 2. one pass over the queue: whole requests, and one piece of each split one
+        // 2. one pass over the queue: whole requests, and one piece of each split one.
+        //    Requests without a phantom go first, those with one after (each in
+        //    arrival order): a CTA runs one event type at a time, and its warps
+        //    then hold histories of one kind, not phantom steps beside flights.
+        std::stable_partition(work.begin(), work.end(), [](const Req *r) { return !r->J.has_phantom; });
         bool pieces_ok = true;
         if (open && std::any_of(work.begin(), work.end(), [](Req *r) { return r->split; })) {
             uint64_t taken = 0;
@@ -626,6 +635,13 @@ extern "C" int gpet_server_submit(gpet_server *S, gpet_scanner *sc, const gpet_s
         const size_t est = r->est;
         delete r;
         return gpet_fail(GPET_ERR_OOM, "request needs ~%zu device bytes, more than the whole budget", est);
+    }
+    if (r->split && r->est + launch_bytes(S) > C.budget) {
+        // its buffers and one launch arena, which runs its pieces, must fit together
+        const size_t est = r->est, arena = launch_bytes(S);
+        delete r;
+        return gpet_fail(GPET_ERR_OOM, "request needs ~%zu device bytes and a launch arena of %zu, more than the budget",
+                         est, arena);
     }
     if (S->stop) {
         delete r;

@@ -187,3 +187,27 @@ def test_two_waiters_on_one_request(G):
     got[0].free()
     srv.close()
     sc.close()
+
+
+def test_split_requests_leave_room_for_a_launch(G):
+    """Many split requests at once whose own buffers together exceed the
+    budget less one launch arena: their buffers are made only while a launch
+    arena still fits beside them (pieces run only through launches), so every
+    request completes, and each equals its plain run."""
+    sc = G.Scanner(W.config2_scanner("A"))
+    dg = W.digitizer()
+    srv = G.Server(hbm_budget_bytes=12 * 10**8, piece_decays=200_000)
+    jobs = [((0.0, 0.0, 0.5 * k), 1_000_000, 300 + k) for k in range(30)]
+    ids = [srv.submit(sc, W.point_source(pos), dg, n, seed) for pos, n, seed in jobs]
+    for k, i in enumerate(ids):
+        r = srv.wait(i)
+        if k in (0, 29):
+            pos, n, seed = jobs[k]
+            alone = sc.simulate(W.point_source(pos), dg, n, seed)
+            assert_same(canon(alone), canon(r))
+            alone.free()
+        r.free()
+    st = srv.stats()
+    assert st["completed"] == len(jobs) and st["pieces"] >= 5 * len(jobs)
+    srv.close()
+    sc.close()
