@@ -272,6 +272,10 @@ struct PState {
 
 struct Counters {
     uint32_t det_steps, flights, trials, entered, ph_steps, hits, screened, singles;
+    // events per phase beyond ph_steps and det_steps (the CTA kernel reports
+    // them): decays, flight events (flights less the photon starts that the
+    // axial screen ends), flights after a panel exit, finish events
+    uint32_t src, fl_ev, fl_out, fin;
 };
 
 __device__ __forceinline__ void to_global(const GeomDev &g, PState &s) {
@@ -357,6 +361,7 @@ __device__ __forceinline__ int64_t pick_voxel(const JobDev &J, double target) {
 
 // decay of history h (Sec. 2.3): time, annihilation point, photon-0 direction
 __device__ __forceinline__ void ev_source(const JobDev &J, const GeomDev &g, PState &s, Counters &cnt) {
+    cnt.src++;
     const uint4 r = draw(J.seed, s.h, kTagSource, 0u, 0u, 0u);
     const uint64_t r64 = ((uint64_t)r.x << 32) | r.y;
     s.t0 = __umul64hi(J.t_span_ps, r64);
@@ -446,6 +451,7 @@ __device__ __forceinline__ int ev_phantom(const JobDev &J, const GeomDev &g, con
 // flight to the next panel by line-plane intersection
 __device__ __forceinline__ void ev_flight(const JobDev &J, const GeomDev &g, PState &s, Counters &cnt) {
     cnt.flights++;
+    cnt.fl_ev++;
     float t_in, t_out;
     const int k = flight(g, s.x, s.y, s.z, s.dx, s.dy, s.dz, s.last, t_in, t_out);
     if (k < 0) {

@@ -106,7 +106,10 @@ __device__ __forceinline__ int run_event(int p, const JobDev &J, const GeomDev &
     switch (p) {
         case kPhSource: ev_source(J, g, s, cnt); break;
         case kPhPhantom: st = ev_phantom(J, g, W, s, cnt); break;
-        case kPhFlight: case kPhFlightOut: ev_flight(J, g, s, cnt); break;
+        case kPhFlight: case kPhFlightOut:
+            cnt.fl_out += p == kPhFlightOut ? 1u : 0u;
+            ev_flight(J, g, s, cnt);
+            break;
         case kPhPanel: st = ev_panel<true>(J, g, W, O, s, SL, kCtaS, cnt); break;
         default: st = kStatusBadPhase; break;
     }
@@ -140,7 +143,6 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
     // i - 1 is cleared after the barrier of iteration i, which every read of
     // it precedes and every add of iteration i + 2 follows.
     __shared__ int census[3][8];
-    __shared__ unsigned long long phase_events[WARPS][kNumPh];  // lanes that ran an event, per warp and phase
     __shared__ uint8_t assign[WARPS][32];  // slot of each lane in the chosen phase
     stage_geometry(W, sgeom, ng_smem);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -148,7 +150,6 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
 #pragma unroll
     for (int g = 0; g < SPL; ++g) P.st[kCpack][g * 32 + lane] = 0;
     if (threadIdx.x < 24) (&census[0][0])[threadIdx.x] = 0;
-    if (threadIdx.x < WARPS * kNumPh) (&phase_events[0][0])[threadIdx.x] = 0;
     __syncthreads();
 
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -243,7 +244,6 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
         if (mine == 0) continue;  // nothing of this phase here: wait for the next choice
         ++iters;
         lanes_used += (unsigned long long)min(mine, 32);
-        if (lane == 0) phase_events[wid][best_p] += (unsigned long long)min(mine, 32);  // this warp's row only
         PState s;
         s.phase = kPhIdle;
         s.job = 0;
@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
         if (best_p == kPhFinish) {
             if (active) cload(P, q, s);
             __syncwarp();
+            cnt.fin += active ? 1u : 0u;
             ev_finish<kLive>(W.jobs, W.geoms, O, s, active, SL, kFullMask, cnt);
             if (active) P.st[kCpack][q] = 0;
             may_idle = true;
@@ -279,18 +280,17 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
             }
             cstore(P, q, s, best_p == kPhSource);
         }
-        if constexpr (MODE == kModeRepeat) {  // the repeated events, beyond the one per lane counted above
-            const int extra = __reduce_add_sync(kFullMask, n_ev > 1 ? n_ev - 1 : 0);
-            if (lane == 0) phase_events[wid][best_p] += (unsigned long long)extra;
-        }
         may_idle = may_idle || __any_sync(kFullMask, active && s.phase == kPhIdle);
         __syncwarp();
     }
-    const uint32_t v[8] = {cnt.det_steps, cnt.flights, cnt.trials, cnt.entered, cnt.ph_steps, cnt.hits,
-                           cnt.screened, cnt.singles};
-    const int slot[8] = {0, 1, 2, 3, 4, 5, 8, 9};
+    // totals, then the events per phase (slots 10 + phase: decay, phantom
+    // step, flight, detector step, finish, flight after a panel exit)
+    const uint32_t v[14] = {cnt.det_steps, cnt.flights, cnt.trials, cnt.entered, cnt.ph_steps, cnt.hits,
+                            cnt.screened, cnt.singles, cnt.src, cnt.ph_steps, cnt.fl_ev - cnt.fl_out,
+                            cnt.det_steps, cnt.fin, cnt.fl_out};
+    const int slot[14] = {0, 1, 2, 3, 4, 5, 8, 9, 11, 12, 13, 14, 15, 16};
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 14; ++i) {
         const uint32_t x = __reduce_add_sync(kFullMask, v[i]);
         if (lane == 0 && x) atomicAdd(O.counters + slot[i], (unsigned long long)x);
     }
@@ -299,13 +299,6 @@ __global__ void __launch_bounds__(WARPS * 32, (16 / WARPS > 1 ? 16 / WARPS : 1))
         atomicAdd(O.counters + 7, lanes_used);
     }
     if (status) atomicOr(O.status, status);
-    __syncthreads();  // every warp's event counts are in
-    if (threadIdx.x >= 1 && threadIdx.x < kNumPh) {
-        unsigned long long n = 0;
-#pragma unroll
-        for (int w = 0; w < WARPS; ++w) n += phase_events[w][threadIdx.x];
-        if (n) atomicAdd(O.counters + 10 + threadIdx.x, n);
-    }
 }
 
 // dynamic shared memory and resident CTAs of one shape (the same in every
