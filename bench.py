@@ -118,17 +118,19 @@ class Clocks:
 # Entries are named by capture id (the summary of each capture under that id
 # gives its command).
 TRANSPORT_SOURCES = ("device.cuh", "transport.cuh", "transport.cu", "transport_cta.cu")
-TRANSPORT_CAPTURE = dict(id="transport_sweep_122x1e7", sha1=None, warp_inst_per_pair=None,
-                         dram_bytes_per_pair=None)
+TRANSPORT_CAPTURE = dict(id="k_transport_cta_sweep_122x1e7", sha1="f4a6704d15a30fafa6a2dd16570072434011662a",
+                         warp_inst_per_pair=143.306, dram_bytes_per_pair=9.798)
 # Issue detail of the same kernel from one ncu --set full capture of a
 # 2e6-pair sweep position: issue-active fraction of the schedulers and SIMT
 # efficiency (thread instructions per warp instruction / 32).
-TRANSPORT_DETAIL = dict(id="k_transport_cta_sweep_position_2e6", sha1=None, issue_active=None,
-                        simt_efficiency=None)
+TRANSPORT_DETAIL = dict(id="k_transport_cta_sweep_position_2e6", sha1="f4a6704d15a30fafa6a2dd16570072434011662a",
+                        issue_active=0.494, simt_efficiency=0.583)
+# algorithmic bytes of the digitizer back end per single (the model in run_ours)
+DIGITIZER_BYTES_PER_SINGLE = 386
 # DRAM bytes of the digitizer back end (make_keys .. job_stats of one step), per single.
 DIGITIZER_SOURCES = ("device.cuh", "sort.cu")
-DIGITIZER_TRAFFIC = dict(id="traffic_digitizer_sweep_8x1e7", sha1="b915a3a10ffec48e46a9c2565b39c68faaa2da0e",
-                         bytes_per_single=463.0)
+DIGITIZER_TRAFFIC = dict(id="traffic_digitizer_sweep_8x1e7", sha1="d9695372e3ca7ddcc4677ea7782eb3e4f5a313cc",
+                         bytes_per_single=416.6)
 
 
 def _current(entry, sources):
@@ -530,10 +532,12 @@ def run_ours(args):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        step(counts)
+        step(counts if batch is None else None)
         e1.record()
         e1.synchronize()
         dev_ms.append(e0.elapsed_time(e1))
+        if batch is not None:
+            counts.append(batch.counts())  # host bookkeeping, after the step's end mark
     torch.cuda.synchronize()
     clk = clocks.stop()
     wall = time.perf_counter() - wall0
@@ -582,16 +586,17 @@ def run_ours(args):
             roof["event_isolated"] = dict(error=f"{type(exc).__name__}: {exc}")
 
     # digitizer back end (time sort + coincidences), HBM-bound: algorithmic bytes
-    # per single = key build 24 + 8 radix passes x 32 (histogram read 8, scatter
-    # read 12 + write 12) + gather 84 (index 4, 8 fields read 40 + written 40)
-    # + coincidence pass 34 = 398
+    # per single = key pass 12 (the key the transport wrote read, the index
+    # written) + 8 radix passes x 32 (histogram read 8, scatter read 12 + write
+    # 12) + gather 84 (index 4, 8 fields read 40 + written 40) + coincidence
+    # pass 34 = 386
     singles_step = sum(c["singles"] for c in counts) / args.steps
-    dig_bytes = 398.0 * singles_step
+    dig_bytes = DIGITIZER_BYTES_PER_SINGLE * singles_step
     dig_gbs = dig_bytes / (dg_ms / args.steps / 1000.0) / 1e9 if dg_ms > 0 else None
     hbm_peak = _measured_hbm_gbs()
     roof_dig = dict(bound="hbm", achieved=dig_gbs, peak=hbm_peak, unit="GB/s",
                     frac=(dig_gbs / hbm_peak) if dig_gbs else None, traffic=_digitizer_traffic(singles_step),
-                    bytes_per_single=398,
+                    bytes_per_single=DIGITIZER_BYTES_PER_SINGLE,
                     note="time sort + coincidence sorting; peak = measured copy GB/s; traffic = DRAM bytes of "
                          "all back-end kernels of one step")
 

@@ -113,6 +113,7 @@ struct __align__(128) JobDev {
     RawSingle *s_raw;
     unsigned long long *n_singles;
     unsigned long long s_cap;
+    uint64_t *s_keys;                 // the sort keys of that buffer (its time stamps)
 };
 
 // ---------------------------------------------------------------------------

@@ -296,6 +296,9 @@ int run_plan(Run &R) {
     S.n_in = &H->n_singles;
     S.status = &H->status;
     S.in_raw = O.s_raw;
+    // the transport writes each single's sort key into the sort's first key buffer
+    O.s_keys = S.keys[0];
+    O.key_shift = S.job_shift;
     SD.n = &H->n_sorted;
     C.n = &H->n_coinc;
     C.window_ps = R.d_window;

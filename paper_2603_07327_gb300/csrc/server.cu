@@ -296,6 +296,7 @@ bool admit(gpet_server *S, Pipe &P, std::unique_ptr<Launch> &L, Req *r, bool pie
         J.s_raw = M.O.s_raw;
         J.n_singles = &M.d_hdr->n_singles;
         J.s_cap = M.O.s_cap;
+        J.s_keys = M.O.s_keys;
         J.tally_count = M.d_tally_count;
         J.tally_efx = M.d_tally_efx;
         crystals = 0;

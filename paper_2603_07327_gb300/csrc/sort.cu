@@ -4,6 +4,7 @@
 // Keys are (job << shift) | t_ps, with the job in the fewest high bits that
 // number the launch's jobs (none for one job), so a batch of jobs sorts as
 // independent segments and a single run sorts on the whole 64-bit time.  The
+// transport writes them beside the records.  The
 // sort is a least-significant-digit radix sort with 8-bit
 // digits: one fused pass builds the eight digit histograms, a plan kernel
 // drops the passes whose digit is the same for every key (high time bytes,
@@ -36,7 +37,9 @@ __device__ __forceinline__ unsigned long long sort_n(const SortDev &S) {
     return n < S.cap ? n : S.cap;
 }
 
-// keys + values + the eight digit histograms (smem, then global atomics)
+// Values (the identity permutation) and the eight digit histograms of the
+// keys (smem, then global atomics).  The keys themselves were written by the
+// transport's finish event, next to each single's record.
 __global__ void __launch_bounds__(kSortThreads) k_make_keys(SortDev S) {
     __shared__ uint32_t h[kPasses][256];
     for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
@@ -44,11 +47,7 @@ __global__ void __launch_bounds__(kSortThreads) k_make_keys(SortDev S) {
     const unsigned long long n = sort_n(S);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint4 r0 = __ldg(reinterpret_cast<const uint4 *>(S.in_raw + i));
-        const uint32_t job = __ldg(reinterpret_cast<const uint32_t *>(S.in_raw + i) + 6);
-        const uint64_t t = ((uint64_t)r0.y << 32) | r0.x;
-        const uint64_t key = S.job_shift < 64 ? ((uint64_t)job << S.job_shift) | t : t;
-        S.keys[0][i] = key;
+        const uint64_t key = __ldg(S.keys[0] + i);
         S.vals[0][i] = (uint32_t)i;
 #pragma unroll
         for (int p = 0; p < kPasses; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 0xFF], 1u);

@@ -37,6 +37,11 @@ struct OutDev {
     RawSingle *s_raw;
     unsigned long long *n_singles;
     unsigned long long s_cap;
+    // each kept single's 64-bit time-sort key, at its record's slot: (job <<
+    // key_shift) | t_ps, the time alone when key_shift is 64 (the digitizer's
+    // sort starts from these keys instead of reading the records)
+    uint64_t *s_keys;
+    int key_shift;
     // optional crystal interactions
     uint64_t *hit_h, *hit_t;
     int32_t *hit_gstep, *hit_crystal, *hit_layer, *hit_job;
@@ -175,12 +180,14 @@ __device__ __forceinline__ void warp_refill(const WorkDev &W, uint32_t need, Ref
                 R.waiting = true;  // try again at the next refill
                 break;
             }
-            if (c >= R.jend) {
-                // Another job: the last chunk_start entry <= c.  A warp's
-                // claims increase, so the search starts at its current job
-                // (chunk_start[job] <= c), gallops forward, then bisects.
-                int lo = R.job, hi = W.n_jobs - 1, step = 1;
-                while (lo < hi) {
+            if (!kLive || c >= R.jend) {
+                // The job: the last chunk_start entry <= c.  A live launch's
+                // warp searches from its current job (its claims increase, so
+                // chunk_start[job] <= c), galloping forward, then bisects; a
+                // fixed launch bisects the whole table (cached in L1; measured
+                // faster there).
+                int lo = kLive ? R.job : 0, hi = W.n_jobs - 1, step = 1;
+                while (kLive && lo < hi) {
                     const int probe = min(lo + step, hi);
                     if (table_load<kLive>(W.chunk_start + probe) <= c) {
                         lo = probe;
@@ -685,6 +692,9 @@ __device__ __forceinline__ void ev_finish(const JobDev *__restrict__ jobs, const
                 else if (g.readout_level == 1) panel = (int)(unit / (uint32_t)(g.modules_u * g.modules_v));
                 else panel = (int)(unit / (uint32_t)(g.crystals_per_module * g.modules_u * g.modules_v));
                 const uint64_t t = s.t0 + dt;
+                // the sort key: a job with its own buffer is the one job of its run
+                if (kJobDest && J->s_raw) J->s_keys[slot] = t;
+                else O.s_keys[slot] = O.key_shift < 64 ? ((uint64_t)s.job << O.key_shift) | t : t;
                 uint4 *r = reinterpret_cast<uint4 *>(dst + slot);
                 r[0] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)s.h, (uint32_t)(s.h >> 32));
                 // a job with its own buffer is job 0 of the run that buffer belongs to
