@@ -126,7 +126,7 @@ TRANSPORT_CAPTURE = dict(id="k_transport_cta_sweep_122x1e7", sha1="f4a6704d15a30
 TRANSPORT_DETAIL = dict(id="k_transport_cta_sweep_position_2e6", sha1="f4a6704d15a30fafa6a2dd16570072434011662a",
                         issue_active=0.494, simt_efficiency=0.583)
 # algorithmic bytes of the digitizer back end per single (the model in run_ours)
-DIGITIZER_BYTES_PER_SINGLE = 386
+DIGITIZER_BYTES_PER_SINGLE = 330
 # DRAM bytes of the digitizer back end (make_keys .. job_stats of one step), per single.
 DIGITIZER_SOURCES = ("device.cuh", "sort.cu")
 DIGITIZER_TRAFFIC = dict(id="traffic_digitizer_sweep_8x1e7", sha1="d9695372e3ca7ddcc4677ea7782eb3e4f5a313cc",
@@ -587,9 +587,9 @@ def run_ours(args):
 
     # digitizer back end (time sort + coincidences), HBM-bound: algorithmic bytes
     # per single = key pass 12 (the key the transport wrote read, the index
-    # written) + 8 radix passes x 32 (histogram read 8, scatter read 12 + write
-    # 12) + gather 84 (index 4, 8 fields read 40 + written 40) + coincidence
-    # pass 34 = 386
+    # written) + 8 one-sweep radix passes x 25 (key and index read 12 and
+    # written 12, look-back words 1) + gather 84 (index 4, 8 fields read 40 +
+    # written 40) + coincidence pass 34 = 330
     singles_step = sum(c["singles"] for c in counts) / args.steps
     dig_bytes = DIGITIZER_BYTES_PER_SINGLE * singles_step
     dig_gbs = dig_bytes / (dg_ms / args.steps / 1000.0) / 1e9 if dg_ms > 0 else None

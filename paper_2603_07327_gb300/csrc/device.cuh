@@ -42,8 +42,9 @@ enum : uint32_t { kTagSource = 1u, kTagPhantom = 2u, kTagDetector = 3u, kTagDigi
 // device status codes (host maps them to GPET_ERR_*)
 // kStatusBadPhase: a history in a phase no event handles (an internal error);
 // the history is dropped, so no event loop can spin on it.
-// kStatusSortStall: a radix-sort tile copy did not complete within the wait
-// limit; the sort stops and its output is invalid (an internal error).
+// kStatusSortStall: a radix-sort tile copy or look-back did not complete
+// within the wait limit, or a pass computed an offset past its keys; the sort
+// stops (or skips the write) and its output is invalid (an internal error).
 // kStatusLiveStall: a live launch found no new work and no end of the work
 // queue for the whole idle-wait limit; its CTAs stop (an internal error).
 enum : int { kStatusOk = 0, kStatusTimeout = 1, kStatusOverflow = 2, kStatusBadPhase = 4, kStatusSortStall = 8,

@@ -33,6 +33,11 @@ struct SortDev {
     const RawSingle *in_raw;         // unsorted singles
     int *status;                     // run status word (kStatusSortStall), or NULL: unstaged passes
     int job_shift;                   // sort key = (job << job_shift) | t_ps; 64: the key is t_ps alone
+    // one-sweep passes (the simulation path): decoupled look-back words, two
+    // buffers of [tiles][256] that alternate between active passes, and a
+    // tile counter per pass; NULL where the passes run through tile_hist
+    unsigned long long *lb[2] = {nullptr, nullptr};
+    unsigned int *tile_ctr = nullptr;
 };
 
 // Bit position of the job index in the 64-bit sort keys of a launch of n_jobs

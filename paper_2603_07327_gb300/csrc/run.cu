@@ -203,7 +203,8 @@ int run_plan(Run &R) {
     cv.take(S.keys[0], cap); cv.take(S.keys[1], cap);
     cv.take(S.vals[0], cap); cv.take(S.vals[1], cap);
     cv.take(S.plan, 32);
-    cv.take(S.tile_hist, 256 * tiles);
+    cv.take(S.lb[0], 256 * tiles); cv.take(S.lb[1], 256 * tiles);
+    cv.take(S.tile_ctr, 8);
     // sorted singles
     SinglesDev &SD = R.SD;
     cv.take(SD.t, cap); cv.take(SD.h, cap);
@@ -251,7 +252,7 @@ int run_plan(Run &R) {
     }
     rebase(O.ovf_h, base); rebase(O.ovf_job, base);
     rebase(S.keys[0], base); rebase(S.keys[1], base); rebase(S.vals[0], base); rebase(S.vals[1], base);
-    rebase(S.plan, base); rebase(S.tile_hist, base);
+    rebase(S.plan, base); rebase(S.lb[0], base); rebase(S.lb[1], base); rebase(S.tile_ctr, base);
     rebase(SD.t, base); rebase(SD.h, base); rebase(SD.unit, base); rebase(SD.panel, base); rebase(SD.job, base);
     rebase(SD.e, base); rebase(SD.eraw, base); rebase(SD.doi, base);
     rebase(C.flag, base); rebase(C.tile_cnt, base); rebase(C.a, base); rebase(C.b, base);
@@ -448,7 +449,7 @@ int run_collect(Run &R) {
                          H.counters[17] * 1e-9, H.counters[18], H.counters[19],
                          (unsigned long long)R.live_tail);
     if (H.status & kStatusSortStall)
-        return gpet_fail(GPET_ERR_CUDA, "internal error: a time-sort tile copy did not complete");
+        return gpet_fail(GPET_ERR_CUDA, "internal error: a time-sort pass did not complete (a tile copy or look-back wait ran out, or an offset was out of range)");
     if (H.status & kStatusOverflow)
         return gpet_fail(GPET_ERR_OVERFLOW, "a history touched more than 64 readout units");
     return GPET_OK;
@@ -484,7 +485,7 @@ size_t run_footprint(uint64_t total_decays, int64_t total_crystals, int n_jobs, 
     b += cap * sizeof(RawSingle);                // raw singles
     b += hcap * (8 + 8 + 4 * 4 + 12 + 4);        // hits
     b += ocap * 12;                              // overflow list
-    b += cap * (2 * 8 + 2 * 4) + 256 * 4 * tiles + 128;  // sort
+    b += cap * (2 * 8 + 2 * 4) + 2 * 256 * 8 * tiles + 8 * 4 + 128;  // sort (look-back words, tile counters)
     b += cap * (8 + 8 + 4 * 6);                  // sorted singles
     b += cap + 4 * tiles + 2 * 4 * (cap / 2 + 1); // coincidences
     b += 8 * (n_jobs + 1) * 2 + 8 * n_jobs * 3;  // per-job statistics

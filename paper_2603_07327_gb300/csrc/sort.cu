@@ -8,8 +8,11 @@
 // sort is a least-significant-digit radix sort with 8-bit
 // digits: one fused pass builds the eight digit histograms, a plan kernel
 // drops the passes whose digit is the same for every key (high time bytes,
-// unused job bits), and every remaining pass is tile histogram -> per-digit
-// scan -> stable scatter.  Stable ranks inside a tile come from the lanes of
+// unused job bits), and in the simulation path every remaining pass is one
+// kernel (k_onesweep: tiles claimed in order, each tile's digit offsets from
+// the global histogram and a decoupled look-back over the tiles before it).
+// The allocation-free sort runs each pass as tile histogram -> per-digit scan
+// -> stable scatter.  Stable ranks inside a tile come from the lanes of
 // a warp with the same digit (the intersection of bit-plane ballots), in input
 // order.  In the simulation path the scatter's input tiles are streamed into
 // shared memory by the bulk-copy engine (cp.async.bulk completing on an
@@ -51,6 +54,13 @@ __global__ void __launch_bounds__(kSortThreads) k_make_keys(SortDev S) {
         S.vals[0][i] = (uint32_t)i;
 #pragma unroll
         for (int p = 0; p < kPasses; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 0xFF], 1u);
+    }
+    // the first active pass's look-back words (each pass clears the next one's)
+    if (S.lb[0]) {
+        const unsigned long long words = (n + kTile - 1) / kTile * 256;
+        for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+             i += (unsigned long long)gridDim.x * blockDim.x)
+            S.lb[0][i] = 0ull;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kPasses * 256; i += blockDim.x) {
@@ -109,7 +119,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_hist(SortDev S, int p) {
     }
 }
 
-// block-wide exclusive scan of one value per thread (blockDim = 1024)
+// block-wide exclusive scan of one value per thread (blockDim a multiple of 32, at most 1024)
 __device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t &total, uint32_t *sw) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t x = v;
@@ -352,10 +362,231 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_scatter(SortDev S, int p) {
     }
 }
 
+// Decoupled look-back words of the one-sweep passes: the kind in the top two
+// bits (a tile's own count of a digit, or the count of that digit over all
+// tiles up to and including it), the count below.  A word is written whole
+// (one aligned 64-bit store), so a reader sees 0 or a complete word.
+constexpr unsigned long long kLbAgg = 1ull << 62, kLbIncl = 2ull << 62, kLbCount = (1ull << 62) - 1ull;
+// polls of a look-back word before the pass gives up (with 64 ns sleeps after
+// the first 64 polls: about a second); a tile whose owner never publishes is
+// reported, not waited for forever
+constexpr int kLookbackPolls = 1 << 24;
+
+__device__ __forceinline__ void lb_store(unsigned long long *p, unsigned long long v) {
+    *reinterpret_cast<volatile unsigned long long *>(p) = v;
+}
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long *p) {
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+
+// One radix pass in one kernel (the simulation path): tiles are claimed in
+// order from a counter; a tile's digit counts come from its own ranking, and
+// its global run starts from the digits' bases (the global histogram) plus
+// the counts of the tiles before it, found by looking back over their
+// published words until an inclusive count.  Every tile a CTA waits on was
+// claimed earlier by a running CTA, and waits only on tiles before it, so the
+// waits end.  The tile histogram and digit scan passes are not needed.  Tiles
+// are staged into shared memory one ahead by the bulk-copy engine, as in
+// k_scatter; the ranking and the write-out are those of k_scatter.
+__global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(SortDev S, int p) {
+    if (!S.plan[p]) return;
+    extern __shared__ __align__(16) unsigned char scatter_raw[];
+    ScatterSmem &sm = *reinterpret_cast<ScatterSmem *>(scatter_raw);
+    ScatterStage &sg = *reinterpret_cast<ScatterStage *>(scatter_raw + sizeof(ScatterSmem));
+    __shared__ uint32_t dbase[256];
+    __shared__ uint32_t thist[256];  // the tile's own digit counts
+    __shared__ unsigned long long tile_sh[2];  // the tile being sorted, the one claimed next
+    const int src = S.plan[kPasses + p];
+    const unsigned long long n = sort_n(S);
+    const unsigned long long tiles = (n + kTile - 1) / kTile;
+    const unsigned long long full_tiles = n / kTile;
+    constexpr int kWarps = kSortThreads / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint64_t *kin = src ? S.keys[1] : S.keys[0];
+    const uint32_t *vin = src ? S.vals[1] : S.vals[0];
+    uint64_t *kout = src ? S.keys[0] : S.keys[1];
+    uint32_t *vout = src ? S.vals[0] : S.vals[1];
+    unsigned long long *lbc = src ? S.lb[1] : S.lb[0];  // this pass's words
+    unsigned long long *lbn = src ? S.lb[0] : S.lb[1];  // the next active pass's, cleared here
+    {
+        // the digits' bases: exclusive scan of this pass's global histogram
+        uint32_t tot;
+        dbase[threadIdx.x] = block_exscan(S.ghist[p * 256 + threadIdx.x], tot, sm.sw);
+    }
+    uint32_t parity = 0;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sg.bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const unsigned long long t0 = atomicAdd(S.tile_ctr + p, 1u);
+        tile_sh[0] = t0;
+        tile_sh[1] = tiles;
+        if (t0 < full_tiles) stage_issue(sg, kin, vin, t0);
+    }
+    __syncthreads();
+    for (;;) {
+        const unsigned long long t = tile_sh[0];
+        if (t >= tiles) break;
+        for (int i = threadIdx.x; i < kWarps * 256; i += blockDim.x) (&sm.wh[0][0])[i] = 0;
+        thist[threadIdx.x] = 0;
+        const unsigned long long wb = t * kTile + (unsigned long long)w * (32 * kSortItems);
+        uint64_t k[kSortItems];
+        uint32_t v[kSortItems];
+        uint32_t rank[kSortItems];
+        if (t < full_tiles) {
+            const bool ok = stage_wait(smem_addr(&sg.bar), parity);
+            if (!__syncthreads_and(ok)) {
+                if (threadIdx.x == 0) {
+                    atomicOr(S.status, kStatusSortStall);
+                    stage_wait(smem_addr(&sg.bar), parity);  // let the copy in flight land
+                }
+                return;
+            }
+            parity ^= 1u;
+            const int lb = w * (32 * kSortItems) + lane;
+#pragma unroll
+            for (int j = 0; j < kSortItems; ++j) {
+                k[j] = sg.keys[lb + j * 32];
+                v[j] = sg.vals[lb + j * 32];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kSortItems; ++j) {
+                const unsigned long long i = wb + (unsigned long long)j * 32 + lane;
+                k[j] = i < n ? __ldg(kin + i) : 0ull;
+                v[j] = i < n ? __ldg(vin + i) : 0u;
+            }
+        }
+        __syncthreads();  // the staging buffer is free and the histograms are cleared
+        if (threadIdx.x == 0) {
+            // claim the next tile and stream it in while this one is sorted
+            const unsigned long long nt = atomicAdd(S.tile_ctr + p, 1u);
+            tile_sh[1] = nt;
+            if (nt < full_tiles) stage_issue(sg, kin, vin, nt);
+        }
+        // The tile's digit counts first, published before the ranking, so that
+        // the tiles after it rarely find its word missing.
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const unsigned long long i = wb + (unsigned long long)j * 32 + lane;
+            if (i < n) atomicAdd(&thist[(uint32_t)((k[j] >> (8 * p)) & 0xFF)], 1u);
+        }
+        __syncthreads();
+        unsigned long long *row = lbc + t * 256;
+        const uint32_t cnt = thist[threadIdx.x];
+        lb_store(row + threadIdx.x, (t == 0 ? kLbIncl : kLbAgg) | cnt);
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const unsigned long long i = wb + (unsigned long long)j * 32 + lane;
+            const bool ok = i < n;
+            const uint32_t d = ok ? (uint32_t)((k[j] >> (8 * p)) & 0xFF) : 256u;
+            uint32_t peers = kFullMask;
+#pragma unroll
+            for (int bit = 0; bit < 9; ++bit) {
+                const uint32_t m = __ballot_sync(kFullMask, (d >> bit) & 1u);
+                peers &= ((d >> bit) & 1u) ? m : ~m;
+            }
+            const uint32_t before = (d < 256u) ? sm.wh[w][d] : 0u;
+            rank[j] = before + __popc(peers & lane_lt());
+            __syncwarp();
+            if (d < 256u && (peers & lane_lt()) == 0) sm.wh[w][d] = before + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        uint32_t lstart;
+        {
+            const int d = threadIdx.x;  // kSortThreads == 256 digits
+            uint32_t c = 0;
+#pragma unroll
+            for (int ww = 0; ww < kWarps; ++ww) {
+                const uint32_t x = sm.wh[ww][d];
+                sm.wh[ww][d] = c;
+                c += x;
+            }
+            uint32_t tot;
+            lstart = block_exscan(c, tot, sm.sw);
+#pragma unroll
+            for (int ww = 0; ww < kWarps; ++ww) sm.wh[ww][d] += lstart;
+        }
+        __syncthreads();
+        // the tile in digit order in shared memory; its global offsets follow
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const unsigned long long i = wb + (unsigned long long)j * 32 + lane;
+            if (i < n) {
+                const uint32_t lp = sm.wh[w][(uint32_t)((k[j] >> (8 * p)) & 0xFF)] + rank[j];
+                sm.keys[lp] = k[j];
+                sm.vals[lp] = v[j];
+            }
+        }
+        // Look back: add the counts of the tiles before this one, eight words
+        // per round trip, newest first, until an inclusive count.
+        int fail = 0;
+        {
+            const int d = threadIdx.x;
+            unsigned long long excl = 0;
+            if (t > 0) {
+                constexpr int kWin = 8;
+                unsigned long long j = t;  // tiles [0, j) not yet added
+                bool found = false;
+                int polls = 0;
+                while (!found && !fail) {
+                    unsigned long long wv[kWin];
+#pragma unroll
+                    for (int q = 0; q < kWin; ++q)
+                        wv[q] = (unsigned long long)q < j ? lb_load(lbc + (j - 1 - q) * 256 + d) : kLbIncl;
+#pragma unroll
+                    for (int q = 0; q < kWin; ++q) {
+                        if (found || fail || (unsigned long long)q >= j) break;
+                        unsigned long long x = wv[q];
+                        while ((x >> 62) == 0) {
+                            if (++polls > kLookbackPolls) { fail = 1; break; }
+                            if (polls > 64) __nanosleep(64);
+                            x = lb_load(lbc + (j - 1 - q) * 256 + d);
+                        }
+                        if (fail) break;
+                        excl += x & kLbCount;
+                        if ((x >> 62) == 2) found = true;
+                    }
+                    j = j > (unsigned long long)kWin ? j - kWin : 0;
+                    if (j == 0 && !found) fail = 1;  // tile 0 always publishes an inclusive count
+                }
+                if (!fail) lb_store(row + d, kLbIncl | (excl + cnt));
+            }
+            sm.gdelta[d] = dbase[d] + (uint32_t)excl - lstart;
+            lbn[t * 256 + d] = 0ull;
+        }
+        if (__syncthreads_or(fail)) {
+            if (threadIdx.x == 0) {
+                atomicOr(S.status, kStatusSortStall);
+                if (tile_sh[1] < full_tiles) stage_wait(smem_addr(&sg.bar), parity);  // the copy in flight
+            }
+            return;
+        }
+        const unsigned long long rem = n - t * kTile;
+        const int tn = rem < (unsigned long long)kTile ? (int)rem : kTile;
+        bool stray = false;
+        for (int i = threadIdx.x; i < tn; i += kSortThreads) {
+            const uint64_t key = sm.keys[i];
+            const uint32_t pos = sm.gdelta[(uint32_t)((key >> (8 * p)) & 0xFF)] + (uint32_t)i;
+            if (pos < n) {
+                kout[pos] = key;
+                vout[pos] = sm.vals[i];
+            } else {
+                stray = true;  // an offset past the keys: reported, never written
+            }
+        }
+        if (stray) atomicOr(S.status, kStatusSortStall);
+        __syncthreads();
+        if (threadIdx.x == 0) tile_sh[0] = tile_sh[1];
+        __syncthreads();
+    }
+}
+
 static cudaError_t scatter_smem_attr() {
     cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void *>(k_scatter<false>), kScatterSmem);
+    if (e == cudaSuccess) e = ensure_dynamic_smem(reinterpret_cast<const void *>(k_scatter<true>), kScatterSmemStaged);
     if (e != cudaSuccess) return e;
-    return ensure_dynamic_smem(reinterpret_cast<const void *>(k_scatter<true>), kScatterSmemStaged);
+    return ensure_dynamic_smem(reinterpret_cast<const void *>(k_onesweep), kScatterSmemStaged);
 }
 
 // singles into time order
@@ -525,19 +756,19 @@ cudaError_t launch_radix_passes(const SortDev &S, int sm_count, cudaStream_t st)
 
 cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const CoincDev &C, int sm_count,
                               cudaStream_t st) {
-    if (!S.status) return cudaErrorInvalidValue;  // the staged passes report a stalled copy there
+    // the staged passes report a stalled copy or look-back in the status word
+    if (!S.status || !S.lb[0] || !S.lb[1] || !S.tile_ctr) return cudaErrorInvalidValue;
     cudaError_t e = scatter_smem_attr();
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(S.ghist, 0, sizeof(uint32_t) * kPasses * 256, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.tile_ctr, 0, sizeof(unsigned int) * kPasses, st);
     if (e != cudaSuccess) return e;
     k_make_keys<<<sm_count * 4, kSortThreads, 0, st>>>(S);
     k_plan<<<1, kPasses * 32, 0, st>>>(S);
-    for (int p = 0; p < kPasses; ++p) {
-        const int tg = (int)(S.max_tiles < (unsigned long long)sm_count * 8 ? S.max_tiles : (unsigned long long)sm_count * 8);
-        k_tile_hist<<<tg, kSortThreads, 0, st>>>(S, p);
-        k_digit_scan<<<256, 1024, 0, st>>>(S, p);
-        k_scatter<true><<<tg, kSortThreads, kScatterSmemStaged, st>>>(S, p);
-    }
+    // two CTAs per SM are resident; more would only claim tiles later
+    const int tg = (int)(S.max_tiles < (unsigned long long)sm_count * 2 ? (S.max_tiles ? S.max_tiles : 1)
+                                                                        : (unsigned long long)sm_count * 2);
+    for (int p = 0; p < kPasses; ++p) k_onesweep<<<tg, kSortThreads, kScatterSmemStaged, st>>>(S, p);
     const int grid = sm_count * 4;
     k_gather<<<grid, 256, 0, st>>>(S, out);
     // a cluster's flags are written by the thread at its start, possibly past
@@ -556,6 +787,7 @@ cudaError_t launch_sort_coinc(const SortDev &S, const SinglesDev &out, const Coi
 cudaError_t preload_sort_kernels() {
     const void *fns[] = {reinterpret_cast<const void *>(k_make_keys), reinterpret_cast<const void *>(k_plan),
                          reinterpret_cast<const void *>(k_tile_hist), reinterpret_cast<const void *>(k_digit_scan),
+                         reinterpret_cast<const void *>(k_onesweep),
                          reinterpret_cast<const void *>(k_gather), reinterpret_cast<const void *>(k_coinc_flags),
                          reinterpret_cast<const void *>(k_coinc_count), reinterpret_cast<const void *>(k_coinc_scan),
                          reinterpret_cast<const void *>(k_coinc_write), reinterpret_cast<const void *>(k_job_stats)};
