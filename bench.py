@@ -129,8 +129,8 @@ TRANSPORT_DETAIL = dict(id="k_transport_cta_sweep_position_2e6", sha1="f4a6704d1
 DIGITIZER_BYTES_PER_SINGLE = 330
 # DRAM bytes of the digitizer back end (make_keys .. job_stats of one step), per single.
 DIGITIZER_SOURCES = ("device.cuh", "sort.cu")
-DIGITIZER_TRAFFIC = dict(id="traffic_digitizer_sweep_8x1e7", sha1="d9695372e3ca7ddcc4677ea7782eb3e4f5a313cc",
-                         bytes_per_single=416.6)
+DIGITIZER_TRAFFIC = dict(id="traffic_digitizer_sweep_8x1e7", sha1="dac322b49793164d8e2975ec5fbef23c0b5ed50f",
+                         bytes_per_single=359.0)
 
 
 def _current(entry, sources):
