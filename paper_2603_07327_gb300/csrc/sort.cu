@@ -481,9 +481,13 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(SortDev S, int p) 
             const uint32_t d = ok ? (uint32_t)((k[j] >> (8 * p)) & 0xFF) : 256u;
             uint32_t peers = kFullMask;
 #pragma unroll
-            for (int bit = 0; bit < 9; ++bit) {
+            for (int bit = 0; bit < 8; ++bit) {
                 const uint32_t m = __ballot_sync(kFullMask, (d >> bit) & 1u);
                 peers &= ((d >> bit) & 1u) ? m : ~m;
+            }
+            if (t >= full_tiles) {  // the last, partial tile: separate the lanes past the end
+                const uint32_t m = __ballot_sync(kFullMask, d >> 8);
+                peers &= (d >> 8) ? m : ~m;
             }
             const uint32_t before = (d < 256u) ? sm.wh[w][d] : 0u;
             rank[j] = before + __popc(peers & lane_lt());
