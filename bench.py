@@ -129,8 +129,8 @@ TRANSPORT_DETAIL = dict(id="k_transport_cta_sweep_position_2e6", sha1="f4a6704d1
 DIGITIZER_BYTES_PER_SINGLE = 330
 # DRAM bytes of the digitizer back end (make_keys .. job_stats of one step), per single.
 DIGITIZER_SOURCES = ("device.cuh", "sort.cu")
-DIGITIZER_TRAFFIC = dict(id="traffic_digitizer_sweep_8x1e7", sha1="dac322b49793164d8e2975ec5fbef23c0b5ed50f",
-                         bytes_per_single=359.0)
+DIGITIZER_TRAFFIC = dict(id="traffic_digitizer_sweep_8x1e7", sha1="6fd97e665d63322ce912e6a20bee0aebc691fc9c",
+                         bytes_per_single=361.6)
 
 
 def _current(entry, sources):
@@ -696,9 +696,9 @@ def run_ours(args):
                 per_step_counts=dict(hits=sum(c["hits"] for c in counts) // args.steps,
                                      singles=sum(c["singles"] for c in counts) // args.steps,
                                      coincidences=sum(c["coincidences"] for c in counts) // args.steps))
-    # kernels per launch: transport + redo, keys, plan, 8 x 3 radix passes, gather, 4 coincidence
-    # kernels, job statistics
-    per_launch = 2 + 2 + 8 * 3 + 1 + 4 + 1
+    # kernels per launch: transport + redo, key pass, plan, 8 one-sweep radix passes, gather,
+    # 4 coincidence kernels, job statistics
+    per_launch = 2 + 2 + 8 + 1 + 4 + 1
     line["gpu_launches"] = per_launch * args.steps * (1 if args.form == "batched" else len(jobs))
     if args.form == "batched" and args.compare_plain:
         # the plain per-position form on the same sweep, for the batched-vs-plain metric
