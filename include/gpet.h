@@ -470,7 +470,12 @@ int gpet_event_costs(gpet_scanner *sc, const gpet_source *src, const gpet_digiti
  * per launch (a quarter of the budget at most) and per split request, until
  * the results that view it are freed, so a client that keeps results while it
  * waits for later requests can stall admission: free results once read.  A
- * request's result equals gpet_simulate's for the same inputs. */
+ * launch's results then move to memory of their own size, and its buffers go
+ * back: during that copy the server holds both, so its peak can pass the
+ * budget by the size of the results being copied.  A request whose singles
+ * overflowed its launch's buffer runs again alone, at its exact size, once no
+ * launch is running; that run is not held to the budget either.  A request's
+ * result equals gpet_simulate's for the same inputs. */
 typedef struct gpet_server gpet_server;
 typedef struct {
     size_t hbm_budget_bytes;      /* device memory the server may hold */

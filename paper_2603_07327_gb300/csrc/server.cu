@@ -387,7 +387,10 @@ void finish_launch(gpet_server *S, Launch &L, int close_status, const std::strin
         S->stats.digitizer_ms += std::max(0.f, L.R->digitizer_ms);
     }
     // the results move to memory of their own size, and the launch's buffers
-    // go back at once (results a client keeps then hold only what they are)
+    // go back at once (results a client keeps then hold only what they are).
+    // The copy is made whatever the budget's state: results left viewing the
+    // launch's buffers would keep the whole arena charged, and a client that
+    // holds them could then keep every later launch from opening.
     std::shared_ptr<Run> views = L.R;
     if (st == GPET_OK && !L.whole.empty()) {
         int cst = GPET_OK;
@@ -508,7 +511,21 @@ void pipeline_main(gpet_server *S) {
         //    Requests without a phantom go first, those with one after (each in
         //    arrival order): a CTA runs one event type at a time, and its warps
         //    then hold histories of one kind, not phantom steps beside flights.
-        std::stable_partition(work.begin(), work.end(), [](const Req *r) { return !r->J.has_phantom; });
+        //    Only while two more launch arenas fit the budget: a client that
+        //    takes results in submission order holds the later ones, and once
+        //    the budget runs short the request it waits for must come first.
+        //    The results of the launch still finishing take at most one arena,
+        //    so the next launch can still open, and takes the oldest request.
+        const size_t arena = launch_bytes(S);
+        bool reorder = false;
+        {
+            std::lock_guard<std::mutex> lk(C.mu);
+            reorder = C.in_use + 2 * arena <= C.budget;
+        }
+        if (reorder)
+            std::stable_partition(work.begin(), work.end(), [](const Req *r) { return !r->J.has_phantom; });
+        else  // arrival order again: ids rise with submission
+            std::sort(work.begin(), work.end(), [](const Req *a, const Req *b) { return a->id < b->id; });
         bool pieces_ok = true;
         if (open && std::any_of(work.begin(), work.end(), [](Req *r) { return r->split; })) {
             uint64_t taken = 0;

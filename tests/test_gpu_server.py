@@ -159,6 +159,8 @@ def test_admission_by_footprint(G):
     st = srv.stats()
     assert st["completed"] == len(ids)
     assert st["rejected"] == busy and busy > 0
+    # the budget, passed at most by the results being copied to their own memory
+    assert st["peak_bytes"] <= 200 * 10**6 * 5 // 4
     srv.close()
 
 
@@ -209,5 +211,67 @@ def test_split_requests_leave_room_for_a_launch(G):
         r.free()
     st = srv.stats()
     assert st["completed"] == len(jobs) and st["pieces"] >= 5 * len(jobs)
+    # the budget, passed at most by the results being copied to their own memory
+    assert st["peak_bytes"] <= 12 * 10**8 * 5 // 4
     srv.close()
     sc.close()
+
+
+def test_in_order_client_behind_a_phantom_request(G):
+    """A phantom request ahead of 200 point-source requests, under a budget
+    that the point-source results alone would more than fill, and a client
+    that takes results in submission order.  Admission passes put requests
+    without a phantom first only while two launch arenas still fit the
+    budget; past that they take arrival order, so the phantom request is
+    admitted before the results held behind it fill the budget.  If the
+    client stalls anyway, it releases every result in any order, so that the
+    pipeline and close() still end, and the test fails."""
+    dg = W.digitizer()
+    sc = G.Scanner(W.config2_scanner("A"))
+    scp = G.Scanner(W.config2_scanner("A"), W.hot_rod_phantom())
+    budget = 12 * 10**8
+    srv = G.Server(hbm_budget_bytes=budget)
+    n = 200
+    ids = [None] * (n + 1)
+
+    def submit_all():
+        ids[0] = srv.submit(scp, W.phantom_source(), dg, 1_000_000, 7)
+        for k in range(n):
+            ids[k + 1] = srv.submit(sc, W.point_source((0.0, 0.0, 0.1 * k)), dg, 1_000_000, 100 + k)
+
+    th = threading.Thread(target=submit_all)
+    th.start()
+    deadline = time.perf_counter() + 90.0
+    taken = 0
+    held = 0
+    while taken <= n and time.perf_counter() < deadline:
+        r = srv.poll(ids[taken]) if ids[taken] is not None else None
+        if r is None:
+            time.sleep(0.002)
+            continue
+        assert r.counts()["singles"] > 0
+        if taken == 0:
+            assert r.counts()["phantom_steps"] > 0
+        held = max(held, srv.stats()["bytes_in_use"])
+        r.free()
+        taken += 1
+    stalled = taken <= n
+    if stalled:
+        left = set(range(taken, n + 1))
+        drain = time.perf_counter() + 90.0
+        while left and time.perf_counter() < drain:
+            for k in sorted(left):
+                r = srv.poll(ids[k]) if ids[k] is not None else None
+                if r is not None:
+                    r.free()
+                    left.discard(k)
+            time.sleep(0.01)
+    th.join()
+    st = srv.stats()
+    srv.close()
+    sc.close()
+    scp.close()
+    assert not stalled, f"request {taken} not done while the client held the later results"
+    assert st["completed"] == n + 1
+    # the budget, passed at most by the results being copied to their own memory
+    assert st["peak_bytes"] <= budget * 5 // 4
