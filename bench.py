@@ -691,7 +691,8 @@ def run_ours(args):
                          copy_ms_per_step=1000 * (e2e_dt - e2e_sim_s), copy_ms_steps=[round(c, 2) for c in copy_ms],
                          d2h_gbs=d2h / (1e-3 * min(copy_ms)) / 1e9 if copy_ms and min(copy_ms) > 0 else None,
                          plain_pinned_d2h_gbs=plain_gbs, host_buffers="pinned, caller-owned, reused",
-                         copies="one async copy per array of the whole launch, arrays on concurrent streams"),
+                         copies="one async copy per array of the whole launch, arrays on concurrent streams; into page-locked "
+                                "memory the library copies by SM stores over the host link"),
                 stages=dict(transport_ms_per_step=tr_ms / args.steps, digitizer_ms_per_step=dg_ms / args.steps),
                 per_step_counts=dict(hits=sum(c["hits"] for c in counts) // args.steps,
                                      singles=sum(c["singles"] for c in counts) // args.steps,

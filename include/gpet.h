@@ -284,11 +284,19 @@ int gpet_result_copy(const gpet_result *r, int32_t which, void *dst, size_t cap_
  * cap_bytes = 0 only queries it.  GPET_ERR_TOO_SMALL when cap_bytes is below
  * the size. */
 int gpet_result_copy_run(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes, size_t *bytes);
-/* The same copy enqueued on `stream` (a cudaStream_t) and returned at once,
- * so that it overlaps later work on other streams (e.g. the next simulation).
- * dst should be pinned host memory for the copy to run asynchronously.  The
- * caller keeps r (and with it the device arrays) alive and dst untouched
- * until the stream has passed the copy. */
+/* The same copy enqueued on `stream` (a cudaStream_t) and returned at once.
+ * The caller keeps r (and with it the device arrays) alive and dst untouched
+ * until the stream has passed the copy.
+ * How both run copies move the bytes: into page-locked host memory
+ * (cudaHostAlloc, cudaHostRegister) whose address is 16-byte aligned, a
+ * kernel whose threads load the device array and store into dst through its
+ * device mapping; anywhere else, cudaMemcpy / cudaMemcpyAsync.  The copy
+ * engines' reads of device memory that had been freed and allocated again
+ * fell to a fifth of the host link's rate once other GPU work had run on the
+ * device, where the stores kept the link's rate (193 GB/s on GB300).  The
+ * kernel needs free SMs: enqueued beside a running persistent launch, it runs
+ * once that launch ends.  Into pageable memory the async copy is not
+ * asynchronous. */
 int gpet_result_copy_run_async(const gpet_result *r, int32_t which, void *dst, size_t cap_bytes, size_t *bytes,
                                void *stream);
 

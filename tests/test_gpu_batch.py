@@ -139,21 +139,31 @@ def test_whole_launch_copy_equals_the_job_views(G):
 
 def test_async_whole_launch_copy_equals_the_blocking_one(G):
     """gpet_result_copy_run_async on a side stream delivers the same bytes as
-    the blocking copy once the stream has passed it."""
+    the blocking copy once the stream has passed it.  Into page-locked memory
+    at a 16-byte boundary the copy is a kernel of SM stores; into pageable
+    memory, or page-locked memory 4 bytes off the boundary, it is a copy-engine
+    copy: every form gives the same bytes, and none writes past the array."""
     import torch
     designs = W.config4(n_designs=3, scale=0.02)
     jobs = [dict(scanner=G.Scanner(d["scanner"]), source=d["source"], digitizer=d["digitizer"],
                  n_decays=d["n_decays"], seed=d["seed"]) for d in designs]
     res = G.simulate_batch(jobs)
     st = torch.cuda.Stream()
-    for w in (G.SINGLES_T_PS, G.SINGLES_E, G.COINC_B, G.TALLY_EFX):
+    for w in (G.SINGLES_T_PS, G.SINGLES_UNIT, G.SINGLES_E, G.COINC_A, G.COINC_B, G.TALLY_COUNT, G.TALLY_EFX):
         nb = res[0].run_nbytes(w)
-        pinned = torch.zeros(nb + 16, dtype=torch.uint8, pin_memory=True)
-        assert res[1].copy_run_into_async(w, pinned.data_ptr(), pinned.numel(), st.cuda_stream) == nb
-        st.synchronize()
         ref = np.zeros(nb, dtype=np.uint8)
-        res[2].copy_run_into(w, ref.ctypes.data, ref.nbytes)
-        np.testing.assert_array_equal(pinned.numpy()[:nb], ref)
+        res[2].copy_run_into(w, ref.ctypes.data, ref.nbytes)   # pageable: copy engine
+        for off in (0, 4):
+            pinned = torch.full((nb + 32,), 0xA5, dtype=torch.uint8, pin_memory=True)
+            assert res[1].copy_run_into_async(w, pinned.data_ptr() + off, nb, st.cuda_stream) == nb
+            st.synchronize()
+            got = pinned.numpy()
+            np.testing.assert_array_equal(got[off:off + nb], ref)
+            assert (got[:off] == 0xA5).all() and (got[off + nb:] == 0xA5).all()
+        blocking = torch.full((nb + 32,), 0xA5, dtype=torch.uint8, pin_memory=True)
+        assert res[0].copy_run_into(w, blocking.data_ptr(), nb) == nb
+        np.testing.assert_array_equal(blocking.numpy()[:nb], ref)
+        assert (blocking.numpy()[nb:] == 0xA5).all()
     for r in res:
         r.free()
     for j in jobs:
