@@ -78,6 +78,7 @@ cudaError_t preload_kernels() {
     e = preload_transport_kernels();
     if (e == cudaSuccess) e = preload_sort_kernels();
     if (e == cudaSuccess) e = preload_window_kernels();
+    if (e == cudaSuccess) e = preload_copy_kernels();
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }

@@ -96,6 +96,7 @@ cudaError_t preload_wave_kernels();
 cudaError_t preload_cta_kernels();
 cudaError_t preload_sort_kernels();
 cudaError_t preload_window_kernels();
+cudaError_t preload_copy_kernels();
 
 // Geometry descriptors a transport launch stages in shared memory: as many of
 // the first min(n_geoms, max_geoms) as fit without fewer resident CTAs than a

@@ -843,6 +843,12 @@ static void *store_target(void *dst, const void *src, size_t bytes) {
     return a.devicePointer;
 }
 
+// load the copy kernel with the others (internal.h)
+cudaError_t gpet::preload_copy_kernels() {
+    cudaFuncAttributes fa;
+    return cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(k_store_to_host));
+}
+
 static cudaError_t store_to_host(void *dst_dev, const void *src, size_t bytes, cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
